@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark: effective TFLOP/s (m*n^2 classical-equivalent) of low(A^T A).
+
+Workload (default): A is 8192 x 8192 FP64, i.i.d. U[-1,1) (seed 2110); one
+step is one ata_lower call computing the lower triangle of C = A^T A with the
+FP64-accurate split-digit emulation (tcgen05 BF16 digit products, exact integer
+accumulation) and the AtA recursion with Strassen on the off-diagonal blocks.
+Inputs are resident in HBM for `value`; `e2e` repeats the measurement with the
+host->device copy of A and the device->host copy of C inside the timed region.
+A (512 MiB) and C (512 MiB) are both larger than the 129 MB L2.
+
+--impl reference times the CPU oracle (the plain FP64 definition, all host
+cores) on a bounded column sample of the same workload.
+
+Multi-GPU: the product does not shard across GPUs (one Gram product per GPU);
+under torchrun every rank computes its own independent replica (weak scaling)
+and value = total work of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A^T A effective TFLOP/s (m·n² eq.) vs plain tiled AtA on GB300 at stated error"
+UNIT = "TFLOP/s"
+MODES = {"f64": 0, "f64_emu": 1, "f32": 2, "f32_bf16": 4}
+DTYPE_DESC = {0: "f64 (DMMA)", 1: "bf16 digits x fp32 acc -> int64 (fp64-accurate)",
+              2: "bf16 digits x fp32 acc -> int64 (fp32-accurate)", 4: "bf16 x fp32"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="f64_emu", choices=list(MODES))
+    ap.add_argument("--m", type=int, default=8192)
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--depth", type=int, default=-1)
+    ap.add_argument("--cutoff", type=int, default=0)
+    ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=2110)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain-tiled, e2e, cpu baseline")
+    ap.add_argument("--ref-seconds", type=float, default=4.0, help="CPU seconds per reference step")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ utils --
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(A_cols_fn, m, n, target_s, threads=0):
+    """Time the oracle (plain definition, all host cores) on the leading
+    column panel of the workload, sized to take about target_s seconds.
+    Returns (effective TFLOP/s, seconds, cores, description)."""
+    import oracle
+    cores = oracle.set_threads(threads)
+    nb = 64
+    A = A_cols_fn(nb)
+    t0 = time.perf_counter()
+    oracle.ata_lower(A)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    # work ~ nb^2: grow the panel to fill the time budget
+    nb = int(min(n, max(64, nb * (target_s / dt) ** 0.5)))
+    A = A_cols_fn(nb)
+    t0 = time.perf_counter()
+    oracle.ata_lower(A)
+    dt = time.perf_counter() - t0
+    work = float(m) * nb * (nb + 1)  # 2 flops per multiply-add of the lower triangle
+    desc = f"low(A[:, :{nb}]^T A[:, :{nb}]) of the {m}x{n} workload ({nb * (nb + 1) // 2} entries)"
+    return work / dt / 1e12, dt, cores, desc
+
+
+# -------------------------------------------------------------- reference --
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2110_13042_gb300 import inputs
+    m, n = args.m, args.n
+    cols_fn = (lambda nb: inputs.uniform(m, n, args.seed, cols=np.arange(nb)))
+    vals, times = [], []
+    cores = 0
+    desc = ""
+    for it in range(args.warmup + args.steps):
+        v, dt, cores, desc = cpu_oracle_sample(cols_fn, m, n, args.ref_seconds)
+        if it >= args.warmup:
+            vals.append(v)
+            times.append(dt)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"A {m}x{n} FP64 U[-1,1) (seed {args.seed}), low(A^T A); "
+                                   "each step a bounded column-panel sample",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours --
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        sys.exit(run_reference(args, rank, world))
+
+    import torch
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        if rank != 0:
+            pass
+        dist.barrier()
+        __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2110_13042_gb300 as ata
+    from paper_2110_13042_gb300 import inputs
+
+    m, n, mode = args.m, args.n, MODES[args.mode]
+    f32 = mode in (2, 4)
+    tdt = torch.float32 if f32 else torch.float64
+    A_host = inputs.uniform(m, n, args.seed + rank)
+    if f32:
+        A_host = A_host.astype(np.float32)
+    A = torch.from_numpy(A_host).to(dev)
+    C = torch.zeros((n, n), dtype=tdt, device=dev)
+    h = ata.Handle(cutoff=args.cutoff, depth=args.depth, slices=args.slices)
+    info = ata.plan_info(m, n, mode, h)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        h.lower(A, C, mode, stream)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / k
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    clocks = ClockSampler(local)
+    for _ in range(args.warmup):
+        step()
+    rc = h.sync(stream)
+    if rc != 0:
+        raise RuntimeError(f"ata_sync: {rc}")
+    clocks.start()
+    ms = timed(step, args.steps, 0)
+    clk = clocks.stop()
+    rc = h.sync(stream)
+    if rc != 0:
+        raise RuntimeError(f"ata_sync after timing: {rc}")
+    eff = float(m) * n * n
+    value = world * eff / (ms * 1e-3) / 1e12
+
+    # Dominant kernel (tcgen05 leaf) timed on the launching stream.
+    h.set_timing(True)
+    phases = []
+    for _ in range(max(3, args.steps // 2)):
+        step()
+        phases.append(h.phase_times())
+    h.set_timing(False)
+    ph = [statistics.median(p[i] for p in phases) for i in range(4)]
+    peaks, src = measured_peaks()
+    slices = info["slices"]
+    pairs = slices * (slices + 1) // 2 if mode != 0 else 1
+    if mode == 0:
+        roof = {"bound": "tensor", "kernel": "leaf_f64_kernel (DMMA)", "achieved": None,
+                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "note": "FP64 peak not in MEASURED_PEAKS.json"}
+        achieved = 2.0 * info["leaf_madds"] / (ph[2] * 1e-3) / 1e12
+        roof["achieved"] = achieved
+    else:
+        leaf_flops = 2.0 * pairs * info["leaf_madds"]
+        achieved = leaf_flops / (ph[2] * 1e-3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        roof = {"bound": "tensor", "kernel": f"leaf_tc_kernel<{slices}> (tcgen05 BF16)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{src} bf16 dense sustained",
+                "work": f"{pairs} digit pairs x 2 x {info['leaf_madds']} tile multiply-adds"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": DTYPE_DESC[mode], "data": "synthetic",
+           "config": {"workload": f"A {m}x{n} {'FP32' if f32 else 'FP64'} U[-1,1) (seed {args.seed}), "
+                                  "lower triangle of C = A^T A",
+                      "mode": args.mode.upper(), "strassen_depth": info["depth"],
+                      "cutoff": info["cutoff"], "slices": slices,
+                      "l2": "inputs larger than L2 (A and C 512 MiB each)"},
+           "roofline": roof,
+           "phases_ms": {"colexp": ph[0], "prep": ph[1], "leaf": ph[2], "combine": ph[3]},
+           "gpu_launches": args.steps * (4 + (1 if info["products"] else 0)),
+           "clocks": clk}
+
+    if not args.no_extras:
+        # plain tiled AtA (Strassen depth 0) on the same GPU, same mode
+        hp = ata.Handle(cutoff=0, depth=0, slices=args.slices)
+        ms_plain = timed(lambda: hp.lower(A, C, mode, stream), args.steps, args.warmup)
+        out["plain_tiled"] = {"value": world * eff / (ms_plain * 1e-3) / 1e12, "ms_per_step": ms_plain,
+                              "speedup_of_value": ms_plain / ms}
+        hp.close()
+        # end to end through the public API with host buffers
+        A_pin = torch.from_numpy(A_host).pin_memory()
+        C_pin = torch.empty((n, n), dtype=tdt).pin_memory()
+
+        def e2e_step():
+            A.copy_(A_pin, non_blocking=True)
+            h.lower(A, C, mode, stream)
+            C_pin.copy_(C, non_blocking=True)
+        ms_e2e = timed(e2e_step, args.steps, args.warmup)
+        out["e2e"] = {"value": world * eff / (ms_e2e * 1e-3) / 1e12, "unit": UNIT,
+                      "h2d_bytes_per_step": A_host.nbytes, "d2h_bytes_per_step": C.numel() * C.element_size(),
+                      "ms_per_step": ms_e2e}
+        # accuracy of the timed configuration on sampled entries
+        import oracle
+        rng = np.random.default_rng(0)
+        j = rng.integers(0, n, 400)
+        k = (rng.random(400) * (j + 1)).astype(np.int64)
+        h.lower(A, C, mode, stream)
+        torch.cuda.synchronize(dev)
+        got = C[torch.from_numpy(j).to(dev), torch.from_numpy(k).to(dev)].double().cpu().numpy()
+        A64 = np.asarray(A_host, np.float64)
+        ref, den = oracle.dot_pairs(np.ascontiguousarray(A64[:, j].T), np.ascontiguousarray(A64[:, k].T))
+        out["error_vs_oracle"] = {"max_rel_to_absAtA": float(np.max(np.abs(got - ref) / den)),
+                                  "samples": 400}
+        if rank == 0 and world == 1:
+            v, dt, cores, desc = cpu_oracle_sample(
+                lambda nb: np.ascontiguousarray(A64[:, :nb]), m, n, 12.0)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": desc, "seconds": dt}
+    h.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,156 @@
+/*
+ * ata.h -- C ABI of the GB300 (sm_103a) lower-triangle Gram-product library.
+ *
+ * The library computes low(C) = low(A^T A) for a rectangular m x n matrix A,
+ * the AtA method of Arrigoni, Maggioli, Massini & Rodola, "Efficiently
+ * Parallelizable Strassen-Based Multiplication of a Matrix by its Transpose"
+ * (arXiv:2110.13042):
+ *   - Section 3.1, Eq. "submatA"/"Cij" and Algorithm 1: A is split 2 x 2;
+ *     C11 and C22 are AtA sub-problems, C21 = A12^T A11 + A22^T A21 is an
+ *     A^T B product done by Strassen's algorithm, and C12 = C21^T is never
+ *     formed (only the lower triangle of C is produced).
+ *   - Section 3.3: Strassen's workspace is allocated once up front
+ *     (FastStrassen); here the handle owns a device workspace that grows on
+ *     demand and is reused by every later call.
+ *   - Algorithm 3 / Section 4.1: the recursion is "simulated" up front into a
+ *     flat list of independent leaf tasks that write disjoint blocks of C; here
+ *     the leaves are GPU tiles executed by persistent kernels.
+ *
+ * All matrices are ROW-MAJOR.  A is m x n with leading dimension lda >= n
+ * (element (i, j) at A[i*lda + j]).  C is n x n with leading dimension
+ * ldc >= n.  All pointers passed to ata_lower / ata_batched are DEVICE
+ * pointers on the current CUDA device; the caller owns them.  A is read only
+ * and must not overlap C.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream); every call is asynchronous on it.
+ *
+ * Semantics: low(C) <- low(A^T A) (overwrite; alpha = 1, beta = 0).  Entries
+ * (j, k) with k <= j are written; the strict upper triangle of C is never
+ * read or written.  m == 0 writes zeros to low(C); n == 0 does nothing.
+ *
+ * Errors: every entry point returns an ata_status.  No exception crosses the
+ * ABI and no call aborts the process.  A device-side wait that exceeds its
+ * budget does not hang: the kernel records ATA_ERR_TIMEOUT in a status word
+ * that ata_sync() returns.
+ */
+#ifndef ATA_H
+#define ATA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ATA_OK = 0,
+    ATA_ERR_INVALID = 1,   /* bad dimension, leading dimension, pointer or overlap */
+    ATA_ERR_DTYPE = 2,     /* unknown or unsupported dtype                          */
+    ATA_ERR_ALLOC = 3,     /* device or host allocation failed                      */
+    ATA_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed           */
+    ATA_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out (see ata_sync)     */
+    ATA_ERR_UNSUPPORTED = 6/* no sm_103a device, or a size beyond a documented limit */
+} ata_status;
+
+/* Arithmetic modes.  The element type of A and C is double for the F64
+ * modes and float for the F32 modes. */
+typedef enum {
+    /* double in/out; FP64 tensor-core (DMMA) leaves, FP64 Strassen sums. */
+    ATA_F64 = 0,
+    /* double in/out; FP64-accurate emulation: every column is scaled by a
+     * power of two, converted to fixed point and split into `slices` BF16
+     * digits (7 bits, then 8 bits per digit); the digit products run on the
+     * tcgen05 tensor cores with FP32 accumulation that is exact by
+     * construction, and are summed exactly in 64-bit integers.  Strassen
+     * operand sums and result sums are exact integer arithmetic. */
+    ATA_F64_EMU = 1,
+    /* float in/out; the same engine with 3 digits (23 bits per column). */
+    ATA_F32 = 2,
+    /* float in/out; one BF16 digit (8 bits per column, power-of-two column
+     * scaling), FP32 tensor-core accumulation. Low precision. */
+    ATA_F32_BF16 = 4
+} ata_dtype;
+
+/* Planning parameters.  Zero (or -1 for strassen_depth) selects the
+ * automatic choice of the autotuner. */
+typedef struct {
+    int cutoff;          /* AtA recursion stops at panels of <= cutoff columns
+                            (Algorithm 1 base case); 0 = auto                     */
+    int strassen_depth;  /* Strassen levels on every off-diagonal block
+                            (0 = classical tiles, i.e. plain tiled AtA);
+                            -1 = auto                                              */
+    int slices;          /* digits per column for ATA_F64_EMU (3..7); 0 = auto    */
+    int reserved[5];     /* must be zero                                          */
+} ata_config;
+
+typedef struct ata_handle_s *ata_handle;
+
+/* Create a handle on the current CUDA device.  cfg may be NULL (all auto).
+ * The handle owns: the device workspace (Strassen operands and products,
+ * digit planes), the plan cache and the device status word.  Allocation is
+ * lazy (first call that needs it).  Returns ATA_ERR_UNSUPPORTED if the
+ * current device is not sm_103. */
+int ata_create(ata_handle *out, const ata_config *cfg);
+
+/* Replace the handle's planning parameters (same meaning as ata_create). */
+int ata_set_config(ata_handle h, const ata_config *cfg);
+
+/* low(C) <- low(A^T A) for one m x n matrix (see the header comment).
+ * dtype: one of ata_dtype.  Asynchronous on `stream`.  The first call for a
+ * new (m, n, dtype) may grow the workspace with cudaMalloc (synchronous);
+ * make it once before capturing the call in a CUDA graph. */
+int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda,
+              void *C, int64_t ldc, int dtype, void *stream);
+
+/* low(C_i) <- low(A_i^T A_i) for `count` independent problems in one
+ * persistent launch.  m, n, lda, ldc: HOST arrays of length count.  A, C:
+ * HOST arrays of `count` DEVICE pointers.  Only ATA_F32, ATA_F32_BF16 and
+ * ATA_F64_EMU are accepted; every problem is done as plain tiles (no
+ * Strassen).  The task table is uploaded from pinned host memory owned by the
+ * handle, so the same call is graph-capturable after a first uncaptured call
+ * with the same problem set. */
+int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n,
+                const void *const *A, const int64_t *lda, void *const *C,
+                const int64_t *ldc, int dtype, void *stream);
+
+/* Wait for `stream`, then return (and clear) the device status word:
+ * ATA_OK, or ATA_ERR_TIMEOUT if a device-side wait ran out since the last
+ * ata_sync, or ATA_ERR_CUDA if the stream reported an error. */
+int ata_sync(ata_handle h, void *stream);
+
+/* Release the handle and its workspace (synchronises the device first). */
+int ata_destroy(ata_handle h);
+
+/* Static English description of a status code. */
+const char *ata_status_string(int status);
+
+/* Host-only plan description, for tests and tuning.  Fills `out` (host array
+ * of ATA_PLAN_FIELDS int64) for the plan ata_lower would run for (m, n,
+ * dtype) under the handle's configuration, without touching the GPU:
+ *   [0] cutoff used            [1] Strassen depth used   [2] digits (slices)
+ *   [3] diagonal panels        [4] off-diagonal blocks   [5] Strassen products
+ *   [6] leaf tiles             [7] workspace bytes       [8] classical-equivalent
+ *                                                           multiply-adds done by
+ *                                                           the leaves (per digit
+ *                                                           pair)
+ *   [9] multiply-adds of plain tiled AtA on the same tile grid
+ * h may be NULL (default configuration). */
+#define ATA_PLAN_FIELDS 10
+int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out);
+
+/* Phase timing.  When enabled, ata_lower records CUDA events on its stream
+ * around each phase; ata_phase_times waits for the most recent call's events
+ * and writes 4 durations in milliseconds: [0] column exponents, [1] operand
+ * preparation (digit planes, Strassen operand sums), [2] leaf products (the
+ * tensor-core kernel), [3] Strassen result sums.  Returns ATA_ERR_INVALID if
+ * timing is off or no call has been timed since it was enabled. */
+int ata_set_timing(ata_handle h, int enable);
+int ata_phase_times(ata_handle h, double *out);
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int ata_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATA_H */

@@ -1,0 +1,154 @@
+"""ctypes binding of the C ABI in ``include/ata.h`` (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in
+``libata.so``; all arithmetic happens in the library's CUDA kernels.  Tensor
+arguments are accepted only to read their device pointer, shape and stride.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+ATA_F64, ATA_F64_EMU, ATA_F32, ATA_F32_BF16 = 0, 1, 2, 4
+STATUS = {0: "ATA_OK", 1: "ATA_ERR_INVALID", 2: "ATA_ERR_DTYPE", 3: "ATA_ERR_ALLOC",
+          4: "ATA_ERR_CUDA", 5: "ATA_ERR_TIMEOUT", 6: "ATA_ERR_UNSUPPORTED"}
+PLAN_FIELDS = ("cutoff", "depth", "slices", "panels", "blocks", "products", "tiles",
+               "workspace_bytes", "leaf_madds", "plain_madds")
+
+_lib = None
+
+
+class AtaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status_string(status)})")
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "_build", "libata.so")
+
+
+def load():
+    """Load libata.so (fails loudly if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c \"import __graft_entry__ as g; g.build()\"`")
+    L = ctypes.CDLL(path)
+    i64, vp, ip = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    L.ata_create.argtypes = [ctypes.POINTER(vp), vp]
+    L.ata_set_config.argtypes = [vp, vp]
+    L.ata_lower.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp]
+    L.ata_batched.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, ip, vp]
+    L.ata_sync.argtypes = [vp, vp]
+    L.ata_destroy.argtypes = [vp]
+    L.ata_status_string.argtypes = [ip]
+    L.ata_status_string.restype = ctypes.c_char_p
+    L.ata_plan_info.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64)]
+    L.ata_set_timing.argtypes = [vp, ip]
+    L.ata_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    for f in ("ata_create", "ata_set_config", "ata_lower", "ata_batched", "ata_sync",
+              "ata_destroy", "ata_plan_info", "ata_version", "ata_set_timing",
+              "ata_phase_times"):
+        getattr(L, f).restype = ip
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return load().ata_status_string(int(status)).decode()
+
+
+def version() -> int:
+    return int(load().ata_version())
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("cutoff", ctypes.c_int), ("strassen_depth", ctypes.c_int),
+                ("slices", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+def _config(cutoff=0, depth=-1, slices=0) -> Config:
+    return Config(int(cutoff), int(depth), int(slices), (ctypes.c_int * 5)())
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise AtaError(rc, what)
+
+
+def plan_info(m: int, n: int, dtype: int, handle: "Handle | None" = None) -> dict:
+    out = (ctypes.c_int64 * len(PLAN_FIELDS))()
+    _check(load().ata_plan_info(handle._h if handle else None, int(m), int(n), int(dtype), out),
+           "ata_plan_info")
+    return dict(zip(PLAN_FIELDS, (int(v) for v in out)))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Handle:
+    """Owns an ``ata_handle`` (workspace, plan cache, device status word)."""
+
+    def __init__(self, cutoff=0, depth=-1, slices=0):
+        L = load()
+        self._h = ctypes.c_void_p()
+        cfg = _config(cutoff, depth, slices)
+        _check(L.ata_create(ctypes.byref(self._h), ctypes.byref(cfg)), "ata_create")
+
+    def set_config(self, cutoff=0, depth=-1, slices=0):
+        cfg = _config(cutoff, depth, slices)
+        _check(load().ata_set_config(self._h, ctypes.byref(cfg)), "ata_set_config")
+
+    def lower_ptr(self, m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:
+        """Raw C-ABI call; returns the status code (no exception)."""
+        return int(load().ata_lower(self._h, int(m), int(n), A_ptr, int(lda), C_ptr, int(ldc),
+                                    int(dtype), _stream_ptr(stream)))
+
+    def lower(self, A, C, dtype, stream=None):
+        """low(C) <- low(A^T A) for row-major CUDA tensors A (m x n) and C (n x n)."""
+        m, n = A.shape
+        if A.stride(1) != 1 or C.stride(1) != 1:
+            raise ValueError("A and C must be row-major with unit column stride")
+        _check(self.lower_ptr(m, n, A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0), dtype,
+                              stream), "ata_lower")
+
+    def batched_ptr(self, ms, ns, A_ptrs, ldas, C_ptrs, ldcs, dtype, stream=None) -> int:
+        count = len(ms)
+        I64 = ctypes.c_int64 * count
+        VP = ctypes.c_void_p * count
+        return int(load().ata_batched(self._h, count, I64(*ms), I64(*ns), VP(*A_ptrs), I64(*ldas),
+                                      VP(*C_ptrs), I64(*ldcs), int(dtype), _stream_ptr(stream)))
+
+    def set_timing(self, enable: bool = True):
+        _check(load().ata_set_timing(self._h, 1 if enable else 0), "ata_set_timing")
+
+    def phase_times(self) -> list:
+        """[colmax, prep, leaf, combine] device milliseconds of the last call."""
+        out = (ctypes.c_double * 4)()
+        _check(load().ata_phase_times(self._h, out), "ata_phase_times")
+        return [float(v) for v in out]
+
+    def sync(self, stream=None) -> int:
+        return int(load().ata_sync(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if self._h:
+            load().ata_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,411 @@
+// C ABI (include/ata.h): handle, argument validation, plan cache, device
+// workspace, tensor maps and the launch sequence of one ata_lower call.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ata.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace ata;
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+using Key = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int, int>;
+
+struct CachedPlan {
+    Plan plan;
+    std::vector<uint8_t> tables;
+    uint8_t *pinned = nullptr;
+    uint64_t ws_generation = 0;
+    LeafParams lp;
+    ~CachedPlan() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+};
+
+bool is_f32_mode(int dtype) { return dtype == ATA_F32 || dtype == ATA_F32_BF16; }
+
+bool valid_dtype(int dtype) {
+    return dtype == ATA_F64 || dtype == ATA_F64_EMU || dtype == ATA_F32 || dtype == ATA_F32_BF16;
+}
+
+}  // namespace
+
+struct ata_handle_s {
+    int device = 0;
+    int num_sms = 0;
+    ata_config cfg{};
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    uint64_t ws_generation = 1;
+    int *d_status = nullptr;
+    const CachedPlan *resident = nullptr;  // whose tables are in the workspace
+    std::map<Key, std::unique_ptr<CachedPlan>> plans;
+    bool timing = false;
+    bool timed = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+int check_config(const ata_config *c) {
+    if (!c) return ATA_OK;
+    if (c->cutoff < 0 || c->strassen_depth < -1 || c->strassen_depth > 4 || c->slices < 0 ||
+        c->slices > MAX_SLICES)
+        return ATA_ERR_INVALID;
+    for (int r : c->reserved)
+        if (r != 0) return ATA_ERR_INVALID;
+    return ATA_OK;
+}
+
+PlanParams params_for(const ata_config &cfg, int64_t m, int64_t n, int64_t lda, int64_t ldc, int dtype) {
+    PlanParams pp;
+    pp.m = m;
+    pp.n = n;
+    pp.lda = lda;
+    pp.ldc = ldc;
+    pp.mode = dtype;
+    pp.cutoff = cfg.cutoff;
+    pp.depth = cfg.strassen_depth;
+    pp.slices = cfg.slices;
+    return pp;
+}
+
+int ensure_workspace(ata_handle h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return ATA_OK;
+    const char *inj = std::getenv("ATA_TEST_FAIL_ALLOC");
+    if (inj && inj[0] == '1') return ATA_ERR_ALLOC;
+    if (h->ws) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return ATA_ERR_CUDA;
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;  // headroom for nearby shapes
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        want = bytes;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return ATA_ERR_ALLOC;
+        }
+    }
+    if (cudaMemset(p, 0, want) != cudaSuccess) {
+        cudaFree(p);
+        return ATA_ERR_CUDA;
+    }
+    h->ws = static_cast<uint8_t *>(p);
+    h->ws_bytes = want;
+    h->ws_generation++;
+    h->resident = nullptr;
+    return ATA_OK;
+}
+
+// Tensor maps and raw family pointers for the current workspace.
+int bind_plan(ata_handle h, CachedPlan &cp) {
+    if (cp.ws_generation == h->ws_generation) return ATA_OK;
+    const Plan &P = cp.plan;
+    LeafParams &lp = cp.lp;
+    std::memset(&lp, 0, sizeof(lp));
+    if (P.uses_digits()) {
+        EncodeTiledFn enc = get_encode_fn();
+        if (!enc) return ATA_ERR_CUDA;
+        for (size_t f = 0; f < P.families.size(); ++f) {
+            const Family &F = P.families[f];
+            if (F.cols == 0) continue;
+            cuuint64_t dims[3] = {static_cast<cuuint64_t>(F.K_pitch), static_cast<cuuint64_t>(F.cols),
+                                  static_cast<cuuint64_t>(P.slices)};
+            cuuint64_t strides[2] = {static_cast<cuuint64_t>(F.K_pitch * 2),
+                                     static_cast<cuuint64_t>(F.plane_elems * 2)};
+            cuuint32_t box[3] = {static_cast<cuuint32_t>(KSTEP), static_cast<cuuint32_t>(TILE),
+                                 static_cast<cuuint32_t>(P.slices)};
+            cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = enc(&lp.maps[f], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h->ws + F.offset, dims,
+                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return ATA_ERR_CUDA;
+        }
+    } else {
+        for (size_t f = 0; f < P.families.size(); ++f) {
+            lp.fam64[f] = reinterpret_cast<const double *>(h->ws + P.families[f].offset);
+            lp.fam_ld[f] = P.families[f].cols;
+        }
+    }
+    cp.ws_generation = h->ws_generation;
+    if (h->resident == &cp) h->resident = nullptr;
+    return ATA_OK;
+}
+
+CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
+    Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices};
+    auto it = h->plans.find(key);
+    if (it != h->plans.end()) return it->second.get();
+    std::unique_ptr<CachedPlan> cp(new CachedPlan());
+    std::string err;
+    if (!make_plan(pp, &cp->plan, &err)) {
+        *status = ATA_ERR_INVALID;
+        return nullptr;
+    }
+    if (cp->plan.families.size() > static_cast<size_t>(MAX_FAMILIES)) {
+        *status = ATA_ERR_UNSUPPORTED;
+        return nullptr;
+    }
+    pack_tables(cp->plan, &cp->tables);
+    if (!cp->tables.empty()) {
+        if (cudaMallocHost(reinterpret_cast<void **>(&cp->pinned), cp->tables.size()) != cudaSuccess) {
+            cudaGetLastError();
+            *status = ATA_ERR_ALLOC;
+            return nullptr;
+        }
+        std::memcpy(cp->pinned, cp->tables.data(), cp->tables.size());
+    }
+    if (h->plans.size() > 64) h->plans.clear(), h->resident = nullptr;
+    CachedPlan *raw = cp.get();
+    h->plans[key] = std::move(cp);
+    return raw;
+}
+
+bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bbytes && y < x + abytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ata_version(void) { return 100; }
+
+const char *ata_status_string(int status) {
+    switch (status) {
+        case ATA_OK: return "ok";
+        case ATA_ERR_INVALID: return "invalid argument (dimension, leading dimension, pointer, overlap or non-finite input)";
+        case ATA_ERR_DTYPE: return "unknown or unsupported dtype";
+        case ATA_ERR_ALLOC: return "allocation failed";
+        case ATA_ERR_CUDA: return "CUDA runtime or launch error";
+        case ATA_ERR_TIMEOUT: return "a device-side wait exceeded its time budget";
+        case ATA_ERR_UNSUPPORTED: return "unsupported device or size";
+        default: return "unknown status";
+    }
+}
+
+int ata_create(ata_handle *out, const ata_config *cfg) {
+    if (!out) return ATA_ERR_INVALID;
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc != ATA_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ATA_ERR_UNSUPPORTED;
+    }
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ATA_ERR_UNSUPPORTED;
+    }
+    if (major != 10 || minor != 3) return ATA_ERR_UNSUPPORTED;
+    ata_handle h = new (std::nothrow) ata_handle_s();
+    if (!h) return ATA_ERR_ALLOC;
+    h->device = dev;
+    h->num_sms = sms;
+    if (cfg) h->cfg = *cfg;
+    else {
+        std::memset(&h->cfg, 0, sizeof(h->cfg));
+        h->cfg.strassen_depth = -1;
+    }
+    if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return ATA_ERR_ALLOC;
+    }
+    *out = h;
+    return ATA_OK;
+}
+
+int ata_set_config(ata_handle h, const ata_config *cfg) {
+    if (!h) return ATA_ERR_INVALID;
+    int rc = check_config(cfg);
+    if (rc != ATA_OK) return rc;
+    if (cfg) h->cfg = *cfg;
+    else {
+        std::memset(&h->cfg, 0, sizeof(h->cfg));
+        h->cfg.strassen_depth = -1;
+    }
+    return ATA_OK;
+}
+
+int ata_destroy(ata_handle h) {
+    if (!h) return ATA_ERR_INVALID;
+    cudaDeviceSynchronize();
+    h->plans.clear();
+    for (cudaEvent_t &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->ws) cudaFree(h->ws);
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return ATA_OK;
+}
+
+int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
+    if (!out) return ATA_ERR_INVALID;
+    if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
+    ata_config cfg{};
+    cfg.strassen_depth = -1;
+    if (h) cfg = h->cfg;
+    Plan P;
+    std::string err;
+    if (!make_plan(params_for(cfg, m, n, n > 0 ? n : 1, n > 0 ? n : 1, dtype), &P, &err))
+        return ATA_ERR_INVALID;
+    out[0] = P.cutoff;
+    out[1] = P.depth;
+    out[2] = P.slices;
+    out[3] = P.n_panels;
+    out[4] = P.n_blocks;
+    out[5] = P.n_products;
+    out[6] = static_cast<int64_t>(P.tasks.size());
+    out[7] = P.workspace_bytes;
+    out[8] = static_cast<int64_t>(P.leaf_madds);
+    out[9] = static_cast<int64_t>(P.plain_madds);
+    return ATA_OK;
+}
+
+int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
+              int dtype, void *stream) {
+    if (!h) return ATA_ERR_INVALID;
+    if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
+    if (m < 0 || n < 0) return ATA_ERR_INVALID;
+    if (n == 0) return ATA_OK;
+    if (ldc < n || !C) return ATA_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool f32 = is_f32_mode(dtype);
+    const size_t es = f32 ? 4 : 8;
+    if (m == 0) return launch_zero_lower(C, n, ldc, f32, s) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
+    if (lda < n || !A) return ATA_ERR_INVALID;
+    if (ranges_overlap(A, ((m - 1) * lda + n) * es, C, ((n - 1) * ldc + n) * es)) return ATA_ERR_INVALID;
+
+    int status = ATA_OK;
+    CachedPlan *cp = get_plan(h, params_for(h->cfg, m, n, lda, ldc, dtype), &status);
+    if (!cp) return status;
+    const Plan &P = cp->plan;
+    int rc = ensure_workspace(h, static_cast<size_t>(P.workspace_bytes));
+    if (rc != ATA_OK) return rc;
+    rc = bind_plan(h, *cp);
+    if (rc != ATA_OK) return rc;
+    if (h->resident != cp && P.table_bytes > 0) {
+        if (cudaMemcpyAsync(h->ws + P.off_tables, cp->pinned, P.table_bytes, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return ATA_ERR_CUDA;
+        h->resident = cp;
+    }
+    uint8_t *ws = h->ws;
+    const uint8_t *tables = ws + P.off_tables;
+    unsigned long long *colmax = reinterpret_cast<unsigned long long *>(ws + P.off_colmax);
+    int *expo = reinterpret_cast<int *>(ws + P.off_expo);
+    const bool need_expo = P.uses_digits() || !P.ops.empty();
+
+    auto mark = [&](int i) {
+        if (h->timing) cudaEventRecord(h->ev[i], s);
+    };
+    mark(0);
+    if (need_expo && launch_colmax(A, m, n, lda, f32, colmax, expo, h->d_status, s) != cudaSuccess)
+        return ATA_ERR_CUDA;
+    mark(1);
+    if (launch_prep(P, A, f32, expo, tables, ws, s) != cudaSuccess) return ATA_ERR_CUDA;
+    mark(2);
+
+    LeafParams &lp = cp->lp;
+    lp.tasks = reinterpret_cast<const LeafTask *>(tables + P.t_tasks);
+    lp.ntasks = static_cast<int>(P.tasks.size());
+    lp.C = C;
+    lp.M = ws + P.off_products;
+    lp.expo = expo;
+    lp.status = h->d_status;
+    lp.A64 = static_cast<const double *>(A);
+    lp.lda = lda;
+    cudaError_t e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
+    if (e != cudaSuccess) return ATA_ERR_CUDA;
+    mark(3);
+    if (launch_combine(P, tables, ws + P.off_products, C, expo, s) != cudaSuccess) return ATA_ERR_CUDA;
+    mark(4);
+    if (h->timing) h->timed = true;
+    return ATA_OK;
+}
+
+int ata_set_timing(ata_handle h, int enable) {
+    if (!h) return ATA_ERR_INVALID;
+    if (enable && !h->ev[0]) {
+        for (cudaEvent_t &e : h->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return ATA_ERR_CUDA;
+    }
+    h->timing = enable != 0;
+    h->timed = false;
+    return ATA_OK;
+}
+
+int ata_phase_times(ata_handle h, double *out) {
+    if (!h || !out || !h->timing || !h->timed) return ATA_ERR_INVALID;
+    if (cudaEventSynchronize(h->ev[4]) != cudaSuccess) return ATA_ERR_CUDA;
+    for (int i = 0; i < 4; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) return ATA_ERR_CUDA;
+        out[i] = ms;
+    }
+    return ATA_OK;
+}
+
+int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, const void *const *A,
+                const int64_t *lda, void *const *C, const int64_t *ldc, int dtype, void *stream) {
+    if (!h || count < 0) return ATA_ERR_INVALID;
+    if (count == 0) return ATA_OK;
+    if (!m || !n || !A || !lda || !C || !ldc) return ATA_ERR_INVALID;
+    if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
+    (void)stream;
+    return ATA_ERR_UNSUPPORTED;
+}
+
+int ata_sync(ata_handle h, void *stream) {
+    if (!h) return ATA_ERR_INVALID;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return ATA_ERR_CUDA;
+    }
+    int st = 0;
+    if (cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ATA_ERR_CUDA;
+    if (st != 0 && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return ATA_ERR_CUDA;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,525 @@
+// Auxiliary device kernels: column exponents (equilibration), operand
+// preparation (exact fixed-point Strassen operand sums + digit slicing),
+// Strassen result sums (exact int64 combine), the native-FP64 DMMA leaf, and
+// the m == 0 zero fill.
+//
+// GB300 note: FP64 arithmetic runs at a small fraction of the integer and
+// FP32 rates on this part, so every exact step here (scaling, operand sums,
+// digit extraction, result sums) is done in 64-bit INTEGER arithmetic on a
+// fixed-point representation; FP64 is used only to form the final values.
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "kernels.h"
+#include "ptx.cuh"
+
+namespace ata {
+namespace {
+
+constexpr int STATUS_NONFINITE = 1;  // == ATA_ERR_INVALID
+
+// 2^x as a double (exact for -1074 <= x <= 1023).
+__device__ __forceinline__ double exp2i(int x) {
+    if (x >= -1022 && x <= 1023) return __longlong_as_double(static_cast<long long>(x + 1023) << 52);
+    return scalbn(1.0, x);
+}
+
+__device__ __forceinline__ float exp2f_i(int x) {
+    if (x >= -126 && x <= 127) return __uint_as_float(static_cast<unsigned>(x + 127) << 23);
+    return scalbnf(1.0f, x);
+}
+
+// round(a * 2^sh) as int64 (round half away from zero), computed from the
+// bits of a with integer operations only.  Requires |a * 2^sh| < 2^62.
+__device__ __forceinline__ int64_t fixed_of(double a, int sh) {
+    const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(a));
+    const int eb = static_cast<int>((bits >> 52) & 0x7FF);
+    const uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+    const uint64_t M = eb ? (mant | (1ull << 52)) : mant;
+    const int s = (eb ? eb - 1075 : -1074) + sh;  // value = M * 2^s
+    uint64_t r;
+    if (s >= 0)
+        r = M << s;
+    else if (s < -62)
+        r = 0;
+    else
+        r = (M + (1ull << (-s - 1))) >> (-s);
+    return (bits >> 63) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+}
+
+__device__ __forceinline__ int64_t fixed_of(float a, int sh) {
+    const uint32_t bits = __float_as_uint(a);
+    const int eb = static_cast<int>((bits >> 23) & 0xFF);
+    const uint64_t mant = bits & 0x7FFFFFu;
+    const uint64_t M = eb ? (mant | 0x800000u) : mant;
+    const int s = (eb ? eb - 150 : -149) + sh;
+    uint64_t r;
+    if (s >= 0)
+        r = M << s;
+    else if (s < -62)
+        r = 0;
+    else
+        r = (M + (1ull << (-s - 1))) >> (-s);
+    return (bits >> 31) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double a) {
+    return static_cast<unsigned long long>(__double_as_longlong(a)) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float a) {
+    return __float_as_uint(a) & 0x7FFFFFFFu;
+}
+
+// ------------------------------------------------------------ exponents --
+// colmax[j] = bits of max_i |a_ij| (order-preserving for non-negative IEEE).
+template <typename T>
+__global__ void __launch_bounds__(256) colmax_kernel(const T *__restrict__ A, int64_t m, int64_t n,
+                                                     int64_t lda, int rows_per_block,
+                                                     unsigned long long *colmax) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x;
+    if (j >= n) return;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.y) * rows_per_block;
+    const int64_t i1 = i0 + rows_per_block < m ? i0 + rows_per_block : m;
+    unsigned long long mx = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+        unsigned long long b = abs_bits(A[i * lda + j]);
+        mx = b > mx ? b : mx;
+    }
+    if (mx) atomicMax(colmax + j, mx);
+}
+
+// e_j = smallest integer with max_i |a_ij| < 2^e_j (0 for a zero column).
+template <typename T>
+__global__ void expo_kernel(const unsigned long long *colmax, int64_t n, int *expo, int *status) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const unsigned long long b = colmax[j];
+    int e = 0;
+    if (sizeof(T) == 8) {
+        const int eb = static_cast<int>(b >> 52);
+        if (eb == 0x7FF) atomicExch(status, STATUS_NONFINITE);
+        if (b == 0)
+            e = 0;
+        else if (eb == 0)
+            e = (64 - __clzll(static_cast<long long>(b & 0xFFFFFFFFFFFFFull))) - 1074;
+        else
+            e = eb - 1022;
+    } else {
+        const unsigned bb = static_cast<unsigned>(b);
+        const int eb = static_cast<int>(bb >> 23);
+        if (eb == 0xFF) atomicExch(status, STATUS_NONFINITE);
+        if (bb == 0)
+            e = 0;
+        else if (eb == 0)
+            e = (32 - __clz(static_cast<int>(bb & 0x7FFFFFu))) - 149;
+        else
+            e = eb - 126;
+    }
+    expo[j] = e;
+}
+
+// -------------------------------------------------------- operand prep --
+struct Families {
+    Family f[MAX_FAMILIES];
+};
+
+__device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t tile) {
+    int lo = 0, hi = nops - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ops[mid].tile_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Digit planes.  For operand o and its 64 x 64 tile (k0, c0):
+//   V[k][c] = sum_t coef_t * round(a(row0_t + k, col0_t + c) * 2^(F - t - e))
+// with F = 7 + 8 (S - 1) fraction bits, exact in int64.  V is then written as
+// S balanced digits x_1 (|x_1| <= 128) and x_q in [-128, 127] (q >= 2) with
+// V = sum_q x_q 2^(8 (S - q)); digit q is stored as the BF16 value
+// x_q * 2^(-8 (q - 1)) (exact), K-major: plane q, column c, contraction k.
+template <int S, typename T>
+__global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
+                                                          const int *__restrict__ expo,
+                                                          const OpDesc *__restrict__ ops, int nops,
+                                                          const OpTerm *__restrict__ terms,
+                                                          Families fams, uint8_t *ws) {
+    __shared__ int64_t sV[PREP_K][PREP_C + 1];
+    const int64_t tile = blockIdx.x;
+    const OpDesc od = ops[find_desc(ops, nops, tile)];
+    const int64_t local = tile - od.tile_base;
+    const int tiles_k = od.K_pitch / PREP_K;
+    const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
+    const int c0 = static_cast<int>(local / tiles_k) * PREP_C;
+    constexpr int F = 7 + 8 * (S - 1);
+
+    const int cc = threadIdx.x & 63;
+    const int kr0 = threadIdx.x >> 6;
+    int64_t V[16];
+#pragma unroll
+    for (int it = 0; it < 16; ++it) V[it] = 0;
+    for (int t = 0; t < od.nterms; ++t) {
+        const OpTerm tm = terms[od.first_term + t];
+        const int c = c0 + cc;
+        if (c < tm.cols) {
+            const int sh = F - od.t_shift - expo[tm.col0 + c];
+            const T *col = A + tm.col0 + c;
+#pragma unroll
+            for (int it = 0; it < 16; ++it) {
+                const int k = k0 + kr0 + 4 * it;
+                if (k < tm.rows) {
+                    const int64_t v = fixed_of(col[(tm.row0 + k) * lda], sh);
+                    V[it] += tm.coef > 0 ? v : -v;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < 16; ++it) sV[kr0 + 4 * it][cc] = V[it];
+    __syncthreads();
+
+    const Family fam = fams.f[od.family];
+    __nv_bfloat162 *planes = reinterpret_cast<__nv_bfloat162 *>(ws + fam.offset);
+    const int kp = threadIdx.x & 31;
+    for (int c = threadIdx.x >> 5; c < PREP_C; c += 8) {
+        int64_t v0 = sV[2 * kp][c], v1 = sV[2 * kp + 1][c];
+        int x0[S], x1[S];
+#pragma unroll
+        for (int q = S - 1; q >= 1; --q) {
+            const int d0 = static_cast<int>((v0 + 128) & 255) - 128;
+            const int d1 = static_cast<int>((v1 + 128) & 255) - 128;
+            x0[q] = d0;
+            x1[q] = d1;
+            v0 = (v0 - d0) >> 8;
+            v1 = (v1 - d1) >> 8;
+        }
+        x0[0] = static_cast<int>(v0);
+        x1[0] = static_cast<int>(v1);
+        const int64_t colg = od.out_col + c0 + c;
+        const int64_t e0 = colg * fam.K_pitch + k0 + 2 * kp;  // even
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            const float sc = exp2f_i(-8 * q);
+            __nv_bfloat162 val;
+            val.x = __float2bfloat16_rn(static_cast<float>(x0[q]) * sc);
+            val.y = __float2bfloat16_rn(static_cast<float>(x1[q]) * sc);
+            planes[(q * fam.plane_elems + e0) >> 1] = val;
+        }
+    }
+}
+
+// Native FP64 operands: U[k][c] = sum_t coef_t * a * 2^-e  (FP64, row-major
+// [k][col] with leading dimension fam.cols).
+template <typename T>
+__global__ void __launch_bounds__(256) prep_f64_kernel(const T *__restrict__ A, int64_t lda,
+                                                       const int *__restrict__ expo,
+                                                       const OpDesc *__restrict__ ops, int nops,
+                                                       const OpTerm *__restrict__ terms,
+                                                       Families fams, uint8_t *ws) {
+    const int64_t tile = blockIdx.x;
+    const OpDesc od = ops[find_desc(ops, nops, tile)];
+    const int64_t local = tile - od.tile_base;
+    const int tiles_k = od.K_pitch / PREP_K;
+    const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
+    const int c0 = static_cast<int>(local / tiles_k) * PREP_C;
+    const int cc = threadIdx.x & 63;
+    const int kr0 = threadIdx.x >> 6;
+    double V[16];
+#pragma unroll
+    for (int it = 0; it < 16; ++it) V[it] = 0.0;
+    for (int t = 0; t < od.nterms; ++t) {
+        const OpTerm tm = terms[od.first_term + t];
+        const int c = c0 + cc;
+        if (c < tm.cols) {
+            const double sc = exp2i(-expo[tm.col0 + c]);
+            const T *col = A + tm.col0 + c;
+#pragma unroll
+            for (int it = 0; it < 16; ++it) {
+                const int k = k0 + kr0 + 4 * it;
+                if (k < tm.rows) {
+                    const double v = static_cast<double>(col[(tm.row0 + k) * lda]) * sc;
+                    V[it] = tm.coef > 0 ? V[it] + v : V[it] - v;
+                }
+            }
+        }
+    }
+    const Family fam = fams.f[od.family];
+    double *out = reinterpret_cast<double *>(ws + fam.offset);
+#pragma unroll
+    for (int it = 0; it < 16; ++it)
+        out[(k0 + kr0 + 4 * it) * fam.cols + od.out_col + c0 + cc] = V[it];
+}
+
+// ------------------------------------------------------------- combine --
+__device__ __forceinline__ int find_comb(const CombDesc *d, int nd, int64_t tile) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].tile_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int MAX_CTERMS = 256;
+
+// Exact Strassen result sums: region = sum_r coef_r * T_r * 2^(shift_r),
+// added in int64 after aligning every product to the finest unit, then one
+// rounding to the output type and the column-scale 2^(e_j + e_k).
+template <typename TOut>
+__global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__restrict__ descs, int nd,
+                                                          const CombTerm *__restrict__ cterms,
+                                                          const int64_t *__restrict__ M, TOut *C,
+                                                          int64_t ldc, const int *__restrict__ expo) {
+    __shared__ CombTerm st[MAX_CTERMS];
+    __shared__ int s_min;
+    const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
+    const int nt = d.nterms < MAX_CTERMS ? d.nterms : MAX_CTERMS;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) st[t] = cterms[d.first_term + t];
+    if (threadIdx.x == 0) s_min = 1 << 20;
+    __syncthreads();
+    if (threadIdx.x < nt) atomicMin(&s_min, st[threadIdx.x].shift);
+    __syncthreads();
+    const int smin = s_min;
+    const int64_t local = blockIdx.x - d.tile_base;
+    const int tcols = (d.cols + 31) / 32;
+    const int r0 = static_cast<int>(local / tcols) * 32;
+    const int col = static_cast<int>(local % tcols) * 32 + (threadIdx.x & 31);
+    if (col >= d.cols) return;
+    const int ec = expo[d.e_col0 + col];
+    for (int rr = threadIdx.x >> 5; rr < 32; rr += 8) {
+        const int row = r0 + rr;
+        if (row >= d.rows) break;
+        int64_t sum = 0;
+        for (int t = 0; t < nt; ++t) {
+            const CombTerm ct = st[t];
+            int64_t v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
+            v = v * (int64_t(1) << (ct.shift - smin));
+            sum += ct.coef > 0 ? v : -v;
+        }
+        const int x = -38 + smin + expo[d.e_row0 + row] + ec;
+        if (sizeof(TOut) == 8)
+            C[d.c_off + static_cast<int64_t>(row) * ldc + col] =
+                static_cast<TOut>(static_cast<double>(sum) * exp2i(x));
+        else
+            C[d.c_off + static_cast<int64_t>(row) * ldc + col] =
+                static_cast<TOut>(__ll2float_rn(sum) * exp2f_i(x));
+    }
+}
+
+// Native FP64 result sums (fixed term order), then the column scales.
+__global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__restrict__ descs, int nd,
+                                                          const CombTerm *__restrict__ cterms,
+                                                          const double *__restrict__ M, double *C,
+                                                          int64_t ldc, const int *__restrict__ expo) {
+    __shared__ CombTerm st[MAX_CTERMS];
+    const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
+    const int nt = d.nterms < MAX_CTERMS ? d.nterms : MAX_CTERMS;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) st[t] = cterms[d.first_term + t];
+    __syncthreads();
+    const int64_t local = blockIdx.x - d.tile_base;
+    const int tcols = (d.cols + 31) / 32;
+    const int r0 = static_cast<int>(local / tcols) * 32;
+    const int col = static_cast<int>(local % tcols) * 32 + (threadIdx.x & 31);
+    if (col >= d.cols) return;
+    const int ec = expo[d.e_col0 + col];
+    for (int rr = threadIdx.x >> 5; rr < 32; rr += 8) {
+        const int row = r0 + rr;
+        if (row >= d.rows) break;
+        double sum = 0.0;
+        for (int t = 0; t < nt; ++t) {
+            const CombTerm ct = st[t];
+            const double v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
+            sum = ct.coef > 0 ? sum + v : sum - v;
+        }
+        C[d.c_off + static_cast<int64_t>(row) * ldc + col] = sum * exp2i(expo[d.e_row0 + row] + ec);
+    }
+}
+
+// ---------------------------------------------------- native FP64 leaf --
+// One 128 x 128 tile per block with FP64 tensor-core MMA (m8n8k4).
+__device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(c[0]), "+d"(c[1])
+                 : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ LeafParams p) {
+    constexpr int KT = 16, LDS = TILE + 4;
+    __shared__ double Us[KT][LDS];
+    __shared__ double Vs[KT][LDS];
+    const LeafTask t = p.tasks[blockIdx.x];
+    const double *U = t.fam_u < 0 ? p.A64 : p.fam64[t.fam_u];
+    const double *V = t.fam_v < 0 ? p.A64 : p.fam64[t.fam_v];
+    const int64_t ldu = t.fam_u < 0 ? p.lda : p.fam_ld[t.fam_u];
+    const int64_t ldv = t.fam_v < 0 ? p.lda : p.fam_ld[t.fam_v];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 64;
+    double acc[4][8][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+    const int lc = threadIdx.x & 127, lk = threadIdx.x >> 7;
+    for (int k0 = 0; k0 < t.klen; k0 += KT) {
+#pragma unroll
+        for (int i = 0; i < KT / 2; ++i) {
+            const int kk = lk + 2 * i;
+            const int64_t k = static_cast<int64_t>(t.k0) + k0 + kk;
+            const bool kin = (k0 + kk) < t.klen;
+            Us[kk][lc] = (kin && lc < t.rows) ? U[k * ldu + t.col_u + lc] : 0.0;
+            Vs[kk][lc] = (kin && lc < t.cols) ? V[k * ldv + t.col_v + lc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k4 = 0; k4 < KT; k4 += 4) {
+            double a[4], b[8];
+#pragma unroll
+            for (int fm = 0; fm < 4; ++fm) a[fm] = Us[k4 + (lane & 3)][wm + 8 * fm + (lane >> 2)];
+#pragma unroll
+            for (int fn = 0; fn < 8; ++fn) b[fn] = Vs[k4 + (lane & 3)][wn + 8 * fn + (lane >> 2)];
+#pragma unroll
+            for (int fm = 0; fm < 4; ++fm)
+#pragma unroll
+                for (int fn = 0; fn < 8; ++fn) dmma_8x8x4(acc[fm][fn], a[fm], b[fn]);
+        }
+        __syncthreads();
+    }
+    double *out = reinterpret_cast<double *>(t.kind == OUT_M_F64 ? p.M : p.C) + t.out_off;
+#pragma unroll
+    for (int fm = 0; fm < 4; ++fm) {
+        const int row = wm + 8 * fm + (lane >> 2);
+#pragma unroll
+        for (int fn = 0; fn < 8; ++fn) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = wn + 8 * fn + 2 * (lane & 3) + h;
+                if (row < t.rows && col < t.cols && (!t.diag || col <= row))
+                    out[static_cast<int64_t>(row) * t.out_ld + col] = acc[fm][fn][h];
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void zero_lower_kernel(T *C, int64_t n, int64_t ldc) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t j = blockIdx.y + static_cast<int64_t>(blockIdx.z) * 65535;
+    if (j < n && k <= j) C[j * ldc + k] = T(0);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+cudaError_t launch_colmax(const void *A, int64_t m, int64_t n, int64_t lda, bool is_f32,
+                          unsigned long long *colmax, int *expo, int *status, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * n, s);
+    if (e != cudaSuccess) return e;
+    const int rows_per_block = 64;
+    const int64_t gy = (m + rows_per_block - 1) / rows_per_block;
+    int rpb = rows_per_block;
+    int64_t gyy = gy;
+    while (gyy > 65535) {  // keep grid.y legal
+        rpb *= 2;
+        gyy = (m + rpb - 1) / rpb;
+    }
+    dim3 grid(static_cast<unsigned>((n + 255) / 256), static_cast<unsigned>(gyy > 0 ? gyy : 1));
+    if (is_f32)
+        colmax_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(A), m, n, lda, rpb, colmax);
+    else
+        colmax_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(A), m, n, lda, rpb, colmax);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned g = static_cast<unsigned>((n + 255) / 256);
+    if (is_f32)
+        expo_kernel<float><<<g, 256, 0, s>>>(colmax, n, expo, status);
+    else
+        expo_kernel<double><<<g, 256, 0, s>>>(colmax, n, expo, status);
+    return cudaGetLastError();
+}
+
+template <int S>
+static void prep_digits_dispatch(const Plan &P, const void *A, bool is_f32, const int *expo,
+                                 const uint8_t *tables, uint8_t *ws, const Families &F,
+                                 cudaStream_t s) {
+    const OpDesc *ops = reinterpret_cast<const OpDesc *>(tables + P.t_ops);
+    const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
+    const unsigned g = static_cast<unsigned>(P.prep_tiles);
+    if (is_f32)
+        prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo,
+                                                        ops, static_cast<int>(P.ops.size()), terms, F, ws);
+    else
+        prep_digits_kernel<S, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, expo,
+                                                         ops, static_cast<int>(P.ops.size()), terms, F, ws);
+}
+
+cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *expo,
+                        const uint8_t *tables, uint8_t *ws, cudaStream_t s) {
+    if (P.ops.empty() || P.prep_tiles == 0) return cudaSuccess;
+    if (P.prep_tiles > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+    Families F{};
+    for (size_t i = 0; i < P.families.size() && i < MAX_FAMILIES; ++i) F.f[i] = P.families[i];
+    if (P.p.mode == MODE_F64) {
+        const OpDesc *ops = reinterpret_cast<const OpDesc *>(tables + P.t_ops);
+        const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
+        prep_f64_kernel<double><<<static_cast<unsigned>(P.prep_tiles), 256, 0, s>>>(
+            static_cast<const double *>(A), P.p.lda, expo, ops, static_cast<int>(P.ops.size()), terms,
+            F, ws);
+        return cudaGetLastError();
+    }
+    switch (P.slices) {
+        case 1: prep_digits_dispatch<1>(P, A, is_f32, expo, tables, ws, F, s); break;
+        case 2: prep_digits_dispatch<2>(P, A, is_f32, expo, tables, ws, F, s); break;
+        case 3: prep_digits_dispatch<3>(P, A, is_f32, expo, tables, ws, F, s); break;
+        case 4: prep_digits_dispatch<4>(P, A, is_f32, expo, tables, ws, F, s); break;
+        case 5: prep_digits_dispatch<5>(P, A, is_f32, expo, tables, ws, F, s); break;
+        case 6: prep_digits_dispatch<6>(P, A, is_f32, expo, tables, ws, F, s); break;
+        case 7: prep_digits_dispatch<7>(P, A, is_f32, expo, tables, ws, F, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s) {
+    if (P.tasks.empty()) return cudaSuccess;
+    leaf_f64_kernel<<<static_cast<unsigned>(P.tasks.size()), 256, 0, s>>>(lp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
+                           const int *expo, cudaStream_t s) {
+    if (P.combs.empty() || P.comb_tiles == 0) return cudaSuccess;
+    const CombDesc *d = reinterpret_cast<const CombDesc *>(tables + P.t_combs);
+    const CombTerm *t = reinterpret_cast<const CombTerm *>(tables + P.t_cterms);
+    const unsigned g = static_cast<unsigned>(P.comb_tiles);
+    const int nd = static_cast<int>(P.combs.size());
+    if (P.p.mode == MODE_F64)
+        combine_f64_kernel<<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
+                                              static_cast<double *>(C), P.p.ldc, expo);
+    else if (P.p.mode == MODE_F64_EMU)
+        combine_i64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
+                                                      static_cast<double *>(C), P.p.ldc, expo);
+    else
+        combine_i64_kernel<float><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
+                                                     static_cast<float *>(C), P.p.ldc, expo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_lower(void *C, int64_t n, int64_t ldc, bool is_f32, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    dim3 grid(static_cast<unsigned>((n + 255) / 256), static_cast<unsigned>(n < 65535 ? n : 65535),
+              static_cast<unsigned>((n + 65534) / 65535));
+    if (is_f32)
+        zero_lower_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(C), n, ldc);
+    else
+        zero_lower_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(C), n, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace ata

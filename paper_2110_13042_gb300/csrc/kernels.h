@@ -1,0 +1,41 @@
+// Launch wrappers for the device kernels (host side).  All launches are
+// asynchronous on `stream` and return the launch's cudaError_t.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace ata {
+
+// Parameters shared by the leaf launches.
+struct LeafParams {
+    CUtensorMap maps[MAX_FAMILIES];  // one tiled map per digit family
+    const LeafTask *tasks;
+    int ntasks;
+    int pad0;
+    void *C;            // output matrix (double or float)
+    void *M;            // product workspace (int64 or double)
+    const int *expo;    // column exponents of A
+    int *status;        // device status word
+    const double *A64;  // native FP64: A itself
+    int64_t lda;
+    const double *fam64[MAX_FAMILIES];  // native FP64: family arrays
+    int64_t fam_ld[MAX_FAMILIES];
+};
+
+// Column exponents e_j (smallest e with max_i |a_ij| < 2^e); flags a
+// non-finite column in *status.
+cudaError_t launch_colmax(const void *A, int64_t m, int64_t n, int64_t lda, bool is_f32,
+                          unsigned long long *colmax, int *expo, int *status, cudaStream_t s);
+cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *expo,
+                        const uint8_t *tables, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s);
+cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s);
+cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
+                           const int *expo, cudaStream_t s);
+cudaError_t launch_zero_lower(void *C, int64_t n, int64_t ldc, bool is_f32, cudaStream_t s);
+// Shared-memory bytes the tcgen05 leaf kernel needs for `slices` digits.
+int leaf_tc_smem_bytes(int slices);
+
+}  // namespace ata

@@ -1,0 +1,400 @@
+// Host planner (see plan.h).
+//
+// The AtA recursion of Algorithm 1 (Section 3.1) is applied to column panels
+// with the full contraction height m: splitting n floor-first into n1, n2,
+//   C11 = A[:, :n1]^T A[:, :n1]        (AtA on the left panel)
+//   C22 = A[:, n1:]^T A[:, n1:]        (AtA on the right panel)
+//   C21 = A[:, n1:]^T A[:, :n1]        (one A^T B product)
+// which equals Eq. "Cij" with its two A^T A calls per diagonal block and two
+// Strassen calls for C21 merged along the contraction (A11^T A11 + A21^T A21
+// is the panel product A[:, :n1]^T A[:, :n1]).  Panels of at most `cutoff`
+// columns are leaves (the '?syrk' base case).  Every C21 block is computed by
+// `depth` levels of Strassen's algorithm in its A^T B form, splitting every
+// dimension ceil-first and treating the smaller block as zero-padded
+// (Sections 3.1 and 3.3), with classical tiles at the leaves.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace ata {
+namespace {
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// Strassen's seven products in the A^T B form C = X^T Y (X r x p, Y r x q).
+// Quadrant index = 2 * (contraction half) + (column half) for X and Y, and
+// 2 * (row half) + (column half) for C.
+//   M1 = (X11 + X22)^T (Y11 + Y22)     M5 = (X11 + X21)^T Y22
+//   M2 = (X12 + X22)^T Y11             M6 = (X12 - X11)^T (Y11 + Y12)
+//   M3 = X11^T (Y12 - Y22)             M7 = (X21 - X22)^T (Y21 + Y22)
+//   M4 = X22^T (Y21 - Y11)
+//   C11 = M1 + M4 - M5 + M7   C12 = M3 + M5   C21 = M2 + M4
+//   C22 = M1 - M2 + M3 + M6
+const int kU[7][4] = {{1, 0, 0, 1}, {0, 1, 0, 1}, {1, 0, 0, 0}, {0, 0, 0, 1},
+                      {1, 0, 1, 0}, {-1, 1, 0, 0}, {0, 0, 1, -1}};
+const int kV[7][4] = {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0},
+                      {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}};
+const int kW[7][4] = {{1, 0, 0, 1}, {0, 0, 1, -1}, {0, 1, 0, 1}, {1, 0, 1, 0},
+                      {-1, 1, 0, 0}, {0, 0, 0, 1}, {1, 0, 0, 0}};
+
+struct Region {
+    int64_t off, ext;
+};
+
+// The 2^d regions of a dimension of size D after d ceil-first halvings, in
+// bit order (first split = most significant bit).  A second half that is
+// smaller than the first is zero-padded: its extent is clipped, possibly to
+// zero.  *nominal receives the common padded size ceil^d(D).
+std::vector<Region> split_regions(int64_t D, int d, int64_t *nominal) {
+    std::vector<Region> cur{{0, D}};
+    int64_t N = D;
+    for (int l = 0; l < d; ++l) {
+        int64_t Nc = (N + 1) / 2;
+        std::vector<Region> nxt;
+        nxt.reserve(cur.size() * 2);
+        for (const Region &r : cur) {
+            nxt.push_back({r.off, std::min(Nc, r.ext)});
+            nxt.push_back({r.off + Nc, std::max<int64_t>(0, r.ext - Nc)});
+        }
+        cur.swap(nxt);
+        N = Nc;
+    }
+    *nominal = N;
+    return cur;
+}
+
+int bit(int64_t idx, int l, int d) { return static_cast<int>((idx >> (d - 1 - l)) & 1); }
+
+int log2_ceil(int64_t x) {
+    int t = 0;
+    while ((int64_t(1) << t) < x) ++t;
+    return t;
+}
+
+struct Builder {
+    Plan &P;
+    bool digits;
+    int64_t prod_elems = 0;
+
+    explicit Builder(Plan &p) : P(p), digits(p.p.mode != MODE_F64) {}
+
+    int family_for(int64_t K_nominal) {
+        int64_t Kp = round_up(std::max<int64_t>(K_nominal, 1), PREP_K);
+        for (size_t i = 0; i < P.families.size(); ++i)
+            if (P.families[i].K_pitch == Kp && !(i == 0 && digits)) return static_cast<int>(i);
+        Family f{};
+        f.K_pitch = Kp;
+        f.cols = 0;
+        P.families.push_back(f);
+        return static_cast<int>(P.families.size()) - 1;
+    }
+
+    // Add an operand descriptor; returns its first column in the family.
+    int64_t add_op(int fam, const std::vector<OpTerm> &terms, int64_t P_nominal) {
+        OpDesc o{};
+        o.family = fam;
+        int nonempty = 0;
+        for (const OpTerm &t : terms)
+            if (t.rows > 0 && t.cols > 0) ++nonempty;
+        o.t_shift = log2_ceil(std::max(1, nonempty));
+        o.first_term = static_cast<int32_t>(P.terms.size());
+        for (const OpTerm &t : terms)
+            if (t.rows > 0 && t.cols > 0) P.terms.push_back(t);
+        o.nterms = static_cast<int32_t>(P.terms.size()) - o.first_term;
+        o.K_pitch = static_cast<int32_t>(P.families[fam].K_pitch);
+        o.P_pad = static_cast<int32_t>(round_up(std::max<int64_t>(P_nominal, 1), TILE));
+        o.out_col = P.families[fam].cols;
+        P.families[fam].cols += o.P_pad;
+        P.ops.push_back(o);
+        return o.out_col;
+    }
+
+    void plain_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols, bool diag) {
+        LeafTask t{};
+        t.fam_u = digits ? 0 : -1;
+        t.fam_v = t.fam_u;
+        t.col_u = static_cast<int32_t>(r0);
+        t.col_v = static_cast<int32_t>(c0);
+        t.k0 = 0;
+        t.klen = static_cast<int32_t>(P.p.m);
+        t.rows = static_cast<int32_t>(rows);
+        t.cols = static_cast<int32_t>(cols);
+        t.diag = diag ? 1 : 0;
+        if (P.p.mode == MODE_F64) {
+            t.kind = OUT_C_F64;
+            t.eu = t.ev = -1;  // native FP64 works on A unscaled
+        } else {
+            t.kind = (P.p.mode == MODE_F64_EMU) ? OUT_C_F64 : OUT_C_F32;
+            t.eu = static_cast<int32_t>(r0);
+            t.ev = static_cast<int32_t>(c0);
+        }
+        t.shift = 0;
+        t.out_off = r0 * P.p.ldc + c0;
+        t.out_ld = P.p.ldc;
+        P.tasks.push_back(t);
+        P.plain_madds += static_cast<double>(P.p.m) * TILE * TILE;
+        P.leaf_madds += static_cast<double>(P.p.m) * TILE * TILE;
+    }
+
+    // Lower-triangle tiles of the diagonal panel [c0, c0 + w).
+    void diag_panel(int64_t c0, int64_t w) {
+        P.n_panels++;
+        int64_t nt = ceil_div(w, TILE);
+        for (int64_t J = 0; J < nt; ++J)
+            for (int64_t K = 0; K <= J; ++K)
+                plain_tile(c0 + J * TILE, c0 + K * TILE, std::min<int64_t>(TILE, w - J * TILE),
+                           std::min<int64_t>(TILE, w - K * TILE), J == K);
+    }
+
+    // Classical tiles of the off-diagonal block rows [r0, r0+p) x cols [c0, c0+q).
+    void classical_block(int64_t r0, int64_t p, int64_t c0, int64_t q) {
+        for (int64_t J = 0; J < ceil_div(p, TILE); ++J)
+            for (int64_t K = 0; K < ceil_div(q, TILE); ++K)
+                plain_tile(r0 + J * TILE, c0 + K * TILE, std::min<int64_t>(TILE, p - J * TILE),
+                           std::min<int64_t>(TILE, q - K * TILE), false);
+    }
+
+    int block_depth(int64_t p, int64_t q) const {
+        int d = 0;
+        int64_t pp = p, qq = q, mm = P.p.m;
+        while (d < P.depth) {
+            int64_t np = (pp + 1) / 2, nq = (qq + 1) / 2, nm = (mm + 1) / 2;
+            if (np < P.p.strassen_min || nq < P.p.strassen_min || nm < 2) break;
+            pp = np;
+            qq = nq;
+            mm = nm;
+            ++d;
+        }
+        return d;
+    }
+
+    // C[r0:r0+p, c0:c0+q] = A[:, r0:r0+p]^T A[:, c0:c0+q] by d Strassen levels.
+    void strassen_block(int64_t r0, int64_t p, int64_t c0, int64_t q, int d) {
+        int64_t rn, pn, qn;
+        std::vector<Region> kreg = split_regions(P.p.m, d, &rn);
+        std::vector<Region> preg = split_regions(p, d, &pn);
+        std::vector<Region> qreg = split_regions(q, d, &qn);
+        const int64_t nsub = int64_t(1) << d;
+        int64_t nprod = 1;
+        for (int l = 0; l < d; ++l) nprod *= 7;
+        int fam = family_for(rn);
+
+        std::vector<int64_t> prod_off(nprod);
+        std::vector<int> prod_shift(nprod);
+        for (int64_t r = 0; r < nprod; ++r) {
+            int digit[8];
+            int64_t rr = r;
+            for (int l = d - 1; l >= 0; --l) {
+                digit[l] = static_cast<int>(rr % 7);
+                rr /= 7;
+            }
+            std::vector<OpTerm> ut, vt;
+            for (int64_t ia = 0; ia < nsub; ++ia) {
+                for (int64_t ib = 0; ib < nsub; ++ib) {
+                    int cu = 1, cv = 1;
+                    for (int l = 0; l < d; ++l) {
+                        int quad = 2 * bit(ia, l, d) + bit(ib, l, d);
+                        cu *= kU[digit[l]][quad];
+                        cv *= kV[digit[l]][quad];
+                    }
+                    if (cu != 0)
+                        ut.push_back({kreg[ia].off, r0 + preg[ib].off,
+                                      static_cast<int32_t>(kreg[ia].ext),
+                                      static_cast<int32_t>(preg[ib].ext), cu, 0});
+                    if (cv != 0)
+                        vt.push_back({kreg[ia].off, c0 + qreg[ib].off,
+                                      static_cast<int32_t>(kreg[ia].ext),
+                                      static_cast<int32_t>(qreg[ib].ext), cv, 0});
+                }
+            }
+            size_t ou = P.ops.size();
+            int64_t ucol = add_op(fam, ut, pn);
+            size_t ov = P.ops.size();
+            int64_t vcol = add_op(fam, vt, qn);
+            int shift = P.ops[ou].t_shift + P.ops[ov].t_shift;
+            prod_shift[r] = shift;
+            prod_off[r] = prod_elems;
+            prod_elems += pn * qn;
+            P.n_products++;
+            for (int64_t J = 0; J < ceil_div(pn, TILE); ++J) {
+                for (int64_t K = 0; K < ceil_div(qn, TILE); ++K) {
+                    LeafTask t{};
+                    t.fam_u = fam;
+                    t.fam_v = fam;
+                    t.col_u = static_cast<int32_t>(ucol + J * TILE);
+                    t.col_v = static_cast<int32_t>(vcol + K * TILE);
+                    t.k0 = 0;
+                    t.klen = static_cast<int32_t>(rn);
+                    t.rows = static_cast<int32_t>(std::min<int64_t>(TILE, pn - J * TILE));
+                    t.cols = static_cast<int32_t>(std::min<int64_t>(TILE, qn - K * TILE));
+                    t.diag = 0;
+                    t.kind = digits ? OUT_M_I64 : OUT_M_F64;
+                    t.shift = shift;
+                    t.eu = t.ev = -1;
+                    t.out_off = prod_off[r] + J * TILE * qn + K * TILE;
+                    t.out_ld = qn;
+                    P.tasks.push_back(t);
+                    P.leaf_madds += static_cast<double>(rn) * TILE * TILE;
+                }
+            }
+        }
+        P.plain_madds += static_cast<double>(P.p.m) * ceil_div(p, TILE) * ceil_div(q, TILE) * TILE * TILE;
+
+        // Result sums, one per (row region, column region) of the C block.
+        for (int64_t ir = 0; ir < nsub; ++ir) {
+            for (int64_t ic = 0; ic < nsub; ++ic) {
+                if (preg[ir].ext == 0 || qreg[ic].ext == 0) continue;
+                CombDesc c{};
+                c.c_off = (r0 + preg[ir].off) * P.p.ldc + c0 + qreg[ic].off;
+                c.rows = static_cast<int32_t>(preg[ir].ext);
+                c.cols = static_cast<int32_t>(qreg[ic].ext);
+                c.e_row0 = static_cast<int32_t>(r0 + preg[ir].off);
+                c.e_col0 = static_cast<int32_t>(c0 + qreg[ic].off);
+                c.first_term = static_cast<int32_t>(P.cterms.size());
+                for (int64_t r = 0; r < nprod; ++r) {
+                    int64_t rr = r;
+                    int w = 1;
+                    for (int l = d - 1; l >= 0; --l) {
+                        int dg = static_cast<int>(rr % 7);
+                        rr /= 7;
+                        w *= kW[dg][2 * bit(ir, l, d) + bit(ic, l, d)];
+                    }
+                    if (w != 0)
+                        P.cterms.push_back({prod_off[r], static_cast<int32_t>(qn), w, prod_shift[r], 0});
+                }
+                c.nterms = static_cast<int32_t>(P.cterms.size()) - c.first_term;
+                c.tile_base = P.comb_tiles;
+                P.comb_tiles += ceil_div(c.rows, 32) * ceil_div(c.cols, 32);
+                P.combs.push_back(c);
+            }
+        }
+    }
+
+    void recurse(int64_t c0, int64_t w) {
+        if (w <= P.cutoff || w <= 1) {
+            diag_panel(c0, w);
+            return;
+        }
+        int64_t n1 = w / 2, n2 = w - n1;
+        recurse(c0, n1);
+        recurse(c0 + n1, n2);
+        P.n_blocks++;
+        int d = block_depth(n2, n1);
+        if (d == 0)
+            classical_block(c0 + n1, n2, c0, n1);
+        else
+            strassen_block(c0 + n1, n2, c0, n1, d);
+    }
+};
+
+}  // namespace
+
+int default_slices(int mode, int64_t m) {
+    (void)m;
+    switch (mode) {
+        case MODE_F64_EMU: return 6;
+        case MODE_F32: return 3;
+        case MODE_F32_BF16: return 1;
+        default: return 0;
+    }
+}
+
+bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
+    Plan &P = *plan;
+    P = Plan();
+    P.p = pp;
+    if (pp.m < 0 || pp.n < 0 || pp.lda < std::max<int64_t>(pp.n, 1) ||
+        pp.ldc < std::max<int64_t>(pp.n, 1)) {
+        if (err) *err = "invalid dimensions";
+        return false;
+    }
+    if (pp.m > (int64_t(1) << 30) || pp.n > (int64_t(1) << 30)) {
+        if (err) *err = "dimension beyond the 2^30 limit";
+        return false;
+    }
+    if (pp.mode != MODE_F64 && pp.mode != MODE_F64_EMU && pp.mode != MODE_F32 &&
+        pp.mode != MODE_F32_BF16) {
+        if (err) *err = "unknown mode";
+        return false;
+    }
+    P.slices = pp.slices > 0 ? pp.slices : default_slices(pp.mode, pp.m);
+    if (pp.mode == MODE_F64) P.slices = 0;
+    if (pp.mode != MODE_F64 && (P.slices < 1 || P.slices > MAX_SLICES)) {
+        if (err) *err = "slices out of range";
+        return false;
+    }
+    P.depth = pp.depth >= 0 ? pp.depth : (pp.n >= 4096 ? 1 : 0);
+    if (P.depth > 4) P.depth = 4;
+    if (P.depth == 0)
+        P.cutoff = static_cast<int>(std::max<int64_t>(pp.n, 1));
+    else
+        P.cutoff = pp.cutoff > 0 ? pp.cutoff : static_cast<int>(std::max<int64_t>(pp.n / 4, 256));
+    // Exact int64 combine: |T_r| <= 1.01 K_r 2^38 per product, summed with
+    // shifts of up to 2 bits per Strassen level; keep the worst case < 2^62.
+    while (P.depth > 0) {
+        double K = std::ceil(static_cast<double>(pp.m) / std::pow(2.0, P.depth));
+        double bound = 1.01 * K * std::pow(2.0, 38 + 2 * P.depth) * std::pow(4.0, P.depth);
+        if (bound < std::pow(2.0, 62)) break;
+        P.depth--;
+    }
+
+    Builder B(P);
+    if (B.digits) {
+        // Family 0: digit planes of A itself (diagonal panels, classical tiles).
+        Family f0{};
+        f0.K_pitch = round_up(std::max<int64_t>(pp.m, 1), PREP_K);
+        P.families.push_back(f0);
+        B.add_op(0, {OpTerm{0, 0, static_cast<int32_t>(pp.m), static_cast<int32_t>(pp.n), 1, 0}},
+                 pp.n);
+    }
+    if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
+
+    // Workspace layout.
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+        int64_t o = off;
+        off += round_up(std::max<int64_t>(bytes, 0), 1024);
+        return o;
+    };
+    P.off_colmax = take(pp.n * 8);
+    P.off_expo = take(pp.n * 4);
+    for (Family &f : P.families) {
+        f.plane_elems = f.cols * f.K_pitch;
+        int64_t bytes = B.digits ? f.plane_elems * 2 * P.slices : f.plane_elems * 8;
+        f.offset = take(bytes);
+    }
+    P.product_bytes = B.prod_elems * 8;
+    P.off_products = take(P.product_bytes);
+    // prep tile prefix sums
+    P.prep_tiles = 0;
+    for (OpDesc &o : P.ops) {
+        o.tile_base = P.prep_tiles;
+        P.prep_tiles += (o.K_pitch / PREP_K) * (o.P_pad / PREP_C);
+    }
+    P.t_ops = 0;
+    P.t_terms = round_up(P.t_ops + static_cast<int64_t>(P.ops.size() * sizeof(OpDesc)), 256);
+    P.t_tasks = round_up(P.t_terms + static_cast<int64_t>(P.terms.size() * sizeof(OpTerm)), 256);
+    P.t_combs = round_up(P.t_tasks + static_cast<int64_t>(P.tasks.size() * sizeof(LeafTask)), 256);
+    P.t_cterms = round_up(P.t_combs + static_cast<int64_t>(P.combs.size() * sizeof(CombDesc)), 256);
+    P.table_bytes = round_up(P.t_cterms + static_cast<int64_t>(P.cterms.size() * sizeof(CombTerm)), 256);
+    P.off_tables = take(P.table_bytes);
+    P.workspace_bytes = off;
+    return true;
+}
+
+void pack_tables(const Plan &P, std::vector<uint8_t> *buf) {
+    buf->assign(static_cast<size_t>(P.table_bytes), 0);
+    auto put = [&](int64_t at, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(buf->data() + at, src, bytes);
+    };
+    put(P.t_ops, P.ops.data(), P.ops.size() * sizeof(OpDesc));
+    put(P.t_terms, P.terms.data(), P.terms.size() * sizeof(OpTerm));
+    put(P.t_tasks, P.tasks.data(), P.tasks.size() * sizeof(LeafTask));
+    put(P.t_combs, P.combs.data(), P.combs.size() * sizeof(CombDesc));
+    put(P.t_cterms, P.cterms.data(), P.cterms.size() * sizeof(CombTerm));
+}
+
+}  // namespace ata

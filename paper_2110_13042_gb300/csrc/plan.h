@@ -1,0 +1,132 @@
+// Host planner: flattens the AtA recursion (Algorithm 1) and the Strassen
+// trees of its off-diagonal blocks into flat, phase-ordered task lists that
+// the device kernels execute.  Host-only C++ (no CUDA), shared with the
+// kernels through the plain structs below.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ata {
+
+constexpr int TILE = 128;        // leaf output tile edge (rows and columns)
+constexpr int KSTEP = 32;        // contraction rows per pipeline stage
+constexpr int CHUNK_STEPS = 8;   // stages per exact-accumulation chunk (256 rows)
+constexpr int PREP_K = 64;       // prep tile: contraction rows
+constexpr int PREP_C = 64;       // prep tile: columns
+constexpr int MAX_FAMILIES = 6;  // operand families (tensor maps) per launch
+constexpr int MAX_SLICES = 7;
+
+enum Mode : int { MODE_F64 = 0, MODE_F64_EMU = 1, MODE_F32 = 2, MODE_F32_BF16 = 4 };
+
+// One term of a (possibly summed) Strassen operand: a sub-block of A.
+struct OpTerm {
+    int64_t row0;   // first contraction row in A
+    int64_t col0;   // first column in A
+    int32_t rows;   // valid rows (contraction extent); rows beyond are zero
+    int32_t cols;   // valid columns; columns beyond are zero
+    int32_t coef;   // +1 or -1
+    int32_t pad;
+};
+
+// Operand generator: writes
+//   U[k][c] = sum_t coef_t * A[row0_t + k][col0_t + c] * 2^-e(col0_t + c)
+// for k < K_pitch, c < P_pad (zero outside every term's extent) into the
+// family's planes: either `slices` BF16 digit planes (K-major, [q][col][k])
+// or one FP64 array ([k][col], row-major) for the native FP64 mode.
+struct OpDesc {
+    int32_t family;
+    int32_t t_shift;     // |U| < 2^t_shift (t = log2 of the term count)
+    int32_t nterms;
+    int32_t first_term;
+    int64_t out_col;     // first column of this operand inside the family
+    int32_t K_pitch;     // contraction rows written (multiple of PREP_K)
+    int32_t P_pad;       // columns written (multiple of TILE)
+    int64_t tile_base;   // prefix count of prep tiles (flat grid)
+};
+
+struct Family {
+    int64_t K_pitch;     // contraction pitch in elements (multiple of PREP_K)
+    int64_t cols;        // total columns (multiple of TILE)
+    int64_t offset;      // byte offset of plane 0 in the workspace
+    int64_t plane_elems; // elements per plane = cols * K_pitch
+};
+
+// One leaf output tile (TILE x TILE), all digit pairs (or one FP64 product).
+struct LeafTask {
+    int32_t fam_u, fam_v;   // operand families (-1: A itself, native FP64 only)
+    int32_t col_u, col_v;   // first column of the tile's rows / columns
+    int32_t k0, klen;       // contraction range
+    int32_t rows, cols;     // valid output rows / columns (<= TILE)
+    int32_t diag;           // 1: diagonal tile, write only local col <= local row
+    int32_t kind;           // OUT_* below
+    int32_t shift;          // product unit exponent adjustment (t_u + t_v)
+    int32_t eu, ev;         // exponent index of tile row 0 / column 0 (-1: none)
+    int32_t pad;
+    int64_t out_off;        // element offset of the tile origin in the output
+    int64_t out_ld;         // output leading dimension (elements)
+};
+
+enum OutKind : int {
+    OUT_C_F64 = 0,   // double into C, scaled by 2^(e_row + e_col)
+    OUT_C_F32 = 1,   // float into C, scaled by 2^(e_row + e_col)
+    OUT_M_I64 = 2,   // exact int64 partial into the product workspace
+    OUT_M_F64 = 3    // double into the product workspace (native FP64)
+};
+
+// One Strassen result sum: region of C = sum_r coef_r * M_r (clipped).
+struct CombTerm {
+    int64_t src_off;  // element offset of M_r's origin in the product workspace
+    int32_t ld;       // M_r leading dimension
+    int32_t coef;     // +1 / -1
+    int32_t shift;    // unit exponent of M_r (t_u + t_v)
+    int32_t pad;
+};
+
+struct CombDesc {
+    int64_t c_off;       // element offset in C of the region origin
+    int32_t rows, cols;  // region extent
+    int32_t e_row0;      // A column of region row 0 (exponent index)
+    int32_t e_col0;      // A column of region column 0
+    int32_t first_term, nterms;
+    int64_t tile_base;   // prefix count of 32x32 combine tiles
+};
+
+struct PlanParams {
+    int64_t m = 0, n = 0, lda = 0, ldc = 0;
+    int mode = MODE_F64_EMU;
+    int cutoff = 0;          // 0 = auto
+    int depth = -1;          // -1 = auto
+    int slices = 0;          // 0 = auto
+    int strassen_min = 256;  // smallest leaf-product width Strassen may produce
+};
+
+struct Plan {
+    PlanParams p;
+    int cutoff = 0, depth = 0, slices = 0;
+    int64_t n_panels = 0, n_blocks = 0, n_products = 0;
+    std::vector<Family> families;       // [0] = plain digits of A (if used)
+    std::vector<OpDesc> ops;
+    std::vector<OpTerm> terms;
+    std::vector<LeafTask> tasks;
+    std::vector<CombDesc> combs;
+    std::vector<CombTerm> cterms;
+    int64_t prep_tiles = 0, comb_tiles = 0;
+    // workspace layout (byte offsets)
+    int64_t off_colmax = 0, off_expo = 0, off_products = 0, product_bytes = 0;
+    int64_t off_tables = 0, table_bytes = 0, workspace_bytes = 0;
+    // byte offsets of the task tables inside the table block
+    int64_t t_ops = 0, t_terms = 0, t_tasks = 0, t_combs = 0, t_cterms = 0;
+    double leaf_madds = 0, plain_madds = 0;   // per digit pair / per FP64 product
+    bool uses_digits() const { return p.mode != MODE_F64; }
+};
+
+// Digits per column for a mode (slices == 0 -> default).
+int default_slices(int mode, int64_t m);
+// Build the full plan.  Returns false (and sets *err) on invalid parameters.
+bool make_plan(const PlanParams &pp, Plan *plan, std::string *err);
+// Copy the task tables into a contiguous host buffer laid out as
+// plan.t_* describe (size plan.table_bytes).
+void pack_tables(const Plan &plan, std::vector<uint8_t> *buf);
+
+}  // namespace ata

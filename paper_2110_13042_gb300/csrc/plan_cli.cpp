@@ -1,0 +1,65 @@
+// Host-only planner inspector (used by the CPU tests): builds the plan for
+//   plan_cli m n mode cutoff depth slices
+// and prints key=value statistics, including a coverage check that every
+// lower-triangle entry of C is produced exactly once (by a diagonal/classical
+// tile or by one Strassen result sum) and no upper entry is produced.
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+using namespace ata;
+
+int main(int argc, char **argv) {
+    if (argc < 7) return 2;
+    PlanParams pp;
+    pp.m = std::atoll(argv[1]);
+    pp.n = std::atoll(argv[2]);
+    pp.lda = pp.ldc = pp.n > 0 ? pp.n : 1;
+    pp.mode = std::atoi(argv[3]);
+    pp.cutoff = std::atoi(argv[4]);
+    pp.depth = std::atoi(argv[5]);
+    pp.slices = std::atoi(argv[6]);
+    Plan P;
+    std::string err;
+    if (!make_plan(pp, &P, &err)) {
+        std::fprintf(stderr, "%s\n", err.c_str());
+        return 1;
+    }
+    const int64_t n = pp.n, ldc = pp.ldc;
+    std::vector<uint8_t> cov(static_cast<size_t>(n * n), 0);
+    double s_leaf = 0, s_plain = 0;
+    for (const LeafTask &t : P.tasks) {
+        if (t.kind == OUT_M_I64 || t.kind == OUT_M_F64) {
+            s_leaf += static_cast<double>(t.klen) * t.rows * t.cols;
+            continue;
+        }
+        const int64_t r0 = t.out_off / ldc, c0 = t.out_off % ldc;
+        for (int r = 0; r < t.rows; ++r)
+            for (int c = 0; c < t.cols; ++c)
+                if (!t.diag || c <= r) cov[(r0 + r) * n + c0 + c]++;
+    }
+    for (const CombDesc &d : P.combs) {
+        const int64_t r0 = d.c_off / ldc, c0 = d.c_off % ldc;
+        s_plain += static_cast<double>(pp.m) * d.rows * d.cols;
+        for (int r = 0; r < d.rows; ++r)
+            for (int c = 0; c < d.cols; ++c) cov[(r0 + r) * n + c0 + c]++;
+    }
+    int64_t covered = 0, overlap = 0;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t k = 0; k < n; ++k) {
+            const int v = cov[j * n + k];
+            if (k <= j && v == 1) covered++;
+            if (v > 1 || (k > j && v > 0)) overlap++;
+        }
+    std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
+                "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
+                "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f\n",
+                P.cutoff, P.depth, P.slices, (long long)P.n_panels, (long long)P.n_blocks,
+                (long long)P.n_products, P.tasks.size(), (long long)covered, (long long)overlap,
+                P.cterms.size(), P.ops.size(), P.families.size(), (long long)P.workspace_bytes, s_leaf,
+                s_plain);
+    return 0;
+}
