@@ -78,8 +78,11 @@ typedef struct {
     int strassen_depth;  /* Strassen levels on every off-diagonal block
                             (0 = classical tiles, i.e. plain tiled AtA);
                             -1 = auto                                              */
-    int slices;          /* digits per column for ATA_F64_EMU (3..7); 0 = auto    */
-    int reserved[5];     /* must be zero                                          */
+    int slices;          /* digits per column for ATA_F64_EMU (1..7); 0 = auto    */
+    int strassen_min;    /* a Strassen level splits an off-diagonal (sub)block
+                            only while both its sides are >= strassen_min
+                            columns; 0 = auto                                      */
+    int reserved[4];     /* must be zero                                          */
 } ata_config;
 
 typedef struct ata_handle_s *ata_handle;
@@ -122,6 +125,10 @@ int ata_destroy(ata_handle h);
 
 /* Static English description of a status code. */
 const char *ata_status_string(int status);
+
+/* Description of the most recent failure on this handle ("" if none): the
+ * step that failed and the CUDA error string.  Valid until the next call. */
+const char *ata_last_error(ata_handle h);
 
 /* Host-only plan description, for tests and tuning.  Fills `out` (host array
  * of ATA_PLAN_FIELDS int64) for the plan ata_lower would run for (m, n,

@@ -50,6 +50,8 @@ def load():
     L.ata_status_string.argtypes = [ip]
     L.ata_status_string.restype = ctypes.c_char_p
     L.ata_plan_info.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64)]
+    L.ata_last_error.argtypes = [vp]
+    L.ata_last_error.restype = ctypes.c_char_p
     L.ata_set_timing.argtypes = [vp, ip]
     L.ata_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     for f in ("ata_create", "ata_set_config", "ata_lower", "ata_batched", "ata_sync",
@@ -70,11 +72,12 @@ def version() -> int:
 
 class Config(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int), ("strassen_depth", ctypes.c_int),
-                ("slices", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("slices", ctypes.c_int), ("strassen_min", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
-def _config(cutoff=0, depth=-1, slices=0) -> Config:
-    return Config(int(cutoff), int(depth), int(slices), (ctypes.c_int * 5)())
+def _config(cutoff=0, depth=-1, slices=0, strassen_min=0) -> Config:
+    return Config(int(cutoff), int(depth), int(slices), int(strassen_min), (ctypes.c_int * 4)())
 
 
 def _check(rc: int, what: str):
@@ -100,14 +103,14 @@ def _stream_ptr(stream):
 class Handle:
     """Owns an ``ata_handle`` (workspace, plan cache, device status word)."""
 
-    def __init__(self, cutoff=0, depth=-1, slices=0):
+    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0):
         L = load()
         self._h = ctypes.c_void_p()
-        cfg = _config(cutoff, depth, slices)
+        cfg = _config(cutoff, depth, slices, strassen_min)
         _check(L.ata_create(ctypes.byref(self._h), ctypes.byref(cfg)), "ata_create")
 
-    def set_config(self, cutoff=0, depth=-1, slices=0):
-        cfg = _config(cutoff, depth, slices)
+    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0):
+        cfg = _config(cutoff, depth, slices, strassen_min)
         _check(load().ata_set_config(self._h, ctypes.byref(cfg)), "ata_set_config")
 
     def lower_ptr(self, m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:
@@ -115,13 +118,17 @@ class Handle:
         return int(load().ata_lower(self._h, int(m), int(n), A_ptr, int(lda), C_ptr, int(ldc),
                                     int(dtype), _stream_ptr(stream)))
 
+    def last_error(self) -> str:
+        return load().ata_last_error(self._h).decode()
+
     def lower(self, A, C, dtype, stream=None):
         """low(C) <- low(A^T A) for row-major CUDA tensors A (m x n) and C (n x n)."""
         m, n = A.shape
         if A.stride(1) != 1 or C.stride(1) != 1:
             raise ValueError("A and C must be row-major with unit column stride")
-        _check(self.lower_ptr(m, n, A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0), dtype,
-                              stream), "ata_lower")
+        rc = self.lower_ptr(m, n, A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0), dtype, stream)
+        if rc != 0:
+            raise AtaError(rc, f"ata_lower [{self.last_error()}]")
 
     def batched_ptr(self, ms, ns, A_ptrs, ldas, C_ptrs, ldcs, dtype, stream=None) -> int:
         count = len(ms)

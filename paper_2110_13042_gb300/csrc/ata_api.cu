@@ -39,7 +39,7 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
-using Key = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int, int>;
+using Key = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int, int, int>;
 
 struct CachedPlan {
     Plan plan;
@@ -73,6 +73,7 @@ struct ata_handle_s {
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::string last_error;
 };
 
 namespace {
@@ -80,7 +81,7 @@ namespace {
 int check_config(const ata_config *c) {
     if (!c) return ATA_OK;
     if (c->cutoff < 0 || c->strassen_depth < -1 || c->strassen_depth > 4 || c->slices < 0 ||
-        c->slices > MAX_SLICES)
+        c->slices > MAX_SLICES || c->strassen_min < 0)
         return ATA_ERR_INVALID;
     for (int r : c->reserved)
         if (r != 0) return ATA_ERR_INVALID;
@@ -97,7 +98,18 @@ PlanParams params_for(const ata_config &cfg, int64_t m, int64_t n, int64_t lda, 
     pp.cutoff = cfg.cutoff;
     pp.depth = cfg.strassen_depth;
     pp.slices = cfg.slices;
+    pp.strassen_min = cfg.strassen_min;
     return pp;
+}
+
+int fail(ata_handle h, int status, const char *step, cudaError_t e = cudaSuccess) {
+    h->last_error = step;
+    if (e != cudaSuccess) {
+        h->last_error += ": ";
+        h->last_error += cudaGetErrorString(e);
+        cudaGetLastError();
+    }
+    return status;
 }
 
 int ensure_workspace(ata_handle h, size_t bytes) {
@@ -139,7 +151,7 @@ int bind_plan(ata_handle h, CachedPlan &cp) {
     std::memset(&lp, 0, sizeof(lp));
     if (P.uses_digits()) {
         EncodeTiledFn enc = get_encode_fn();
-        if (!enc) return ATA_ERR_CUDA;
+        if (!enc) return fail(h, ATA_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
         for (size_t f = 0; f < P.families.size(); ++f) {
             const Family &F = P.families[f];
             if (F.cols == 0) continue;
@@ -147,13 +159,21 @@ int bind_plan(ata_handle h, CachedPlan &cp) {
                                   static_cast<cuuint64_t>(P.slices)};
             cuuint64_t strides[2] = {static_cast<cuuint64_t>(F.K_pitch * 2),
                                      static_cast<cuuint64_t>(F.plane_elems * 2)};
-            cuuint32_t box[3] = {static_cast<cuuint32_t>(KSTEP), static_cast<cuuint32_t>(TILE),
-                                 static_cast<cuuint32_t>(P.slices)};
             cuuint32_t estr[3] = {1, 1, 1};
-            CUresult r = enc(&lp.maps[f], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h->ws + F.offset, dims,
-                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return ATA_ERR_CUDA;
+            for (int side = 0; side < 2; ++side) {
+                cuuint32_t box[3] = {static_cast<cuuint32_t>(KSTEP),
+                                     static_cast<cuuint32_t>(side == 0 ? TILE_M : TILE_N),
+                                     static_cast<cuuint32_t>(P.slices)};
+                CUtensorMap *map = side == 0 ? &lp.maps_a[f] : &lp.maps_b[f];
+                CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h->ws + F.offset, dims, strides,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    h->last_error = "cuTensorMapEncodeTiled failed with CUresult " +
+                                    std::to_string(static_cast<int>(r));
+                    return ATA_ERR_CUDA;
+                }
+            }
         }
     } else {
         for (size_t f = 0; f < P.families.size(); ++f) {
@@ -167,7 +187,7 @@ int bind_plan(ata_handle h, CachedPlan &cp) {
 }
 
 CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
-    Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices};
+    Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices, pp.strassen_min};
     auto it = h->plans.find(key);
     if (it != h->plans.end()) return it->second.get();
     std::unique_ptr<CachedPlan> cp(new CachedPlan());
@@ -205,6 +225,8 @@ bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) 
 extern "C" {
 
 int ata_version(void) { return 100; }
+
+const char *ata_last_error(ata_handle h) { return h ? h->last_error.c_str() : ""; }
 
 const char *ata_status_string(int status) {
     switch (status) {
@@ -305,6 +327,7 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
 int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
               int dtype, void *stream) {
     if (!h) return ATA_ERR_INVALID;
+    h->last_error.clear();
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
     if (m < 0 || n < 0) return ATA_ERR_INVALID;
     if (n == 0) return ATA_OK;
@@ -325,9 +348,9 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
     rc = bind_plan(h, *cp);
     if (rc != ATA_OK) return rc;
     if (h->resident != cp && P.table_bytes > 0) {
-        if (cudaMemcpyAsync(h->ws + P.off_tables, cp->pinned, P.table_bytes, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
-            return ATA_ERR_CUDA;
+        cudaError_t ce = cudaMemcpyAsync(h->ws + P.off_tables, cp->pinned, P.table_bytes,
+                                         cudaMemcpyHostToDevice, s);
+        if (ce != cudaSuccess) return fail(h, ATA_ERR_CUDA, "task-table upload", ce);
         h->resident = cp;
     }
     uint8_t *ws = h->ws;
@@ -340,10 +363,12 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
         if (h->timing) cudaEventRecord(h->ev[i], s);
     };
     mark(0);
-    if (need_expo && launch_colmax(A, m, n, lda, f32, colmax, expo, h->d_status, s) != cudaSuccess)
-        return ATA_ERR_CUDA;
+    cudaError_t e;
+    if (need_expo && (e = launch_colmax(A, m, n, lda, f32, colmax, expo, h->d_status, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "column-exponent launch", e);
     mark(1);
-    if (launch_prep(P, A, f32, expo, tables, ws, s) != cudaSuccess) return ATA_ERR_CUDA;
+    if ((e = launch_prep(P, A, f32, expo, tables, ws, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "operand-prep launch", e);
     mark(2);
 
     LeafParams &lp = cp->lp;
@@ -355,10 +380,11 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
     lp.status = h->d_status;
     lp.A64 = static_cast<const double *>(A);
     lp.lda = lda;
-    cudaError_t e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
-    if (e != cudaSuccess) return ATA_ERR_CUDA;
+    e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
+    if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "leaf launch", e);
     mark(3);
-    if (launch_combine(P, tables, ws + P.off_products, C, expo, s) != cudaSuccess) return ATA_ERR_CUDA;
+    if ((e = launch_combine(P, tables, ws + P.off_products, C, expo, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "combine launch", e);
     mark(4);
     if (h->timing) h->timed = true;
     return ATA_OK;

@@ -137,10 +137,11 @@ __device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t ti
 
 // Digit planes.  For operand o and its 64 x 64 tile (k0, c0):
 //   V[k][c] = sum_t coef_t * round(a(row0_t + k, col0_t + c) * 2^(F - t - e))
-// with F = 7 + 8 (S - 1) fraction bits, exact in int64.  V is then written as
-// S balanced digits x_1 (|x_1| <= 128) and x_q in [-128, 127] (q >= 2) with
-// V = sum_q x_q 2^(8 (S - q)); digit q is stored as the BF16 value
-// x_q * 2^(-8 (q - 1)) (exact), K-major: plane q, column c, contraction k.
+// with F = 8 + 9 (S - 1) fraction bits, exact in int64.  V is then written as
+// S balanced digits x_1 (|x_1| <= 256) and x_q in [-256, 255] (q >= 2) with
+// V = sum_q x_q 2^(9 (S - q)); digit q is stored as the BF16 value
+// x_q * 2^(-9 (q - 1)) (exact: at most 8 significant bits), K-major: plane q,
+// column c, contraction k.
 template <int S, typename T>
 __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
                                                           const int *__restrict__ expo,
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ 
     const int tiles_k = od.K_pitch / PREP_K;
     const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
     const int c0 = static_cast<int>(local / tiles_k) * PREP_C;
-    constexpr int F = 7 + 8 * (S - 1);
+    constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
 
     const int cc = threadIdx.x & 63;
     const int kr0 = threadIdx.x >> 6;
@@ -189,12 +190,12 @@ __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ 
         int x0[S], x1[S];
 #pragma unroll
         for (int q = S - 1; q >= 1; --q) {
-            const int d0 = static_cast<int>((v0 + 128) & 255) - 128;
-            const int d1 = static_cast<int>((v1 + 128) & 255) - 128;
+            const int d0 = static_cast<int>((v0 + 256) & 511) - 256;
+            const int d1 = static_cast<int>((v1 + 256) & 511) - 256;
             x0[q] = d0;
             x1[q] = d1;
-            v0 = (v0 - d0) >> 8;
-            v1 = (v1 - d1) >> 8;
+            v0 = (v0 - d0) >> DIGIT_BITS;
+            v1 = (v1 - d1) >> DIGIT_BITS;
         }
         x0[0] = static_cast<int>(v0);
         x1[0] = static_cast<int>(v1);
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ 
         const int64_t e0 = colg * fam.K_pitch + k0 + 2 * kp;  // even
 #pragma unroll
         for (int q = 0; q < S; ++q) {
-            const float sc = exp2f_i(-8 * q);
+            const float sc = exp2f_i(-DIGIT_BITS * q);
             __nv_bfloat162 val;
             val.x = __float2bfloat16_rn(static_cast<float>(x0[q]) * sc);
             val.y = __float2bfloat16_rn(static_cast<float>(x1[q]) * sc);
@@ -269,8 +270,9 @@ __device__ __forceinline__ int find_comb(const CombDesc *d, int nd, int64_t tile
 constexpr int MAX_CTERMS = 256;
 
 // Exact Strassen result sums: region = sum_r coef_r * T_r * 2^(shift_r),
-// added in int64 after aligning every product to the finest unit, then one
-// rounding to the output type and the column-scale 2^(e_j + e_k).
+// added in int64 in units of 2^(smin + rshift) (rshift > 0 only when the
+// worst case would overflow; the dropped bits are far below FP64 resolution),
+// then one rounding to the output type and the column scale 2^(e_j + e_k).
 template <typename TOut>
 __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
@@ -299,10 +301,14 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
         for (int t = 0; t < nt; ++t) {
             const CombTerm ct = st[t];
             int64_t v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
-            v = v * (int64_t(1) << (ct.shift - smin));
+            const int dsh = ct.shift - smin - d.rshift;
+            if (dsh >= 0)
+                v = v * (int64_t(1) << dsh);
+            else
+                v = (v + (int64_t(1) << (-dsh - 1))) >> (-dsh);
             sum += ct.coef > 0 ? v : -v;
         }
-        const int x = -38 + smin + expo[d.e_row0 + row] + ec;
+        const int x = -(T_FRAC + 2 * DIGIT_TOP_BITS) + smin + d.rshift + expo[d.e_row0 + row] + ec;
         if (sizeof(TOut) == 8)
             C[d.c_off + static_cast<int64_t>(row) * ldc + col] =
                 static_cast<TOut>(static_cast<double>(sum) * exp2i(x));
@@ -342,7 +348,8 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__rest
 }
 
 // ---------------------------------------------------- native FP64 leaf --
-// One 128 x 128 tile per block with FP64 tensor-core MMA (m8n8k4).
+// One TILE_M x TILE_N (128 x 96) tile per block with FP64 tensor-core MMA
+// (m8n8k4); 8 warps, each 32 rows x 48 columns.
 __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
                  : "+d"(c[0]), "+d"(c[1])
@@ -350,21 +357,21 @@ __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
 }
 
 __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ LeafParams p) {
-    constexpr int KT = 16, LDS = TILE + 4;
-    __shared__ double Us[KT][LDS];
-    __shared__ double Vs[KT][LDS];
+    constexpr int KT = 16, LDU = TILE_M + 4, LDV = TILE_N + 4;
+    __shared__ double Us[KT][LDU];
+    __shared__ double Vs[KT][LDV];
     const LeafTask t = p.tasks[blockIdx.x];
     const double *U = t.fam_u < 0 ? p.A64 : p.fam64[t.fam_u];
     const double *V = t.fam_v < 0 ? p.A64 : p.fam64[t.fam_v];
     const int64_t ldu = t.fam_u < 0 ? p.lda : p.fam_ld[t.fam_u];
     const int64_t ldv = t.fam_v < 0 ? p.lda : p.fam_ld[t.fam_v];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 64;
-    double acc[4][8][2];
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 48;
+    double acc[4][6][2];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+        for (int j = 0; j < 6; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
 
     const int lc = threadIdx.x & 127, lk = threadIdx.x >> 7;
     for (int k0 = 0; k0 < t.klen; k0 += KT) {
@@ -374,20 +381,20 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
             const int64_t k = static_cast<int64_t>(t.k0) + k0 + kk;
             const bool kin = (k0 + kk) < t.klen;
             Us[kk][lc] = (kin && lc < t.rows) ? U[k * ldu + t.col_u + lc] : 0.0;
-            Vs[kk][lc] = (kin && lc < t.cols) ? V[k * ldv + t.col_v + lc] : 0.0;
+            if (lc < TILE_N) Vs[kk][lc] = (kin && lc < t.cols) ? V[k * ldv + t.col_v + lc] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int k4 = 0; k4 < KT; k4 += 4) {
-            double a[4], b[8];
+            double a[4], b[6];
 #pragma unroll
             for (int fm = 0; fm < 4; ++fm) a[fm] = Us[k4 + (lane & 3)][wm + 8 * fm + (lane >> 2)];
 #pragma unroll
-            for (int fn = 0; fn < 8; ++fn) b[fn] = Vs[k4 + (lane & 3)][wn + 8 * fn + (lane >> 2)];
+            for (int fn = 0; fn < 6; ++fn) b[fn] = Vs[k4 + (lane & 3)][wn + 8 * fn + (lane >> 2)];
 #pragma unroll
             for (int fm = 0; fm < 4; ++fm)
 #pragma unroll
-                for (int fn = 0; fn < 8; ++fn) dmma_8x8x4(acc[fm][fn], a[fm], b[fn]);
+                for (int fn = 0; fn < 6; ++fn) dmma_8x8x4(acc[fm][fn], a[fm], b[fn]);
         }
         __syncthreads();
     }
@@ -396,11 +403,11 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
     for (int fm = 0; fm < 4; ++fm) {
         const int row = wm + 8 * fm + (lane >> 2);
 #pragma unroll
-        for (int fn = 0; fn < 8; ++fn) {
+        for (int fn = 0; fn < 6; ++fn) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int col = wn + 8 * fn + 2 * (lane & 3) + h;
-                if (row < t.rows && col < t.cols && (!t.diag || col <= row))
+                if (row < t.rows && col < t.cols && (!t.diag || col <= row + t.diag_off))
                     out[static_cast<int64_t>(row) * t.out_ld + col] = acc[fm][fn][h];
             }
         }

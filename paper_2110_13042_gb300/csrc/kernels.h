@@ -10,7 +10,8 @@ namespace ata {
 
 // Parameters shared by the leaf launches.
 struct LeafParams {
-    CUtensorMap maps[MAX_FAMILIES];  // one tiled map per digit family
+    CUtensorMap maps_a[MAX_FAMILIES];  // per digit family: 32 x TILE_M x S boxes
+    CUtensorMap maps_b[MAX_FAMILIES];  // per digit family: 32 x TILE_N x S boxes
     const LeafTask *tasks;
     int ntasks;
     int pad0;

@@ -1,28 +1,37 @@
-// tcgen05 leaf engine: every 128 x 128 output tile of every leaf product
+// tcgen05 leaf engine: every 128 x 96 output tile of every leaf product
 // (diagonal panels, classical tiles, Strassen products) in one persistent
 // launch.
 //
 // Arithmetic (split-digit emulation of a wide product on BF16 tensor cores):
 // each operand column is a fixed-point number written as S balanced digits,
-//   u = 2^-7 sum_q x_q 2^(-8 (q - 1)),  |x_1| <= 128, x_q in [-128, 127],
-// stored in BF16 as x_q 2^(-8 (q - 1)).  The digit products x_p y_q 2^-8(p+q-2)
-// are summed on the tensor core into FP32 accumulators in TMEM.  Products
-// with the same p + q share one accumulator:
-//   acc0: p + q = 2  (1 pair)  |partial| <= 1024 * 2^14      = 2^24 per 1024 rows
-//   acc1: p + q = 3  (2 pairs) |partial| <= 2 * 512 * 2^14   = 2^24 per 512 rows
-//   acc2: p + q = 4  (3 pairs) |partial| <= 3 * 256 * 2^14   < 2^24 per 256 rows
-//   acc3: p + q >= 5 (the rest, weight <= 2^-24 of acc0's unit; not exact)
-// so acc0..acc2 hold integers (in their units) below 2^24 and are EXACT in
-// FP32 when drained at those intervals.  The epilogue warps drain them into
-// a per-element int64 sum T (units of 2^-24 of the leading product), so the
-// tile's value is T * 2^(-38 + shift + e_row + e_col) with no rounding
-// except the folded low-order digits (acc3) and the final conversion.
+//   u = 2^-8 sum_q x_q 2^(-9 (q - 1)),  |x_1| <= 256, x_q in [-256, 255],
+// stored in BF16 as x_q 2^(-9 (q - 1)) (exact).  The digit products
+// x_p y_q 2^(-9 (p + q - 2)) (|x_p y_q| <= 2^16) are summed by the tensor core
+// into FP32 accumulators in TMEM; products with the same p + q share one:
+//   acc0: p + q = 2 (1 pair)   |partial| <= 1 * 256 * 2^16 = 2^24 (256 rows)
+//   acc1: p + q = 3 (2 pairs)  |partial| <= 2 * 128 * 2^16 = 2^24 (128 rows)
+//   acc2: p + q = 4 (3 pairs)  |partial| <= 3 *  64 * 2^16 < 2^24  (64 rows)
+//   acc3: p + q = 5 (4 pairs)  |partial| <= 4 *  64 * 2^16 = 2^24  (64 rows)
+//   acc4: p + q >= 6 (the rest, weight <= 2^-36 of acc0's unit; not exact)
+// Each of acc0..acc3 holds integers (in its unit) of magnitude <= 2^24, which
+// FP32 represents exactly, and is drained at the interval shown into a
+// per-element int64 sum T in units of 2^-27 (acc4 is rounded to that unit).
+// The tile's value is T * 2^(-43 + shift + e_row + e_col).
+//
+// Tile 128 x 96: five 96-column FP32 accumulators fit the 512 TMEM columns.
+// K step 16 (one MMA per digit pair per stage, 32-byte swizzle) keeps stages
+// small, so 4-10 of them are in flight.
 //
 // Pipeline (one CTA per SM, persistent over a static round-robin task list):
-//   warp 0      TMA producer: one 3-D box per operand per stage, all S digit
-//               planes of a 128-column x 32-row slab (64-byte swizzle).
-//   warp 1      TMEM allocator + single-thread tcgen05.mma issuer.
-//   warps 2..9  epilogue: tcgen05.ld drains, int64 accumulation, stores.
+//   warp 0       TMA producer: two 3-D boxes per stage (all S digit planes of
+//                a 128-row and a 96-row x 16-column slab).
+//   warp 1       TMEM allocator + single-thread tcgen05.mma issuer.
+//   warps 4..11  epilogue: tcgen05.ld drains, int64 accumulation, stores.
+//   (warps 2, 3 idle: 12 warps keep the 4 SM sub-partitions balanced, which
+//    bounds the register budget at 168 per thread.)
+// The issuer and the epilogue visit the accumulators in the same fixed order
+// (4, 0, 1, 2, 3): the ones drained every chunk come last, so the tensor core
+// keeps working on the others while they are drained.
 // All mbarrier waits are bounded (ptx.cuh).
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -33,37 +42,48 @@
 namespace ata {
 namespace {
 
-constexpr int NUM_THREADS = 320;
-constexpr int SLICE_BYTES = TILE * KSTEP * 2;  // one digit plane of one operand slab
+constexpr int NUM_THREADS = 384;
+constexpr int EPI_WARP0 = 4;
+constexpr int NUM_EPI = 256;
+constexpr int EPI_COLS = TILE_N / 2;                  // 48 columns per epilogue thread
+constexpr int A_SLICE_BYTES = TILE_M * KSTEP * 2;     // 4 KB
+constexpr int B_SLICE_BYTES = TILE_N * KSTEP * 2;     // 3 KB
+constexpr int MAX_ACC = 5;
+constexpr int MAX_STAGES = 10;
+constexpr uint32_t IDESC = idesc_bf16_f32(TILE_M, TILE_N);
 
 template <int S>
 struct Cfg {
-    static constexpr int STAGE_BYTES = 2 * S * SLICE_BYTES;
-    static constexpr int STAGES = S == 1 ? 8 : S == 2 ? 6 : S == 3 ? 4 : S == 4 ? 3 : 2;
-    static constexpr int NACC = S >= 4 ? 4 : S;
+    static constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);
+    static constexpr int STAGES_FIT = 229000 / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_FIT < MAX_STAGES ? STAGES_FIT : MAX_STAGES;
+    static constexpr int NACC = S >= MAX_ACC ? MAX_ACC : S;
     static constexpr int TMEM_COLS = NACC == 1 ? 128 : NACC == 2 ? 256 : 512;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + BAR_BYTES;
+    static_assert(STAGES >= 2, "pipeline depth");
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+    static_assert(NACC * TILE_N <= TMEM_COLS, "TMEM budget");
 };
 
 __host__ __device__ constexpr int acc_of(int p, int q) {
-    return (p + q - 2) < 3 ? (p + q - 2) : 3;
+    return (p + q - 2) < MAX_ACC - 1 ? (p + q - 2) : MAX_ACC - 1;
 }
 
-// Accumulators due for draining at the end of 256-row chunk `c`.
+// Accumulators due for draining at the end of 64-row chunk `c`.  The most
+// frequently drained accumulator present is in every non-empty mask.
 __device__ __forceinline__ uint32_t due_mask(int c, bool last, int nacc) {
-    uint32_t m = 1u << 2;                     // acc2 every chunk
-    if ((c & 1) == 1 || last) m |= 1u << 1;   // acc1 every 2 chunks
-    if ((c & 3) == 3 || last) m |= 1u | (1u << 3);  // acc0, acc3 every 4 chunks
+    uint32_t m = (1u << 2) | (1u << 3);             // acc2, acc3 every chunk
+    if ((c & 1) == 1 || last) m |= 1u << 1;          // acc1 every 2 chunks
+    if ((c & 3) == 3 || last) m |= 1u | (1u << 4);   // acc0, acc4 every 4 chunks
     return m & ((1u << nacc) - 1u);
 }
 
 struct Shared {
-    uint64_t full[8];
-    uint64_t empty[8];
+    uint64_t full[MAX_STAGES];
+    uint64_t empty[MAX_STAGES];
     uint64_t accf;
-    uint64_t acce[4];
+    uint64_t acce[MAX_ACC];
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -83,39 +103,88 @@ __device__ __forceinline__ float exp2f_(int x) {
     return scalbnf(1.0f, x);
 }
 
-// Add one drained accumulator (32 columns) into T.
-template <int ACC>
-__device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[32]) {
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const float v = __uint_as_float(r[i]);
-        if (ACC == 0) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v)) << 24;
-        } else if (ACC == 1) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 256.0f)) << 16;
-        } else if (ACC == 2) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 65536.0f)) << 8;
+// All digit pairs (P, Q) of accumulator ACC, unrolled at compile time.  The
+// shared-memory descriptors of digit P / Q differ from the stage's first by
+// the slice offset (in 16-byte units of the start-address field).
+template <int S, int ACC, int P = 1, int Q = 1>
+__device__ __forceinline__ void issue_pairs(uint32_t d_tmem, uint64_t da0, uint64_t db0, uint32_t &accum) {
+    if constexpr (P <= S) {
+        if constexpr (P + Q <= S + 1) {
+            if constexpr (acc_of(P, Q) == ACC) {
+                umma_f16(d_tmem, da0 + static_cast<uint64_t>((P - 1) * (A_SLICE_BYTES >> 4)),
+                         db0 + static_cast<uint64_t>((Q - 1) * (B_SLICE_BYTES >> 4)), IDESC, accum);
+                accum = 1u;
+            }
+            issue_pairs<S, ACC, P, Q + 1>(d_tmem, da0, db0, accum);
         } else {
-            T[i] += __float2ll_rn(v * 16777216.0f);
+            issue_pairs<S, ACC, P + 1, 1>(d_tmem, da0, db0, accum);
         }
     }
 }
 
+struct IssueState {
+    uint32_t acce_phase;  // bit a: parity of the next acce[a] wait
+    uint32_t pending;     // bit a: accumulator a handed to the epilogue
+    uint32_t fresh;       // bit a: next MMA into a overwrites
+};
+
 template <int S, int ACC>
-__device__ __forceinline__ void drain_one(int64_t (&T)[64], uint32_t tbase, int colbase, Shared *sh) {
-    uint32_t r[32];
-    tmem_ld_32x32b_x32(tbase + ACC * 128 + colbase, r);
-    tmem_ld_wait();
-    absorb<ACC>(T, r);
-    tmem_ld_32x32b_x32(tbase + ACC * 128 + colbase + 32, r);
-    tmem_ld_wait();
-    tc_fence_before();
-    mbar_arrive(&sh->acce[ACC]);
-    absorb<ACC>(T + 32, r);
+__device__ __forceinline__ bool step_acc(IssueState &st, Shared *sh, uint32_t tmem, uint64_t da0,
+                                         uint64_t db0, volatile int *abort_flag, int *status) {
+    if constexpr (ACC >= Cfg<S>::NACC) {
+        return true;
+    } else {
+        constexpr uint32_t bit = 1u << ACC;
+        if (st.pending & bit) {
+            if (!mbar_wait(&sh->acce[ACC], (st.acce_phase >> ACC) & 1u, abort_flag, status)) return false;
+            st.acce_phase ^= bit;
+            st.pending &= ~bit;
+            tc_fence_after();
+        }
+        uint32_t accum = (st.fresh & bit) ? 0u : 1u;
+        issue_pairs<S, ACC>(tmem + ACC * TILE_N, da0, db0, accum);
+        st.fresh &= ~bit;
+        return true;
+    }
+}
+
+// Add one drained accumulator (16 columns) into T (units 2^-27).
+template <int ACC>
+__device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float v = __uint_as_float(r[i]);
+        if (ACC == 0) {
+            T[i] += static_cast<int64_t>(__float2int_rn(v)) << 27;
+        } else if (ACC == 1) {
+            T[i] += static_cast<int64_t>(__float2int_rn(v * 512.0f)) << 18;
+        } else if (ACC == 2) {
+            T[i] += static_cast<int64_t>(__float2int_rn(v * 262144.0f)) << 9;
+        } else if (ACC == 3) {
+            T[i] += static_cast<int64_t>(__float2int_rn(v * 134217728.0f));
+        } else {
+            T[i] += __float2ll_rn(v * 134217728.0f);
+        }
+    }
+}
+
+template <int ACC>
+__device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh) {
+    uint32_t r[16];
+#pragma unroll
+    for (int c = 0; c < EPI_COLS / 16; ++c) {
+        tmem_ld_32x32b_x16(tbase + ACC * TILE_N + colbase + 16 * c, r);
+        tmem_ld_wait();
+        if (c == EPI_COLS / 16 - 1) {
+            tc_fence_before();
+            mbar_arrive(&sh->acce[ACC]);
+        }
+        absorb<ACC>(T + 16 * c, r);
+    }
 }
 
 template <int S>
-__global__ void __maxnreg__(200) leaf_tc_kernel(const __grid_constant__ LeafParams p) {
+__global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_constant__ LeafParams p) {
     using C = Cfg<S>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -130,7 +199,7 @@ __global__ void __maxnreg__(200) leaf_tc_kernel(const __grid_constant__ LeafPara
             mbar_init(&sh->empty[s], 1);
         }
         mbar_init(&sh->accf, 1);
-        for (int a = 0; a < 4; ++a) mbar_init(&sh->acce[a], 256);
+        for (int a = 0; a < MAX_ACC; ++a) mbar_init(&sh->acce[a], NUM_EPI);
         sh->abort_flag = 0;
         fence_mbar_init();
     }
@@ -159,11 +228,11 @@ __global__ void __maxnreg__(200) leaf_tc_kernel(const __grid_constant__ LeafPara
                         break;
                     }
                     uint8_t *a_dst = smem + stage * C::STAGE_BYTES;
-                    uint8_t *b_dst = a_dst + S * SLICE_BYTES;
+                    uint8_t *b_dst = a_dst + S * A_SLICE_BYTES;
                     mbar_arrive_expect_tx(&sh->full[stage], C::STAGE_BYTES);
                     const int k = t.k0 + step * KSTEP;
-                    tma_load_3d(a_dst, &p.maps[t.fam_u], &sh->full[stage], k, t.col_u, 0);
-                    tma_load_3d(b_dst, &p.maps[t.fam_v], &sh->full[stage], k, t.col_v, 0);
+                    tma_load_3d(a_dst, &p.maps_a[t.fam_u], &sh->full[stage], k, t.col_u, 0);
+                    tma_load_3d(b_dst, &p.maps_b[t.fam_v], &sh->full[stage], k, t.col_v, 0);
                     if (++stage == C::STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -175,71 +244,37 @@ __global__ void __maxnreg__(200) leaf_tc_kernel(const __grid_constant__ LeafPara
     } else if (warp == 1) {
         // ------------------------------------------------- MMA issuer --
         if (lane == 0) {
-            constexpr uint32_t IDESC = idesc_bf16_f32(TILE, TILE);
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t acce_phase = 0;  // bit a: parity of the next acce[a] wait
-            uint32_t pending = 0;     // bit a: accumulator a handed to the epilogue
-            uint32_t fresh = 0xFu;    // bit a: next MMA into a overwrites
+            IssueState st{0u, 0u, 0x1Fu};
             bool ok = true;
             const uint32_t smem_base = smem_u32(smem);
             for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
-                const LeafTask t = p.tasks[ti];
-                const int nsteps = (t.klen + KSTEP - 1) / KSTEP;
-                for (int step = 0; step < nsteps && ok; ++step) {
+                const int nsteps = (p.tasks[ti].klen + KSTEP - 1) / KSTEP;
+                for (int step = 0; step < nsteps; ++step) {
                     if (!mbar_wait(&sh->full[stage], phase, abort_flag, p.status)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
-                    const uint32_t b_base = a_base + S * SLICE_BYTES;
-                    // Free accumulators first (3, 0, 1, 2); accumulators still
-                    // being drained last, in the epilogue's drain order (2, 1, 0, 3).
-                    for (int oi = 0; oi < 8 && ok; ++oi) {
-                        const int acc = oi < 4 ? ((oi + 3) & 3) : (oi == 4 ? 2 : oi == 5 ? 1 : oi == 6 ? 0 : 3);
-                        const bool busy = (pending >> acc) & 1u;
-                        if (acc >= C::NACC || busy != (oi >= 4)) continue;
-                        if (busy) {
-                            if (!mbar_wait(&sh->acce[acc], (acce_phase >> acc) & 1u, abort_flag, p.status)) {
-                                ok = false;
-                                break;
-                            }
-                            acce_phase ^= 1u << acc;
-                            pending &= ~(1u << acc);
-                            tc_fence_after();
-                        }
-                        const uint32_t d_tmem = tmem + acc * 128;
-#pragma unroll
-                        for (int pp = 1; pp <= S; ++pp) {
-#pragma unroll
-                            for (int qq = 1; qq + pp <= S + 1; ++qq) {
-                                if (acc_of(pp, qq) != acc) continue;
-                                const uint64_t da = sdesc_kmajor_sw64(a_base + (pp - 1) * SLICE_BYTES);
-                                const uint64_t db = sdesc_kmajor_sw64(b_base + (qq - 1) * SLICE_BYTES);
-#pragma unroll
-                                for (int kk = 0; kk < KSTEP / 16; ++kk) {
-                                    umma_f16(d_tmem, da + 2 * kk, db + 2 * kk, IDESC,
-                                             ((fresh >> acc) & 1u) ? 0u : 1u);
-                                    fresh &= ~(1u << acc);
-                                }
-                            }
-                        }
-                    }
+                    const uint64_t da0 = sdesc_kmajor_sw32(a_base);
+                    const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
+                    ok = step_acc<S, 4>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                         step_acc<S, 0>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                         step_acc<S, 1>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                         step_acc<S, 2>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                         step_acc<S, 3>(st, sh, tmem, da0, db0, abort_flag, p.status);
                     if (!ok) break;
                     umma_commit(&sh->empty[stage]);
                     const bool last = step == nsteps - 1;
-                    // Chunk end: hand the due accumulators to the epilogue.  The
-                    // most frequently drained accumulator present is due at
-                    // every commit and is used by every step, so at most one
-                    // accf phase is ever outstanding.
                     const uint32_t due = (last || (step % CHUNK_STEPS) == CHUNK_STEPS - 1)
                                              ? due_mask(step / CHUNK_STEPS, last, C::NACC)
                                              : 0u;
-                    if (due) {
+                    if (due) {  // hand the due accumulators to the epilogue
                         umma_commit(&sh->accf);
-                        pending |= due;
-                        fresh |= due;
+                        st.pending |= due;
+                        st.fresh |= due;
                     }
                     if (++stage == C::STAGES) {
                         stage = 0;
@@ -249,22 +284,23 @@ __global__ void __maxnreg__(200) leaf_tc_kernel(const __grid_constant__ LeafPara
             }
             if (!ok) spin_ns(2000000);  // let MMAs already issued retire
         }
-    } else {
+    } else if (warp >= EPI_WARP0) {
         // --------------------------------------------------- epilogue --
-        const int q = warp & 3;                 // TMEM lane quadrant of this warp
-        const int half = (warp - 2) >> 2;       // which 64 columns
-        const int row = 32 * q + lane;          // tile row == TMEM lane
+        const int q = warp & 3;                      // TMEM lane quadrant of this warp
+        const int half = (warp - EPI_WARP0) >> 2;    // which 48 columns
+        const int row = 32 * q + lane;               // tile row == TMEM lane
         const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16);
-        const int colbase = 64 * half;
+        const int colbase = EPI_COLS * half;
         uint32_t accf_phase = 0;
         bool ok = true;
         for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
-            const LeafTask t = p.tasks[ti];
-            const int nsteps = (t.klen + KSTEP - 1) / KSTEP;
+            // Only the chunk count stays live across the K loop; the rest of
+            // the task record is re-read for the store (register budget).
+            const int nsteps = (p.tasks[ti].klen + KSTEP - 1) / KSTEP;
             const int nchunks = (nsteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
-            int64_t T[64];
+            int64_t T[EPI_COLS];
 #pragma unroll
-            for (int i = 0; i < 64; ++i) T[i] = 0;
+            for (int i = 0; i < EPI_COLS; ++i) T[i] = 0;
             for (int c = 0; c < nchunks; ++c) {
                 const bool last = c == nchunks - 1;
                 const uint32_t due = due_mask(c, last, C::NACC);
@@ -275,41 +311,41 @@ __global__ void __maxnreg__(200) leaf_tc_kernel(const __grid_constant__ LeafPara
                 }
                 accf_phase ^= 1u;
                 tc_fence_after();
-                if (due & 4u) drain_one<S, 2>(T, tbase, colbase, sh);
-                if (due & 2u) drain_one<S, 1>(T, tbase, colbase, sh);
-                if (due & 1u) drain_one<S, 0>(T, tbase, colbase, sh);
-                if (due & 8u) drain_one<S, 3>(T, tbase, colbase, sh);
+                if (due & 16u) drain_one<4>(T, tbase, colbase, sh);
+                if (due & 1u) drain_one<0>(T, tbase, colbase, sh);
+                if (due & 2u) drain_one<1>(T, tbase, colbase, sh);
+                if (due & 4u) drain_one<2>(T, tbase, colbase, sh);
+                if (due & 8u) drain_one<3>(T, tbase, colbase, sh);
             }
             if (!ok) break;
+            const LeafTask t = p.tasks[ti];
             if (row < t.rows) {
+                const int lim0 = t.diag ? min(t.cols, row + t.diag_off + 1) : t.cols;
+                const int lim = lim0 < 0 ? 0 : lim0;
                 if (t.kind == OUT_M_I64) {
                     int64_t *out = static_cast<int64_t *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) {
+                    for (int i = 0; i < EPI_COLS; ++i) {
                         const int col = colbase + i;
-                        if (col < t.cols) out[col] = T[i];
+                        if (col < lim) out[col] = T[i];
                     }
                 } else {
-                    const int er = t.eu >= 0 ? p.expo[t.eu + row] : 0;
+                    const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) + t.shift + (t.eu >= 0 ? p.expo[t.eu + row] : 0);
+                    const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                     if (t.kind == OUT_C_F64) {
                         double *out = static_cast<double *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
-                        for (int i = 0; i < 64; ++i) {
+                        for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
-                            if (col < t.cols && (!t.diag || col <= row)) {
-                                const int ec = t.ev >= 0 ? p.expo[t.ev + col] : 0;
-                                out[col] = static_cast<double>(T[i]) * exp2d(-38 + t.shift + er + ec);
-                            }
+                            if (col < lim)
+                                out[col] = static_cast<double>(T[i]) * exp2d(er + (ev ? ev[col] : 0));
                         }
                     } else {
                         float *out = static_cast<float *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
-                        for (int i = 0; i < 64; ++i) {
+                        for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
-                            if (col < t.cols && (!t.diag || col <= row)) {
-                                const int ec = t.ev >= 0 ? p.expo[t.ev + col] : 0;
-                                out[col] = __ll2float_rn(T[i]) * exp2f_(-38 + t.shift + er + ec);
-                            }
+                            if (col < lim) out[col] = __ll2float_rn(T[i]) * exp2f_(er + (ev ? ev[col] : 0));
                         }
                     }
                 }

@@ -112,7 +112,7 @@ struct Builder {
         return o.out_col;
     }
 
-    void plain_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols, bool diag) {
+    void plain_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
         LeafTask t{};
         t.fam_u = digits ? 0 : -1;
         t.fam_v = t.fam_u;
@@ -122,7 +122,10 @@ struct Builder {
         t.klen = static_cast<int32_t>(P.p.m);
         t.rows = static_cast<int32_t>(rows);
         t.cols = static_cast<int32_t>(cols);
-        t.diag = diag ? 1 : 0;
+        // The tile crosses the diagonal if its last column lies right of its
+        // first row: then only entries with c0 + col <= r0 + row are written.
+        t.diag = (c0 + cols - 1 > r0) ? 1 : 0;
+        t.diag_off = static_cast<int32_t>(r0 - c0);
         if (P.p.mode == MODE_F64) {
             t.kind = OUT_C_F64;
             t.eu = t.ev = -1;  // native FP64 works on A unscaled
@@ -135,34 +138,35 @@ struct Builder {
         t.out_off = r0 * P.p.ldc + c0;
         t.out_ld = P.p.ldc;
         P.tasks.push_back(t);
-        P.plain_madds += static_cast<double>(P.p.m) * TILE * TILE;
-        P.leaf_madds += static_cast<double>(P.p.m) * TILE * TILE;
+        P.plain_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
+        P.leaf_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
     }
 
-    // Lower-triangle tiles of the diagonal panel [c0, c0 + w).
+    // Tiles of the diagonal panel [c0, c0 + w) that hold lower-triangle entries.
     void diag_panel(int64_t c0, int64_t w) {
         P.n_panels++;
-        int64_t nt = ceil_div(w, TILE);
-        for (int64_t J = 0; J < nt; ++J)
-            for (int64_t K = 0; K <= J; ++K)
-                plain_tile(c0 + J * TILE, c0 + K * TILE, std::min<int64_t>(TILE, w - J * TILE),
-                           std::min<int64_t>(TILE, w - K * TILE), J == K);
+        for (int64_t J = 0; J < ceil_div(w, TILE_M); ++J) {
+            const int64_t rows = std::min<int64_t>(TILE_M, w - J * TILE_M);
+            for (int64_t K = 0; K * TILE_N < w && K * TILE_N <= J * TILE_M + rows - 1; ++K)
+                plain_tile(c0 + J * TILE_M, c0 + K * TILE_N, rows,
+                           std::min<int64_t>(TILE_N, w - K * TILE_N));
+        }
     }
 
     // Classical tiles of the off-diagonal block rows [r0, r0+p) x cols [c0, c0+q).
     void classical_block(int64_t r0, int64_t p, int64_t c0, int64_t q) {
-        for (int64_t J = 0; J < ceil_div(p, TILE); ++J)
-            for (int64_t K = 0; K < ceil_div(q, TILE); ++K)
-                plain_tile(r0 + J * TILE, c0 + K * TILE, std::min<int64_t>(TILE, p - J * TILE),
-                           std::min<int64_t>(TILE, q - K * TILE), false);
+        for (int64_t J = 0; J < ceil_div(p, TILE_M); ++J)
+            for (int64_t K = 0; K < ceil_div(q, TILE_N); ++K)
+                plain_tile(r0 + J * TILE_M, c0 + K * TILE_N, std::min<int64_t>(TILE_M, p - J * TILE_M),
+                           std::min<int64_t>(TILE_N, q - K * TILE_N));
     }
 
     int block_depth(int64_t p, int64_t q) const {
         int d = 0;
         int64_t pp = p, qq = q, mm = P.p.m;
         while (d < P.depth) {
+            if (pp < P.strassen_min || qq < P.strassen_min || pp < 2 || qq < 2 || mm < 2) break;
             int64_t np = (pp + 1) / 2, nq = (qq + 1) / 2, nm = (mm + 1) / 2;
-            if (np < P.p.strassen_min || nq < P.p.strassen_min || nm < 2) break;
             pp = np;
             qq = nq;
             mm = nm;
@@ -219,29 +223,29 @@ struct Builder {
             prod_off[r] = prod_elems;
             prod_elems += pn * qn;
             P.n_products++;
-            for (int64_t J = 0; J < ceil_div(pn, TILE); ++J) {
-                for (int64_t K = 0; K < ceil_div(qn, TILE); ++K) {
+            for (int64_t J = 0; J < ceil_div(pn, TILE_M); ++J) {
+                for (int64_t K = 0; K < ceil_div(qn, TILE_N); ++K) {
                     LeafTask t{};
                     t.fam_u = fam;
                     t.fam_v = fam;
-                    t.col_u = static_cast<int32_t>(ucol + J * TILE);
-                    t.col_v = static_cast<int32_t>(vcol + K * TILE);
+                    t.col_u = static_cast<int32_t>(ucol + J * TILE_M);
+                    t.col_v = static_cast<int32_t>(vcol + K * TILE_N);
                     t.k0 = 0;
                     t.klen = static_cast<int32_t>(rn);
-                    t.rows = static_cast<int32_t>(std::min<int64_t>(TILE, pn - J * TILE));
-                    t.cols = static_cast<int32_t>(std::min<int64_t>(TILE, qn - K * TILE));
+                    t.rows = static_cast<int32_t>(std::min<int64_t>(TILE_M, pn - J * TILE_M));
+                    t.cols = static_cast<int32_t>(std::min<int64_t>(TILE_N, qn - K * TILE_N));
                     t.diag = 0;
                     t.kind = digits ? OUT_M_I64 : OUT_M_F64;
                     t.shift = shift;
                     t.eu = t.ev = -1;
-                    t.out_off = prod_off[r] + J * TILE * qn + K * TILE;
+                    t.out_off = prod_off[r] + J * TILE_M * qn + K * TILE_N;
                     t.out_ld = qn;
                     P.tasks.push_back(t);
-                    P.leaf_madds += static_cast<double>(rn) * TILE * TILE;
+                    P.leaf_madds += static_cast<double>(rn) * TILE_M * TILE_N;
                 }
             }
         }
-        P.plain_madds += static_cast<double>(P.p.m) * ceil_div(p, TILE) * ceil_div(q, TILE) * TILE * TILE;
+        P.plain_madds += static_cast<double>(P.p.m) * ceil_div(p, TILE_M) * ceil_div(q, TILE_N) * TILE_M * TILE_N;
 
         // Result sums, one per (row region, column region) of the C block.
         for (int64_t ir = 0; ir < nsub; ++ir) {
@@ -266,6 +270,22 @@ struct Builder {
                         P.cterms.push_back({prod_off[r], static_cast<int32_t>(qn), w, prod_shift[r], 0});
                 }
                 c.nterms = static_cast<int32_t>(P.cterms.size()) - c.first_term;
+                // Sum the exact products in units 2^(smin + rshift) with the
+                // worst case below 2^62: |T_r| <= 1.004 K 2^T_BOUND_LOG2.
+                int smin = 1 << 20;
+                for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
+                    smin = std::min(smin, P.cterms[i].shift);
+                c.rshift = 0;
+                if (digits) {
+                    for (;;) {
+                        double bound = 0;
+                        for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
+                            bound += 1.004 * static_cast<double>(rn) *
+                                     std::ldexp(1.0, T_BOUND_LOG2 + P.cterms[i].shift - smin - c.rshift);
+                        if (bound < std::ldexp(1.0, 62)) break;
+                        c.rshift++;
+                    }
+                }
                 c.tile_base = P.comb_tiles;
                 P.comb_tiles += ceil_div(c.rows, 32) * ceil_div(c.cols, 32);
                 P.combs.push_back(c);
@@ -332,13 +352,13 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         P.cutoff = static_cast<int>(std::max<int64_t>(pp.n, 1));
     else
         P.cutoff = pp.cutoff > 0 ? pp.cutoff : static_cast<int>(std::max<int64_t>(pp.n / 4, 256));
-    // Exact int64 combine: |T_r| <= 1.01 K_r 2^38 per product, summed with
-    // shifts of up to 2 bits per Strassen level; keep the worst case < 2^62.
-    while (P.depth > 0) {
-        double K = std::ceil(static_cast<double>(pp.m) / std::pow(2.0, P.depth));
-        double bound = 1.01 * K * std::pow(2.0, 38 + 2 * P.depth) * std::pow(4.0, P.depth);
-        if (bound < std::pow(2.0, 62)) break;
-        P.depth--;
+    // A Strassen level on an N-wide block saves 1/8 of its leaf work but adds
+    // ~14 operand sums of (m/2) x (N/2); on GB300 the extra HBM traffic only
+    // pays for blocks of a few thousand columns (see the design notes).
+    P.strassen_min = pp.strassen_min > 0 ? pp.strassen_min : 4096;
+    if (pp.mode != MODE_F64 && pp.m > MAX_DIGIT_K) {
+        if (err) *err = "contraction length beyond the exact-accumulation limit";
+        return false;
     }
 
     Builder B(P);

@@ -9,9 +9,18 @@
 
 namespace ata {
 
-constexpr int TILE = 128;        // leaf output tile edge (rows and columns)
-constexpr int KSTEP = 32;        // contraction rows per pipeline stage
-constexpr int CHUNK_STEPS = 8;   // stages per exact-accumulation chunk (256 rows)
+constexpr int TILE = 128;        // column padding unit of operand families
+constexpr int TILE_M = 128;      // leaf output tile rows (U-operand columns)
+constexpr int TILE_N = 96;       // leaf output tile columns (V-operand columns)
+constexpr int KSTEP = 16;        // contraction rows per pipeline stage (one MMA K step)
+constexpr int CHUNK_STEPS = 4;   // stages per exact-accumulation chunk (64 rows)
+// The leaf's exact int64 sum T is in units of 2^-T_FRAC of the leading digit
+// product; |T| <= 1.004 * K * 2^T_BOUND_LOG2 for a contraction of K rows.
+constexpr int T_FRAC = 27;
+constexpr int T_BOUND_LOG2 = 43;
+constexpr int DIGIT_TOP_BITS = 8;   // first digit: |x_1| <= 2^8
+constexpr int DIGIT_BITS = 9;       // every further digit carries 9 bits
+constexpr int64_t MAX_DIGIT_K = int64_t(1) << 19;  // keeps |T| < 2^63
 constexpr int PREP_K = 64;       // prep tile: contraction rows
 constexpr int PREP_C = 64;       // prep tile: columns
 constexpr int MAX_FAMILIES = 6;  // operand families (tensor maps) per launch
@@ -58,11 +67,11 @@ struct LeafTask {
     int32_t col_u, col_v;   // first column of the tile's rows / columns
     int32_t k0, klen;       // contraction range
     int32_t rows, cols;     // valid output rows / columns (<= TILE)
-    int32_t diag;           // 1: diagonal tile, write only local col <= local row
+    int32_t diag;           // 1: tile crosses the diagonal (see diag_off)
     int32_t kind;           // OUT_* below
     int32_t shift;          // product unit exponent adjustment (t_u + t_v)
     int32_t eu, ev;         // exponent index of tile row 0 / column 0 (-1: none)
-    int32_t pad;
+    int32_t diag_off;       // with diag: write only where col <= row + diag_off
     int64_t out_off;        // element offset of the tile origin in the output
     int64_t out_ld;         // output leading dimension (elements)
 };
@@ -90,6 +99,8 @@ struct CombDesc {
     int32_t e_col0;      // A column of region column 0
     int32_t first_term, nterms;
     int64_t tile_base;   // prefix count of 32x32 combine tiles
+    int32_t rshift;      // products are summed in units 2^(min shift + rshift)
+    int32_t pad;
 };
 
 struct PlanParams {
@@ -98,12 +109,13 @@ struct PlanParams {
     int cutoff = 0;          // 0 = auto
     int depth = -1;          // -1 = auto
     int slices = 0;          // 0 = auto
-    int strassen_min = 256;  // smallest leaf-product width Strassen may produce
+    int strassen_min = 0;    // Strassen splits a (sub)block only while both its
+                             // sides are >= strassen_min (0 = auto)
 };
 
 struct Plan {
     PlanParams p;
-    int cutoff = 0, depth = 0, slices = 0;
+    int cutoff = 0, depth = 0, slices = 0, strassen_min = 0;
     int64_t n_panels = 0, n_blocks = 0, n_products = 0;
     std::vector<Family> families;       // [0] = plain digits of A (if used)
     std::vector<OpDesc> ops;

@@ -22,6 +22,7 @@ int main(int argc, char **argv) {
     pp.cutoff = std::atoi(argv[4]);
     pp.depth = std::atoi(argv[5]);
     pp.slices = std::atoi(argv[6]);
+    pp.strassen_min = argc > 7 ? std::atoi(argv[7]) : 1;
     Plan P;
     std::string err;
     if (!make_plan(pp, &P, &err)) {
@@ -39,7 +40,7 @@ int main(int argc, char **argv) {
         const int64_t r0 = t.out_off / ldc, c0 = t.out_off % ldc;
         for (int r = 0; r < t.rows; ++r)
             for (int c = 0; c < t.cols; ++c)
-                if (!t.diag || c <= r) cov[(r0 + r) * n + c0 + c]++;
+                if (!t.diag || c <= r + t.diag_off) cov[(r0 + r) * n + c0 + c]++;
     }
     for (const CombDesc &d : P.combs) {
         const int64_t r0 = d.c_off / ldc, c0 = d.c_off % ldc;

@@ -156,6 +156,18 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
         : "memory");
 }
 
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -172,6 +184,18 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t smem_addr) {
     d |= static_cast<uint64_t>(512 >> 4) << 32;                // [32,46) SBO = 512 B
     d |= static_cast<uint64_t>(1) << 46;                       // [46,48) descriptor version
     d |= static_cast<uint64_t>(4) << 61;                       // [61,64) swizzle: 64 B
+    return d;
+}
+
+// Same for the 32-byte swizzle: rows of 32 bytes (16 BF16 along K, one MMA
+// K step), 8-row core-matrix groups 256 bytes apart; 256-byte aligned tiles.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw32(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((smem_addr & 0x3FFFFu) >> 4);  // [0,14)  start address
+    d |= static_cast<uint64_t>(1) << 16;                       // [16,30) LBO (unused here)
+    d |= static_cast<uint64_t>(256 >> 4) << 32;                // [32,46) SBO = 256 B
+    d |= static_cast<uint64_t>(1) << 46;                       // [46,48) descriptor version
+    d |= static_cast<uint64_t>(6) << 61;                       // [61,64) swizzle: 32 B
     return d;
 }
 

@@ -66,8 +66,19 @@ def test_create_without_gpu_is_unsupported(lib):
 
 # ------------------------------------------------------------- planner ----
 
-def tiles(n):
-    return (n + 127) // 128
+TM, TN = 128, 96   # leaf tile: 128 rows (j) x 96 columns (k)
+
+
+def lower_tiles(n):
+    """Tiles of a TM x TN grid over an n x n matrix holding an entry k <= j."""
+    count = 0
+    for J in range(-(-n // TM)):
+        rows = min(TM, n - J * TM)
+        K = 0
+        while K * TN < n and K * TN <= J * TM + rows - 1:
+            count += 1
+            K += 1
+    return count
 
 
 @pytest.mark.parametrize("n", [1, 64, 128, 129, 255, 1000, 4096])
@@ -77,8 +88,7 @@ def test_plain_plan_is_all_lower_tiles(lib, n, mode):
     info = lib.plan_info(300, n, mode, h)
     # depth 0 is only chosen automatically for small n
     if info["depth"] == 0:
-        T = tiles(n)
-        assert info["tiles"] == T * (T + 1) // 2
+        assert info["tiles"] == lower_tiles(n)
         assert info["panels"] == 1 and info["products"] == 0
         assert info["leaf_madds"] == info["plain_madds"]
 
@@ -112,7 +122,7 @@ def test_recursion_structure(plan_cli, n, cutoff, depth):
     if depth == 0:
         # Strassen depth 0 is plain tiled AtA: one panel, all lower tiles.
         assert P["panels"] == 1 and P["blocks"] == 0 and P["products"] == 0
-        assert P["tiles"] == tiles(n) * (tiles(n) + 1) // 2
+        assert P["tiles"] == lower_tiles(n)
     else:
         assert P["panels"] == leaves(n)
         assert P["blocks"] == blocks(n)

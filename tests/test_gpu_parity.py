@@ -41,8 +41,9 @@ def is_f32(mode):
     return mode in (F32, F32_BF16)
 
 
-def run(h, A, mode, cutoff=0, depth=0, slices=0, sentinel=float("nan")):
-    h.set_config(cutoff, depth, slices)
+def run(h, A, mode, cutoff=0, depth=0, slices=0, sentinel=float("nan"), strassen_min=2):
+    # strassen_min=2: apply the requested Strassen depth even to small blocks
+    h.set_config(cutoff, depth, slices, strassen_min)
     dt = torch.float32 if is_f32(mode) else torch.float64
     n = A.shape[1]
     Ad = torch.from_numpy(np.ascontiguousarray(A)).to(dt).cuda()
@@ -226,7 +227,7 @@ def test_error_codes(h, ata):
 def test_nonfinite_input_reported(h):
     A = inputs.uniform(64, 32, seed=2)
     A[3, 5] = np.inf
-    h.set_config(0, 0, 0)
+    h.set_config(0, 0, 0, 0)
     Ad = torch.from_numpy(A).cuda()
     Cd = torch.zeros((32, 32), dtype=torch.float64, device="cuda")
     assert h.lower_ptr(64, 32, Ad.data_ptr(), 32, Cd.data_ptr(), 32, F64_EMU) == 0
@@ -258,7 +259,7 @@ def test_8192_square_sampled(h, mode, depth):
     A = inputs.uniform(m, n, seed=2110)
     if is_f32(mode):
         A = A.astype(np.float32)
-    C = run(h, A, mode, cutoff=2048, depth=depth, sentinel=0.0)
+    C = run(h, A, mode, cutoff=2048, depth=depth, sentinel=0.0, strassen_min=1024)
     j, k = sampled_pairs(n, 3000, seed=depth)
     A64 = np.asarray(A, np.float64)
     vals, dens = oracle.dot_pairs(np.ascontiguousarray(A64[:, j].T), np.ascontiguousarray(A64[:, k].T))
