@@ -12,32 +12,13 @@
 #include <tuple>
 #include <vector>
 
-#include "../../include/ata.h"
+#include "ata.h"
 #include "kernels.h"
 #include "plan.h"
 
 using namespace ata;
 
 namespace {
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    });
-    return fn;
-}
 
 using Key = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int, int, int>;
 
@@ -150,30 +131,9 @@ int bind_plan(ata_handle h, CachedPlan &cp) {
     LeafParams &lp = cp.lp;
     std::memset(&lp, 0, sizeof(lp));
     if (P.uses_digits()) {
-        EncodeTiledFn enc = get_encode_fn();
-        if (!enc) return fail(h, ATA_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
         for (size_t f = 0; f < P.families.size(); ++f) {
-            const Family &F = P.families[f];
-            if (F.cols == 0) continue;
-            cuuint64_t dims[3] = {static_cast<cuuint64_t>(F.K_pitch), static_cast<cuuint64_t>(F.cols),
-                                  static_cast<cuuint64_t>(P.slices)};
-            cuuint64_t strides[2] = {static_cast<cuuint64_t>(F.K_pitch * 2),
-                                     static_cast<cuuint64_t>(F.plane_elems * 2)};
-            cuuint32_t estr[3] = {1, 1, 1};
-            for (int side = 0; side < 2; ++side) {
-                cuuint32_t box[3] = {static_cast<cuuint32_t>(KSTEP),
-                                     static_cast<cuuint32_t>(side == 0 ? TILE_M : TILE_N),
-                                     static_cast<cuuint32_t>(P.slices)};
-                CUtensorMap *map = side == 0 ? &lp.maps_a[f] : &lp.maps_b[f];
-                CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h->ws + F.offset, dims, strides,
-                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) {
-                    h->last_error = "cuTensorMapEncodeTiled failed with CUresult " +
-                                    std::to_string(static_cast<int>(r));
-                    return ATA_ERR_CUDA;
-                }
-            }
+            lp.fam_base[f] = h->ws + P.families[f].offset;
+            lp.fam_ncb[f] = P.families[f].cols / BLOCK_COLS;
         }
     } else {
         for (size_t f = 0; f < P.families.size(); ++f) {

@@ -182,11 +182,21 @@ __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ 
     for (int it = 0; it < 16; ++it) sV[kr0 + 4 * it][cc] = V[it];
     __syncthreads();
 
+    // Write phase: the 64 x 64 tile is 4 contraction steps x 2 column blocks
+    // of 1 KB images per digit.  Image row r (operand column) holds 16
+    // contraction values in two 16-byte chunks; chunk c sits at position
+    // c ^ ((r >> 2) & 1) (the 32-byte swizzle of the leaf's shared memory).
     const Family fam = fams.f[od.family];
-    __nv_bfloat162 *planes = reinterpret_cast<__nv_bfloat162 *>(ws + fam.offset);
-    const int kp = threadIdx.x & 31;
-    for (int c = threadIdx.x >> 5; c < PREP_C; c += 8) {
-        int64_t v0 = sV[2 * kp][c], v1 = sV[2 * kp + 1][c];
+    const int64_t ncb = fam.cols / BLOCK_COLS;
+    uint8_t *base = ws + fam.offset;
+    const int r = threadIdx.x >> 3;   // image row (column within the block)
+    const int kp = threadIdx.x & 7;   // contraction pair within the step
+    const int in_img = r * 32 + (((kp >> 2) ^ ((r >> 2) & 1)) << 4) + ((kp & 3) << 2);
+#pragma unroll 1
+    for (int img = 0; img < (PREP_K / KSTEP) * (PREP_C / BLOCK_COLS); ++img) {
+        const int ks = img >> 1, cb = img & 1;
+        const int kk = ks * KSTEP + 2 * kp, c = cb * BLOCK_COLS + r;
+        int64_t v0 = sV[kk][c], v1 = sV[kk + 1][c];
         int x0[S], x1[S];
 #pragma unroll
         for (int q = S - 1; q >= 1; --q) {
@@ -199,15 +209,15 @@ __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ 
         }
         x0[0] = static_cast<int>(v0);
         x1[0] = static_cast<int>(v1);
-        const int64_t colg = od.out_col + c0 + c;
-        const int64_t e0 = colg * fam.K_pitch + k0 + 2 * kp;  // even
+        const int64_t kstep = (k0 / KSTEP) + ks;
+        const int64_t cblk = (od.out_col + c0) / BLOCK_COLS + cb;
 #pragma unroll
         for (int q = 0; q < S; ++q) {
             const float sc = exp2f_i(-DIGIT_BITS * q);
             __nv_bfloat162 val;
             val.x = __float2bfloat16_rn(static_cast<float>(x0[q]) * sc);
             val.y = __float2bfloat16_rn(static_cast<float>(x1[q]) * sc);
-            planes[(q * fam.plane_elems + e0) >> 1] = val;
+            *reinterpret_cast<__nv_bfloat162 *>(base + ((kstep * S + q) * ncb + cblk) * BLOCK_BYTES + in_img) = val;
         }
     }
 }

@@ -10,8 +10,8 @@ namespace ata {
 
 // Parameters shared by the leaf launches.
 struct LeafParams {
-    CUtensorMap maps_a[MAX_FAMILIES];  // per digit family: 32 x TILE_M x S boxes
-    CUtensorMap maps_b[MAX_FAMILIES];  // per digit family: 32 x TILE_N x S boxes
+    const uint8_t *fam_base[MAX_FAMILIES];  // digit families (1 KB images)
+    int64_t fam_ncb[MAX_FAMILIES];          // column blocks per family
     const LeafTask *tasks;
     int ntasks;
     int pad0;

@@ -15,20 +15,22 @@
 //   acc4: p + q >= 6 (the rest, weight <= 2^-36 of acc0's unit; not exact)
 // Each of acc0..acc3 holds integers (in its unit) of magnitude <= 2^24, which
 // FP32 represents exactly, and is drained at the interval shown into a
-// per-element int64 sum T in units of 2^-27 (acc4 is rounded to that unit).
-// The tile's value is T * 2^(-43 + shift + e_row + e_col).
+// per-element int64 sum T in units of 2^-(27 + h) (acc4 is rounded to that
+// unit); h = min(9, 19 - log2 K) extra bits keep short contractions as
+// accurate as long ones.  The tile's value is T * 2^(-43 - h + shift + e_row + e_col).
 //
 // Tile 128 x 96: five 96-column FP32 accumulators fit the 512 TMEM columns.
 // K step 16 (one MMA per digit pair per stage, 32-byte swizzle) keeps stages
 // small, so 4-10 of them are in flight.
 //
 // Pipeline (one CTA per SM, persistent over a static round-robin task list):
-//   warp 0       TMA producer: two 3-D boxes per stage (all S digit planes of
-//                a 128-row and a 96-row x 16-column slab).
+//   warp 0       TMA producer: per stage and digit, one bulk copy of the
+//                operand rows' 4 KB (A) and 3 KB (B) pre-swizzled images.
 //   warp 1       TMEM allocator + single-thread tcgen05.mma issuer.
-//   warps 4..11  epilogue: tcgen05.ld drains, int64 accumulation, stores.
-//   (warps 2, 3 idle: 12 warps keep the 4 SM sub-partitions balanced, which
-//    bounds the register budget at 168 per thread.)
+//   warps 4..15  epilogue: tcgen05.ld drains, int64 accumulation, stores
+//                (3 warps per TMEM lane quadrant, 32 columns each).
+//   (warps 2, 3 idle: 16 warps keep the 4 SM sub-partitions balanced at
+//    4 warps each, a budget of 128 registers per thread.)
 // The issuer and the epilogue visit the accumulators in the same fixed order
 // (4, 0, 1, 2, 3): the ones drained every chunk come last, so the tensor core
 // keeps working on the others while they are drained.
@@ -42,10 +44,10 @@
 namespace ata {
 namespace {
 
-constexpr int NUM_THREADS = 384;
+constexpr int NUM_THREADS = 512;
 constexpr int EPI_WARP0 = 4;
-constexpr int NUM_EPI = 256;
-constexpr int EPI_COLS = TILE_N / 2;                  // 48 columns per epilogue thread
+constexpr int NUM_EPI = 384;                          // 12 epilogue warps, 3 per lane quadrant
+constexpr int EPI_COLS = TILE_N / 3;                  // 32 columns per epilogue thread
 constexpr int A_SLICE_BYTES = TILE_M * KSTEP * 2;     // 4 KB
 constexpr int B_SLICE_BYTES = TILE_N * KSTEP * 2;     // 3 KB
 constexpr int MAX_ACC = 5;
@@ -148,39 +150,42 @@ __device__ __forceinline__ bool step_acc(IssueState &st, Shared *sh, uint32_t tm
     }
 }
 
-// Add one drained accumulator (16 columns) into T (units 2^-27).
+// Add one drained accumulator (16 columns) into T, kept in units of
+// 2^-(27 + h) of the leading digit product (h extra bits for short K).
 template <int ACC>
-__device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16]) {
+__device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int h, float fold_scale) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const float v = __uint_as_float(r[i]);
         if (ACC == 0) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v)) << 27;
+            T[i] += static_cast<int64_t>(__float2int_rn(v)) << (27 + h);
         } else if (ACC == 1) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 512.0f)) << 18;
+            T[i] += static_cast<int64_t>(__float2int_rn(v * 512.0f)) << (18 + h);
         } else if (ACC == 2) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 262144.0f)) << 9;
+            T[i] += static_cast<int64_t>(__float2int_rn(v * 262144.0f)) << (9 + h);
         } else if (ACC == 3) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 134217728.0f));
+            T[i] += static_cast<int64_t>(__float2int_rn(v * 134217728.0f)) << h;
         } else {
-            T[i] += __float2ll_rn(v * 134217728.0f);
+            T[i] += __float2ll_rn(v * fold_scale);
         }
     }
 }
 
+// Drain one accumulator: both TMEM loads are issued before a single wait,
+// and the accumulator is handed back to the MMA issuer before the (longer)
+// conversion work.
 template <int ACC>
-__device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh) {
-    uint32_t r[16];
-#pragma unroll
-    for (int c = 0; c < EPI_COLS / 16; ++c) {
-        tmem_ld_32x32b_x16(tbase + ACC * TILE_N + colbase + 16 * c, r);
-        tmem_ld_wait();
-        if (c == EPI_COLS / 16 - 1) {
-            tc_fence_before();
-            mbar_arrive(&sh->acce[ACC]);
-        }
-        absorb<ACC>(T + 16 * c, r);
-    }
+__device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh,
+                                          int h, float fold_scale) {
+    static_assert(EPI_COLS == 32, "two 16-column loads");
+    uint32_t r0[16], r1[16];
+    tmem_ld_32x32b_x16(tbase + ACC * TILE_N + colbase, r0);
+    tmem_ld_32x32b_x16(tbase + ACC * TILE_N + colbase + 16, r1);
+    tmem_ld_wait();
+    tc_fence_before();
+    mbar_arrive(&sh->acce[ACC]);
+    absorb<ACC>(T, r0, h, fold_scale);
+    absorb<ACC>(T + 16, r1, h, fold_scale);
 }
 
 template <int S>
@@ -222,6 +227,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
                 const LeafTask t = p.tasks[ti];
                 const int nsteps = (t.klen + KSTEP - 1) / KSTEP;
+                // Digit images: ((kstep * S + digit) * ncb + column block) KB; the
+                // tile's TILE_M (TILE_N) columns are 4 (3) consecutive blocks.
+                const uint8_t *ua = p.fam_base[t.fam_u] + static_cast<int64_t>(t.col_u / BLOCK_COLS) * BLOCK_BYTES;
+                const uint8_t *vb = p.fam_base[t.fam_v] + static_cast<int64_t>(t.col_v / BLOCK_COLS) * BLOCK_BYTES;
+                const int64_t ua_step = p.fam_ncb[t.fam_u] * BLOCK_BYTES;  // per digit plane
+                const int64_t vb_step = p.fam_ncb[t.fam_v] * BLOCK_BYTES;
                 for (int step = 0; step < nsteps; ++step) {
                     if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.status)) {
                         ok = false;
@@ -230,9 +241,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     uint8_t *a_dst = smem + stage * C::STAGE_BYTES;
                     uint8_t *b_dst = a_dst + S * A_SLICE_BYTES;
                     mbar_arrive_expect_tx(&sh->full[stage], C::STAGE_BYTES);
-                    const int k = t.k0 + step * KSTEP;
-                    tma_load_3d(a_dst, &p.maps_a[t.fam_u], &sh->full[stage], k, t.col_u, 0);
-                    tma_load_3d(b_dst, &p.maps_b[t.fam_v], &sh->full[stage], k, t.col_v, 0);
+                    const int64_t ks = (t.k0 / KSTEP) + step;
+#pragma unroll
+                    for (int q = 0; q < S; ++q) {
+                        bulk_load(a_dst + q * A_SLICE_BYTES, ua + (ks * S + q) * ua_step, A_SLICE_BYTES,
+                                  &sh->full[stage]);
+                        bulk_load(b_dst + q * B_SLICE_BYTES, vb + (ks * S + q) * vb_step, B_SLICE_BYTES,
+                                  &sh->full[stage]);
+                    }
                     if (++stage == C::STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -287,10 +303,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     } else if (warp >= EPI_WARP0) {
         // --------------------------------------------------- epilogue --
         const int q = warp & 3;                      // TMEM lane quadrant of this warp
-        const int half = (warp - EPI_WARP0) >> 2;    // which 48 columns
+        const int third = (warp - EPI_WARP0) >> 2;   // which 32 columns
         const int row = 32 * q + lane;               // tile row == TMEM lane
         const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16);
-        const int colbase = EPI_COLS * half;
+        const int colbase = EPI_COLS * third;
         uint32_t accf_phase = 0;
         bool ok = true;
         for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
@@ -298,6 +314,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             // the task record is re-read for the store (register budget).
             const int nsteps = (p.tasks[ti].klen + KSTEP - 1) / KSTEP;
             const int nchunks = (nsteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
+            const int h = p.tasks[ti].hbits;
+            const float fold_scale = __uint_as_float(static_cast<unsigned>(127 + 27 + h) << 23);
             int64_t T[EPI_COLS];
 #pragma unroll
             for (int i = 0; i < EPI_COLS; ++i) T[i] = 0;
@@ -311,11 +329,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 }
                 accf_phase ^= 1u;
                 tc_fence_after();
-                if (due & 16u) drain_one<4>(T, tbase, colbase, sh);
-                if (due & 1u) drain_one<0>(T, tbase, colbase, sh);
-                if (due & 2u) drain_one<1>(T, tbase, colbase, sh);
-                if (due & 4u) drain_one<2>(T, tbase, colbase, sh);
-                if (due & 8u) drain_one<3>(T, tbase, colbase, sh);
+                if (due & 16u) drain_one<4>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 1u) drain_one<0>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 2u) drain_one<1>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 4u) drain_one<2>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 8u) drain_one<3>(T, tbase, colbase, sh, h, fold_scale);
             }
             if (!ok) break;
             const LeafTask t = p.tasks[ti];
@@ -330,7 +348,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         if (col < lim) out[col] = T[i];
                     }
                 } else {
-                    const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) + t.shift + (t.eu >= 0 ? p.expo[t.eu + row] : 0);
+                    const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) - t.hbits + t.shift +
+                                   (t.eu >= 0 ? p.expo[t.eu + row] : 0);
                     const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                     if (t.kind == OUT_C_F64) {
                         double *out = static_cast<double *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;

@@ -135,6 +135,7 @@ struct Builder {
             t.ev = static_cast<int32_t>(c0);
         }
         t.shift = 0;
+        t.hbits = hbits_for(P.p.m);
         t.out_off = r0 * P.p.ldc + c0;
         t.out_ld = P.p.ldc;
         P.tasks.push_back(t);
@@ -218,7 +219,10 @@ struct Builder {
             int64_t ucol = add_op(fam, ut, pn);
             size_t ov = P.ops.size();
             int64_t vcol = add_op(fam, vt, qn);
-            int shift = P.ops[ou].t_shift + P.ops[ov].t_shift;
+            // Product unit: 2^(-43 - h + t_u + t_v); the combine sees it as
+            // 2^(-43 + shift) with shift = t_u + t_v - h.
+            const int hb = hbits_for(rn);
+            int shift = P.ops[ou].t_shift + P.ops[ov].t_shift - hb;
             prod_shift[r] = shift;
             prod_off[r] = prod_elems;
             prod_elems += pn * qn;
@@ -237,6 +241,7 @@ struct Builder {
                     t.diag = 0;
                     t.kind = digits ? OUT_M_I64 : OUT_M_F64;
                     t.shift = shift;
+                    t.hbits = hb;
                     t.eu = t.ev = -1;
                     t.out_off = prod_off[r] + J * TILE_M * qn + K * TILE_N;
                     t.out_ld = qn;
@@ -281,7 +286,8 @@ struct Builder {
                         double bound = 0;
                         for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
                             bound += 1.004 * static_cast<double>(rn) *
-                                     std::ldexp(1.0, T_BOUND_LOG2 + P.cterms[i].shift - smin - c.rshift);
+                                     std::ldexp(1.0, T_BOUND_LOG2 + hbits_for(rn) + P.cterms[i].shift -
+                                                         smin - c.rshift);
                         if (bound < std::ldexp(1.0, 62)) break;
                         c.rshift++;
                     }
@@ -298,7 +304,14 @@ struct Builder {
             diag_panel(c0, w);
             return;
         }
-        int64_t n1 = w / 2, n2 = w - n1;
+        // Split near the middle on a SPLIT_ALIGN boundary, so every diagonal
+        // panel and classical tile starts on a digit-image column block (the
+        // identity C = [C11 C12; C21 C22] holds for any split point).
+        int64_t n1 = (w / (2 * SPLIT_ALIGN)) * SPLIT_ALIGN, n2 = w - n1;
+        if (n1 == 0) {
+            diag_panel(c0, w);
+            return;
+        }
         recurse(c0, n1);
         recurse(c0 + n1, n2);
         P.n_blocks++;
@@ -372,6 +385,17 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     }
     if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
 
+    // Every digit-family tile must start on a column block: the leaf loads
+    // whole 1 KB images with bulk copies.
+    if (B.digits) {
+        for (const LeafTask &t : P.tasks) {
+            if (t.col_u % BLOCK_COLS != 0 || t.col_v % BLOCK_COLS != 0 || t.k0 % KSTEP != 0) {
+                if (err) *err = "internal: leaf tile not aligned to a digit-image block";
+                return false;
+            }
+        }
+    }
+
     // Workspace layout.
     int64_t off = 0;
     auto take = [&](int64_t bytes) {
@@ -382,6 +406,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     P.off_colmax = take(pp.n * 8);
     P.off_expo = take(pp.n * 4);
     for (Family &f : P.families) {
+        f.cols += TILE;  // padding: a leaf box may extend up to TILE columns past the last operand
         f.plane_elems = f.cols * f.K_pitch;
         int64_t bytes = B.digits ? f.plane_elems * 2 * P.slices : f.plane_elems * 8;
         f.offset = take(bytes);

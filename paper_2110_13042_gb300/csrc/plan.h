@@ -21,6 +21,9 @@ constexpr int T_BOUND_LOG2 = 43;
 constexpr int DIGIT_TOP_BITS = 8;   // first digit: |x_1| <= 2^8
 constexpr int DIGIT_BITS = 9;       // every further digit carries 9 bits
 constexpr int64_t MAX_DIGIT_K = int64_t(1) << 19;  // keeps |T| < 2^63
+constexpr int BLOCK_COLS = 32;   // digit-plane image: 32 columns x KSTEP rows = 1 KB
+constexpr int BLOCK_BYTES = BLOCK_COLS * KSTEP * 2;
+constexpr int SPLIT_ALIGN = 32;  // AtA column splits are multiples of this
 constexpr int PREP_K = 64;       // prep tile: contraction rows
 constexpr int PREP_C = 64;       // prep tile: columns
 constexpr int MAX_FAMILIES = 6;  // operand families (tensor maps) per launch
@@ -41,7 +44,10 @@ struct OpTerm {
 // Operand generator: writes
 //   U[k][c] = sum_t coef_t * A[row0_t + k][col0_t + c] * 2^-e(col0_t + c)
 // for k < K_pitch, c < P_pad (zero outside every term's extent) into the
-// family's planes: either `slices` BF16 digit planes (K-major, [q][col][k])
+// family: either `slices` BF16 digit planes, stored as 1 KB images of
+// 32 columns x 16 contraction rows in exactly the order the leaf kernel's
+// shared memory needs them (K-major rows of 32 bytes, 32-byte swizzle;
+// image (kstep, digit, colblock) at ((kstep * S + digit) * ncb + colblock) KB),
 // or one FP64 array ([k][col], row-major) for the native FP64 mode.
 struct OpDesc {
     int32_t family;
@@ -56,9 +62,9 @@ struct OpDesc {
 
 struct Family {
     int64_t K_pitch;     // contraction pitch in elements (multiple of PREP_K)
-    int64_t cols;        // total columns (multiple of TILE)
-    int64_t offset;      // byte offset of plane 0 in the workspace
-    int64_t plane_elems; // elements per plane = cols * K_pitch
+    int64_t cols;        // total columns (multiple of TILE, plus TILE of padding)
+    int64_t offset;      // byte offset of the family in the workspace
+    int64_t plane_elems; // elements per digit plane = cols * K_pitch
 };
 
 // One leaf output tile (TILE x TILE), all digit pairs (or one FP64 product).
@@ -74,7 +80,19 @@ struct LeafTask {
     int32_t diag_off;       // with diag: write only where col <= row + diag_off
     int64_t out_off;        // element offset of the tile origin in the output
     int64_t out_ld;         // output leading dimension (elements)
+    int32_t hbits;          // extra fraction bits of T for short contractions
+    int32_t pad;
 };
+
+// Extra fraction bits of the leaf's int64 sum for a contraction of K rows:
+// T is kept in units of 2^-(T_FRAC + h) of the leading digit product, which
+// stays below 2^63 while K * 2^(T_BOUND_LOG2 + h) < 2^62.
+inline int hbits_for(int64_t K) {
+    int lg = 0;
+    while ((int64_t(1) << lg) < K) ++lg;
+    int h = 19 - lg;
+    return h < 0 ? 0 : (h > 9 ? 9 : h);
+}
 
 enum OutKind : int {
     OUT_C_F64 = 0,   // double into C, scaled by 2^(e_row + e_col)

@@ -112,12 +112,20 @@ def plan_cli(lib):
 @pytest.mark.parametrize("depth", [0, 1, 2])
 def test_recursion_structure(plan_cli, n, cutoff, depth):
     P = plan_cli(4096, n, 1, cutoff, depth)
-    # Panels: the number of leaves of the floor/ceil column recursion.
+    # Panels: the leaves of the column recursion; the split point is the
+    # largest multiple of 32 not above w/2 (a panel if that is 0).
+    def split(w):
+        return (w // 64) * 32
+
     def leaves(w):
-        return 1 if w <= cutoff else leaves(w // 2) + leaves(w - w // 2)
+        if w <= cutoff or split(w) == 0:
+            return 1
+        return leaves(split(w)) + leaves(w - split(w))
 
     def blocks(w):
-        return 0 if w <= cutoff else 1 + blocks(w // 2) + blocks(w - w // 2)
+        if w <= cutoff or split(w) == 0:
+            return 0
+        return 1 + blocks(split(w)) + blocks(w - split(w))
 
     if depth == 0:
         # Strassen depth 0 is plain tiled AtA: one panel, all lower tiles.
