@@ -153,6 +153,31 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out);
 int ata_set_timing(ata_handle h, int enable);
 int ata_phase_times(ata_handle h, double *out);
 
+/* Allocation-free variant of ata_lower, for callers that cannot allocate
+ * device memory when they need the product (inside a CUDA-graph capture they
+ * do not control, under a framework memory pool that forbids side
+ * allocations, or in a service that must not call cudaMalloc after start-up).
+ * The paper has no counterpart: this is a deployment convenience.
+ *
+ * Computes low(C) <- low(A^T A) exactly like ata_lower with
+ * strassen_depth = 0 (plain tiled, same kernels and digit count) for dtype
+ * ATA_F64_EMU, ATA_F32 or ATA_F32_BF16 (others: ATA_ERR_DTYPE).  Arguments
+ * are as for ata_lower; there is no handle.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine: its scratch is one fixed 32 MiB device array
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  Problems whose scratch (column exponents, task tables and
+ * digit planes: about 2 * slices * roundup(m, 64) * (roundup(n, 128) + 128)
+ * bytes) exceeds 32 MiB return ATA_ERR_UNSUPPORTED.
+ *
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (the call clears what must start at zero): calls that overlap on the GPU
+ * race, so serialise them (one stream, or events).  Device-side wait
+ * timeouts end the kernels but are not reported (there is no handle). */
+int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t lda,
+                      void *C, int64_t ldc, int dtype, void *stream);
+
 /* Version of this ABI (major * 10000 + minor * 100 + patch). */
 int ata_version(void);
 

@@ -50,6 +50,8 @@ def load():
     L.ata_status_string.argtypes = [ip]
     L.ata_status_string.restype = ctypes.c_char_p
     L.ata_plan_info.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64)]
+    L.ata_lower_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, ip, vp]
+    L.ata_lower_noalloc.restype = ip
     L.ata_last_error.argtypes = [vp]
     L.ata_last_error.restype = ctypes.c_char_p
     L.ata_set_timing.argtypes = [vp, ip]
@@ -90,6 +92,12 @@ def plan_info(m: int, n: int, dtype: int, handle: "Handle | None" = None) -> dic
     _check(load().ata_plan_info(handle._h if handle else None, int(m), int(n), int(dtype), out),
            "ata_plan_info")
     return dict(zip(PLAN_FIELDS, (int(v) for v in out)))
+
+
+def lower_noalloc_ptr(m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:
+    """ata_lower_noalloc through the C ABI; returns the status code."""
+    return int(load().ata_lower_noalloc(int(m), int(n), A_ptr, int(lda), C_ptr, int(ldc), int(dtype),
+                                        _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):

@@ -19,7 +19,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libata.so")
 
-CUDA_UNITS = ["ata_api.cu", "kernels.cu", "leaf_tc.cu"]
+CUDA_UNITS = ["ata_api.cu", "kernels.cu", "leaf_tc.cu", "noalloc.cu"]
 CXX_UNITS = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

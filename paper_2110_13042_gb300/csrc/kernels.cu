@@ -540,3 +540,40 @@ cudaError_t launch_zero_lower(void *C, int64_t n, int64_t ldc, bool is_f32, cuda
 }
 
 }  // namespace ata
+
+namespace ata {
+
+// Prep launch from explicit tables (used by the allocation-free entry point,
+// whose tables live in its fixed device scratch rather than in a plan).
+cudaError_t launch_prep_digits_raw(int slices, const void *A, bool is_f32, int64_t lda, const int *expo,
+                                   const OpDesc *ops, int nops, const OpTerm *terms, const Family &fam0,
+                                   int64_t prep_tiles, uint8_t *ws, cudaStream_t s) {
+    if (prep_tiles <= 0) return cudaSuccess;
+    if (prep_tiles > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+    Families F{};
+    F.f[0] = fam0;
+    const unsigned g = static_cast<unsigned>(prep_tiles);
+#define ATA_PREP_RAW(SS)                                                                                   \
+    case SS:                                                                                               \
+        if (is_f32)                                                                                        \
+            prep_digits_kernel<SS, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), lda, expo, ops, \
+                                                             nops, terms, F, ws);                          \
+        else                                                                                               \
+            prep_digits_kernel<SS, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), lda, expo,    \
+                                                              ops, nops, terms, F, ws);                    \
+        break;
+    switch (slices) {
+        ATA_PREP_RAW(1)
+        ATA_PREP_RAW(2)
+        ATA_PREP_RAW(3)
+        ATA_PREP_RAW(4)
+        ATA_PREP_RAW(5)
+        ATA_PREP_RAW(6)
+        ATA_PREP_RAW(7)
+        default: return cudaErrorInvalidValue;
+    }
+#undef ATA_PREP_RAW
+    return cudaGetLastError();
+}
+
+}  // namespace ata

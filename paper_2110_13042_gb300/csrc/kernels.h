@@ -36,6 +36,11 @@ cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s)
 cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
                            const int *expo, cudaStream_t s);
 cudaError_t launch_zero_lower(void *C, int64_t n, int64_t ldc, bool is_f32, cudaStream_t s);
+// Launches from explicit tables (allocation-free entry point).
+cudaError_t launch_prep_digits_raw(int slices, const void *A, bool is_f32, int64_t lda, const int *expo,
+                                   const OpDesc *ops, int nops, const OpTerm *terms, const Family &fam0,
+                                   int64_t prep_tiles, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_leaf_tc_raw(int slices, const LeafParams &lp, int ntasks, int num_sms, cudaStream_t s);
 // Shared-memory bytes the tcgen05 leaf kernel needs for `slices` digits.
 int leaf_tc_smem_bytes(int slices);
 

@@ -426,3 +426,33 @@ cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cud
 }
 
 }  // namespace ata
+
+namespace ata {
+
+// Leaf launch from an explicit task count (used by the allocation-free entry
+// point).  Sets the shared-memory attribute on every call.
+cudaError_t launch_leaf_tc_raw(int slices, const LeafParams &lp, int ntasks, int num_sms, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    const int grid = ntasks < num_sms ? ntasks : num_sms;
+#define ATA_LEAF_RAW(SS)                                                                                     \
+    case SS: {                                                                                               \
+        cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             Cfg<SS>::SMEM_BYTES);                                           \
+        if (e != cudaSuccess) return e;                                                                      \
+        leaf_tc_kernel<SS><<<grid, NUM_THREADS, Cfg<SS>::SMEM_BYTES, s>>>(lp);                              \
+        return cudaGetLastError();                                                                           \
+    }
+    switch (slices) {
+        ATA_LEAF_RAW(1)
+        ATA_LEAF_RAW(2)
+        ATA_LEAF_RAW(3)
+        ATA_LEAF_RAW(4)
+        ATA_LEAF_RAW(5)
+        ATA_LEAF_RAW(6)
+        ATA_LEAF_RAW(7)
+        default: return cudaErrorInvalidValue;
+    }
+#undef ATA_LEAF_RAW
+}
+
+}  // namespace ata
