@@ -42,7 +42,7 @@ DTYPE_DESC = {0: "f64 (DMMA)", 1: "bf16 digits x fp32 acc -> int64 (fp64-accurat
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f64_emu", choices=list(MODES))
@@ -76,24 +76,34 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host time, csv line)
         self.t = None
+        self.window = None
 
-    def start(self):
+    def start(self, warm_s: float = 5.0):
+        """Start sampling every 100 ms; return once the first sample arrived
+        (nvidia-smi start-up must not eat the timed region)."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                 "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < warm_s and self.proc.poll() is None:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t_begin: float, t_end: float):
+        """Host-time bounds of the timed region."""
+        self.window = (t_begin, t_end)
 
     def stop(self):
         if not self.proc:
@@ -107,7 +117,14 @@ class ClockSampler:
             self.t.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.window:
+            inside = [l for t, l in lines if self.window[0] <= t <= self.window[1]]
+            # a sample taken up to 150 ms after the end still reflects the region
+            lines = inside or [l for t, l in lines if self.window[0] <= t <= self.window[1] + 0.15]
+        else:
+            lines = [l for _, l in lines]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -249,7 +266,9 @@ def main():
     if rc != 0:
         raise RuntimeError(f"ata_sync: {rc}")
     clocks.start()
+    t_begin = time.time()
     ms = timed(step, args.steps, 0)
+    clocks.mark(t_begin, time.time())
     clk = clocks.stop()
     rc = h.sync(stream)
     if rc != 0:
