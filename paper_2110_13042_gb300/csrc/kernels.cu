@@ -135,6 +135,85 @@ __device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t ti
     return lo;
 }
 
+// round(a * 2^sh) (half away from zero) without branches, for |a * 2^sh| <=
+// 2^F (guaranteed by the column exponents).  With a = M 2^s' and s = s' + sh
+// <= P = max(F - mantissa bits, 0): r = (M 2^(P+1) + 2^u) >> (u + 1), u = P - s,
+// clamped to 62 (the shifted mantissa stays below 2^62, so a clamped u gives
+// 0, as the exact value < 1/2 requires).
+template <int F, typename T>
+struct FastFixed {
+    static constexpr int MB = sizeof(T) == 8 ? 52 : 23;
+    static constexpr int P = F - MB > 0 ? F - MB : 0;
+    static constexpr bool ok = MB + 1 + P + 1 <= 62;
+};
+
+template <int F>
+__device__ __forceinline__ int64_t fixed_of_fast(double a, int sh) {
+    constexpr int P = FastFixed<F, double>::P;
+    const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(a));
+    const int eb = static_cast<int>((bits >> 52) & 0x7FF);
+    const uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+    const uint64_t M = eb ? (mant | (1ull << 52)) : mant;
+    const int s = (eb ? eb - 1075 : -1074) + sh;
+    const int u = min(max(P - s, 0), 62);
+    const uint64_t r = ((M << (P + 1)) + (1ull << u)) >> (u + 1);
+    return (bits >> 63) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+}
+
+template <int F>
+__device__ __forceinline__ int64_t fixed_of_fast(float a, int sh) {
+    constexpr int P = FastFixed<F, float>::P;
+    const uint32_t bits = __float_as_uint(a);
+    const int eb = static_cast<int>((bits >> 23) & 0xFF);
+    const uint64_t mant = bits & 0x7FFFFFu;
+    const uint64_t M = eb ? (mant | 0x800000u) : mant;
+    const int s = (eb ? eb - 150 : -149) + sh;
+    const int u = min(max(P - s, 0), 62);
+    const uint64_t r = ((M << (P + 1)) + (1ull << u)) >> (u + 1);
+    return (bits >> 31) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+}
+
+// Digit q of w = V + sum_{j < S-1} 256 * 512^j as the BF16-exact float
+// x_q * 2^(-9 (q - 1)).  Adding that constant turns the balanced digits of V
+// into plain 9-bit fields of w: x = field - 256 for the S - 1 low digits, and
+// the top digit x_1 is w >> 9 (S - 1).  Both are built from their bits: the
+// field is or-ed into the mantissa of 2^23 and one exact FMA removes 2^23 + 256
+// and applies the digit's power-of-two scale.
+template <int S, int Q>
+__device__ __forceinline__ float digit_value(int64_t w) {
+    if constexpr (Q == 0) {
+        const int x = static_cast<int>(w >> (DIGIT_BITS * (S - 1)));  // |x| <= 256
+        return __int_as_float(0x4B400000 + x) - 12582912.0f;         // 1.5 * 2^23
+    } else {
+        constexpr int J = S - 1 - Q;  // field index from the least significant
+        const uint32_t f = static_cast<uint32_t>(w >> (DIGIT_BITS * J)) & 511u;
+        constexpr float sc = 1.0f / static_cast<float>(1ull << (DIGIT_BITS * Q));
+        return fmaf(__uint_as_float(0x4B000000u | f), sc, -8388864.0f * sc);
+    }
+}
+
+template <int S, int Q>
+__device__ __forceinline__ void store_digit_row(const int64_t (&w)[KSTEP], uint8_t *img_row, int swz) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(digit_value<S, Q>(w[2 * i]), digit_value<S, Q>(w[2 * i + 1]));
+        pk[i] = *reinterpret_cast<const uint32_t *>(&v);
+    }
+    // chunk h (contraction values 8h .. 8h + 7) sits at 16-byte slot h ^ swz
+    *reinterpret_cast<uint4 *>(img_row + (swz << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4 *>(img_row + ((swz ^ 1) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+template <int S, int Q = 0>
+__device__ __forceinline__ void store_digits(const int64_t (&w)[KSTEP], uint8_t *row0, int64_t plane_step,
+                                             int swz) {
+    if constexpr (Q < S) {
+        store_digit_row<S, Q>(w, row0 + Q * plane_step, swz);
+        store_digits<S, Q + 1>(w, row0, plane_step, swz);
+    }
+}
+
 // Digit planes.  For operand o and its 64 x 64 tile (k0, c0):
 //   V[k][c] = sum_t coef_t * round(a(row0_t + k, col0_t + c) * 2^(F - t - e))
 // with F = 8 + 9 (S - 1) fraction bits, exact in int64.  V is then written as
@@ -142,15 +221,20 @@ __device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t ti
 // V = sum_q x_q 2^(9 (S - q)); digit q is stored as the BF16 value
 // x_q * 2^(-9 (q - 1)) (exact: at most 8 significant bits), K-major: plane q,
 // column c, contraction k.
+// Read phase: each warp loads 32 consecutive columns of one row (coalesced);
+// all 16 loads of a term are issued before the column exponent is needed.
+// Write phase: thread (c, ks) owns column c of contraction step ks and writes
+// its 32-byte image row of every digit plane as two 16-byte stores, so one
+// warp fills each 1 KB image.  Blocks are persistent (grid-stride over the
+// tiles) and keep the operand tables in shared memory when they fit, so a
+// tile starts with no dependent global loads before its data loads.
+constexpr int PREP_SMEM_OPS = 64;
+constexpr int PREP_SMEM_TERMS = 128;
+
 template <int S, typename T>
-__global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
-                                                          const int *__restrict__ expo,
-                                                          const OpDesc *__restrict__ ops, int nops,
-                                                          const OpTerm *__restrict__ terms,
-                                                          Families fams, uint8_t *ws) {
-    __shared__ int64_t sV[PREP_K][PREP_C + 1];
-    const int64_t tile = blockIdx.x;
-    const OpDesc od = ops[find_desc(ops, nops, tile)];
+__device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
+                                          const OpDesc &od, const OpTerm *terms, int64_t tile,
+                                          const Families &fams, uint8_t *ws, int64_t (*sV)[PREP_C + 1]) {
     const int64_t local = tile - od.tile_base;
     const int tiles_k = od.K_pitch / PREP_K;
     const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
@@ -165,61 +249,84 @@ __global__ void __launch_bounds__(256) prep_digits_kernel(const T *__restrict__ 
     for (int t = 0; t < od.nterms; ++t) {
         const OpTerm tm = terms[od.first_term + t];
         const int c = c0 + cc;
-        if (c < tm.cols) {
-            const int sh = F - od.t_shift - expo[tm.col0 + c];
-            const T *col = A + tm.col0 + c;
+        const bool cvalid = c < tm.cols;
+        const T *col = A + tm.col0 + c;
+        T raw[16];
 #pragma unroll
-            for (int it = 0; it < 16; ++it) {
-                const int k = k0 + kr0 + 4 * it;
-                if (k < tm.rows) {
-                    const int64_t v = fixed_of(col[(tm.row0 + k) * lda], sh);
-                    V[it] += tm.coef > 0 ? v : -v;
-                }
-            }
+        for (int it = 0; it < 16; ++it) {
+            const int k = k0 + kr0 + 4 * it;
+            raw[it] = (cvalid && k < tm.rows) ? col[(tm.row0 + k) * lda] : T(0);
+        }
+        const int sh = cvalid ? F - od.t_shift - expo[tm.col0 + c] : 0;
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {
+            int64_t v;
+            if constexpr (FastFixed<F, T>::ok)
+                v = fixed_of_fast<F>(raw[it], sh);
+            else
+                v = fixed_of(raw[it], sh);
+            V[it] += tm.coef > 0 ? v : -v;
         }
     }
 #pragma unroll
     for (int it = 0; it < 16; ++it) sV[kr0 + 4 * it][cc] = V[it];
     __syncthreads();
 
-    // Write phase: the 64 x 64 tile is 4 contraction steps x 2 column blocks
-    // of 1 KB images per digit.  Image row r (operand column) holds 16
-    // contraction values in two 16-byte chunks; chunk c sits at position
-    // c ^ ((r >> 2) & 1) (the 32-byte swizzle of the leaf's shared memory).
     const Family fam = fams.f[od.family];
     const int64_t ncb = fam.cols / BLOCK_COLS;
-    uint8_t *base = ws + fam.offset;
-    const int r = threadIdx.x >> 3;   // image row (column within the block)
-    const int kp = threadIdx.x & 7;   // contraction pair within the step
-    const int in_img = r * 32 + (((kp >> 2) ^ ((r >> 2) & 1)) << 4) + ((kp & 3) << 2);
-#pragma unroll 1
-    for (int img = 0; img < (PREP_K / KSTEP) * (PREP_C / BLOCK_COLS); ++img) {
-        const int ks = img >> 1, cb = img & 1;
-        const int kk = ks * KSTEP + 2 * kp, c = cb * BLOCK_COLS + r;
-        int64_t v0 = sV[kk][c], v1 = sV[kk + 1][c];
-        int x0[S], x1[S];
+    const int c = threadIdx.x & 63;    // operand column within the tile
+    const int ks = threadIdx.x >> 6;   // contraction step within the tile
+    const int r = c & (BLOCK_COLS - 1);
+    constexpr int64_t CADD = [] {
+        int64_t v = 0;
+        for (int j = 0; j < S - 1; ++j) v += int64_t(256) << (DIGIT_BITS * j);
+        return v;
+    }();
+    int64_t w[KSTEP];
 #pragma unroll
-        for (int q = S - 1; q >= 1; --q) {
-            const int d0 = static_cast<int>((v0 + 256) & 511) - 256;
-            const int d1 = static_cast<int>((v1 + 256) & 511) - 256;
-            x0[q] = d0;
-            x1[q] = d1;
-            v0 = (v0 - d0) >> DIGIT_BITS;
-            v1 = (v1 - d1) >> DIGIT_BITS;
-        }
-        x0[0] = static_cast<int>(v0);
-        x1[0] = static_cast<int>(v1);
-        const int64_t kstep = (k0 / KSTEP) + ks;
-        const int64_t cblk = (od.out_col + c0) / BLOCK_COLS + cb;
-#pragma unroll
-        for (int q = 0; q < S; ++q) {
-            const float sc = exp2f_i(-DIGIT_BITS * q);
-            __nv_bfloat162 val;
-            val.x = __float2bfloat16_rn(static_cast<float>(x0[q]) * sc);
-            val.y = __float2bfloat16_rn(static_cast<float>(x1[q]) * sc);
-            *reinterpret_cast<__nv_bfloat162 *>(base + ((kstep * S + q) * ncb + cblk) * BLOCK_BYTES + in_img) = val;
-        }
+    for (int i = 0; i < KSTEP; ++i) w[i] = sV[ks * KSTEP + i][c] + CADD;
+    const int64_t kstep = (k0 / KSTEP) + ks;
+    const int64_t cblk = (od.out_col + c0 + c) / BLOCK_COLS;
+    uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
+    store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
+    __syncthreads();  // sV is reused by the block's next tile
+}
+
+template <int S, typename T>
+__global__ void __launch_bounds__(256, 3) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
+                                                             const int *__restrict__ expo,
+                                                             const OpDesc *__restrict__ ops, int nops,
+                                                             const OpTerm *__restrict__ terms, int nterms,
+                                                             int64_t ntiles, Families fams, uint8_t *ws) {
+    __shared__ int64_t sV[PREP_K][PREP_C + 1];
+    __shared__ OpDesc s_ops[PREP_SMEM_OPS];
+    __shared__ OpTerm s_terms[PREP_SMEM_TERMS];
+    const bool cached = nops <= PREP_SMEM_OPS && nterms <= PREP_SMEM_TERMS;
+    if (cached) {
+        for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops[i];
+        for (int i = threadIdx.x; i < nterms; i += blockDim.x) s_terms[i] = terms[i];
+        __syncthreads();
     }
+    const OpDesc *o = cached ? s_ops : ops;
+    const OpTerm *tt = cached ? s_terms : terms;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const OpDesc od = o[find_desc(o, nops, tile)];
+        prep_tile<S, T>(A, lda, expo, od, tt, tile, fams, ws, sV);
+    }
+}
+
+// Persistent grid: three 256-thread blocks per SM (register bound).
+static unsigned prep_grid(int64_t ntiles) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!sms[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = n > 0 ? n : 1;
+    }
+    const int64_t cap = 3 * static_cast<int64_t>(sms[dev]);
+    return static_cast<unsigned>(ntiles < cap ? ntiles : cap);
 }
 
 // Native FP64 operands: U[k][c] = sum_t coef_t * a * 2^-e  (FP64, row-major
@@ -467,13 +574,14 @@ static void prep_digits_dispatch(const Plan &P, const void *A, bool is_f32, cons
                                  cudaStream_t s) {
     const OpDesc *ops = reinterpret_cast<const OpDesc *>(tables + P.t_ops);
     const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
-    const unsigned g = static_cast<unsigned>(P.prep_tiles);
+    const unsigned g = prep_grid(P.prep_tiles);
+    const int nops = static_cast<int>(P.ops.size()), nterms = static_cast<int>(P.terms.size());
     if (is_f32)
-        prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo,
-                                                        ops, static_cast<int>(P.ops.size()), terms, F, ws);
+        prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo, ops, nops,
+                                                        terms, nterms, P.prep_tiles, F, ws);
     else
-        prep_digits_kernel<S, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, expo,
-                                                         ops, static_cast<int>(P.ops.size()), terms, F, ws);
+        prep_digits_kernel<S, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, expo, ops,
+                                                         nops, terms, nterms, P.prep_tiles, F, ws);
 }
 
 cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *expo,
@@ -552,15 +660,15 @@ cudaError_t launch_prep_digits_raw(int slices, const void *A, bool is_f32, int64
     if (prep_tiles > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
     Families F{};
     F.f[0] = fam0;
-    const unsigned g = static_cast<unsigned>(prep_tiles);
+    const unsigned g = prep_grid(prep_tiles);
 #define ATA_PREP_RAW(SS)                                                                                   \
     case SS:                                                                                               \
         if (is_f32)                                                                                        \
             prep_digits_kernel<SS, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), lda, expo, ops, \
-                                                             nops, terms, F, ws);                          \
+                                                             nops, terms, 1, prep_tiles, F, ws);           \
         else                                                                                               \
             prep_digits_kernel<SS, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), lda, expo,    \
-                                                              ops, nops, terms, F, ws);                    \
+                                                              ops, nops, terms, 1, prep_tiles, F, ws);     \
         break;
     switch (slices) {
         ATA_PREP_RAW(1)
