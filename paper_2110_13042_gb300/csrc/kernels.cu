@@ -495,10 +495,10 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
 #pragma unroll
         for (int i = 0; i < KT / 2; ++i) {
             const int kk = lk + 2 * i;
-            const int64_t k = static_cast<int64_t>(t.k0) + k0 + kk;
+            const int64_t ku = static_cast<int64_t>(t.k0) + k0 + kk, kv = static_cast<int64_t>(t.k0v) + k0 + kk;
             const bool kin = (k0 + kk) < t.klen;
-            Us[kk][lc] = (kin && lc < t.rows) ? U[k * ldu + t.col_u + lc] : 0.0;
-            if (lc < TILE_N) Vs[kk][lc] = (kin && lc < t.cols) ? V[k * ldv + t.col_v + lc] : 0.0;
+            Us[kk][lc] = (kin && lc < t.rows) ? U[ku * ldu + t.col_u + lc] : 0.0;
+            if (lc < TILE_N) Vs[kk][lc] = (kin && lc < t.cols) ? V[kv * ldv + t.col_v + lc] : 0.0;
         }
         __syncthreads();
 #pragma unroll

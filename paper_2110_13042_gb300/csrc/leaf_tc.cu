@@ -274,12 +274,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     uint8_t *a_dst = smem + stage * C::STAGE_BYTES;
                     uint8_t *b_dst = a_dst + S * A_SLICE_BYTES;
                     mbar_arrive_expect_tx(&sh->full[stage], C::STAGE_BYTES);
-                    const int64_t ks = (t.k0 / KSTEP) + step;
+                    const int64_t ku = (t.k0 / KSTEP) + step, kv = (t.k0v / KSTEP) + step;
 #pragma unroll
                     for (int q = 0; q < S; ++q) {
-                        bulk_load(a_dst + q * A_SLICE_BYTES, ua + (ks * S + q) * ua_step, A_SLICE_BYTES,
+                        bulk_load(a_dst + q * A_SLICE_BYTES, ua + (ku * S + q) * ua_step, A_SLICE_BYTES,
                                   &sh->full[stage]);
-                        bulk_load(b_dst + q * B_SLICE_BYTES, vb + (ks * S + q) * vb_step, B_SLICE_BYTES,
+                        bulk_load(b_dst + q * B_SLICE_BYTES, vb + (kv * S + q) * vb_step, B_SLICE_BYTES,
                                   &sh->full[stage]);
                     }
                     if (++stage == C::STAGES) {

@@ -77,6 +77,7 @@ int log2_ceil(int64_t x) {
 struct Builder {
     Plan &P;
     bool digits;
+    bool reuse_quadrants = true;
     int64_t prod_elems = 0;
 
     explicit Builder(Plan &p) : P(p), digits(p.p.mode != MODE_F64) {}
@@ -176,6 +177,35 @@ struct Builder {
         return d;
     }
 
+    // Where a Strassen product reads one operand.
+    struct Operand {
+        int fam;
+        int64_t col, k0;
+        int t_shift;
+    };
+
+    // A Strassen operand.  A single +1 term whose region is aligned to the
+    // digit images, and whose zero padding (if any) lies beyond the end of A,
+    // is read straight from the planes of A (family 0) at its row and column
+    // offsets; any other operand gets its own planes in family `fam`.
+    Operand operand(int fam, const std::vector<OpTerm> &tt, int64_t nominal_cols, int64_t rn) {
+        if (digits && reuse_quadrants && tt.size() == 1 && tt[0].coef == 1) {
+            const OpTerm &t = tt[0];
+            const Family &f0 = P.families[0];
+            const int64_t f0_cols = round_up(std::max<int64_t>(P.p.n, 1), TILE) + TILE;
+            const bool rows_ok = t.rows == rn || (t.row0 + t.rows == P.p.m && t.row0 + rn <= f0.K_pitch);
+            const bool cols_ok = t.cols == nominal_cols || t.col0 + t.cols == P.p.n;
+            if (t.row0 % KSTEP == 0 && t.col0 % BLOCK_COLS == 0 && rows_ok && cols_ok &&
+                t.col0 + round_up(nominal_cols, TILE) <= f0_cols) {
+                P.n_reused++;
+                return {0, t.col0, t.row0, 0};
+            }
+        }
+        const size_t o = P.ops.size();
+        const int64_t col = add_op(fam, tt, nominal_cols);
+        return {fam, col, 0, P.ops[o].t_shift};
+    }
+
     // C[r0:r0+p, c0:c0+q] = A[:, r0:r0+p]^T A[:, c0:c0+q] by d Strassen levels.
     void strassen_block(int64_t r0, int64_t p, int64_t c0, int64_t q, int d) {
         int64_t rn, pn, qn;
@@ -215,14 +245,11 @@ struct Builder {
                                       static_cast<int32_t>(qreg[ib].ext), cv, 0});
                 }
             }
-            size_t ou = P.ops.size();
-            int64_t ucol = add_op(fam, ut, pn);
-            size_t ov = P.ops.size();
-            int64_t vcol = add_op(fam, vt, qn);
+            Operand U = operand(fam, ut, pn, rn), V = operand(fam, vt, qn, rn);
             // Product unit: 2^(-43 - h + t_u + t_v); the combine sees it as
             // 2^(-43 + shift) with shift = t_u + t_v - h.
             const int hb = hbits_for(rn);
-            int shift = P.ops[ou].t_shift + P.ops[ov].t_shift - hb;
+            int shift = U.t_shift + V.t_shift - hb;
             prod_shift[r] = shift;
             prod_off[r] = prod_elems;
             prod_elems += pn * qn;
@@ -230,11 +257,12 @@ struct Builder {
             for (int64_t J = 0; J < ceil_div(pn, TILE_M); ++J) {
                 for (int64_t K = 0; K < ceil_div(qn, TILE_N); ++K) {
                     LeafTask t{};
-                    t.fam_u = fam;
-                    t.fam_v = fam;
-                    t.col_u = static_cast<int32_t>(ucol + J * TILE_M);
-                    t.col_v = static_cast<int32_t>(vcol + K * TILE_N);
-                    t.k0 = 0;
+                    t.fam_u = U.fam;
+                    t.fam_v = V.fam;
+                    t.col_u = static_cast<int32_t>(U.col + J * TILE_M);
+                    t.col_v = static_cast<int32_t>(V.col + K * TILE_N);
+                    t.k0 = static_cast<int32_t>(U.k0);
+                    t.k0v = static_cast<int32_t>(V.k0);
                     t.klen = static_cast<int32_t>(rn);
                     t.rows = static_cast<int32_t>(std::min<int64_t>(TILE_M, pn - J * TILE_M));
                     t.cols = static_cast<int32_t>(std::min<int64_t>(TILE_N, qn - K * TILE_N));
@@ -389,7 +417,8 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     // whole 1 KB images with bulk copies.
     if (B.digits) {
         for (const LeafTask &t : P.tasks) {
-            if (t.col_u % BLOCK_COLS != 0 || t.col_v % BLOCK_COLS != 0 || t.k0 % KSTEP != 0) {
+            if (t.col_u % BLOCK_COLS != 0 || t.col_v % BLOCK_COLS != 0 || t.k0 % KSTEP != 0 ||
+                t.k0v % KSTEP != 0) {
                 if (err) *err = "internal: leaf tile not aligned to a digit-image block";
                 return false;
             }

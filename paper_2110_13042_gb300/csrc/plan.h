@@ -71,7 +71,7 @@ struct Family {
 struct LeafTask {
     int32_t fam_u, fam_v;   // operand families (-1: A itself, native FP64 only)
     int32_t col_u, col_v;   // first column of the tile's rows / columns
-    int32_t k0, klen;       // contraction range
+    int32_t k0, klen;       // contraction offset of the row operand, length
     int32_t rows, cols;     // valid output rows / columns (<= TILE)
     int32_t diag;           // 1: tile crosses the diagonal (see diag_off)
     int32_t kind;           // OUT_* below
@@ -81,7 +81,7 @@ struct LeafTask {
     int64_t out_off;        // element offset of the tile origin in the output
     int64_t out_ld;         // output leading dimension (elements)
     int32_t hbits;          // extra fraction bits of T for short contractions
-    int32_t pad;
+    int32_t k0v;            // contraction offset of the column operand (k0: row operand)
 };
 
 // Extra fraction bits of the leaf's int64 sum for a contraction of K rows:
@@ -135,6 +135,7 @@ struct Plan {
     PlanParams p;
     int cutoff = 0, depth = 0, slices = 0, strassen_min = 0;
     int64_t n_panels = 0, n_blocks = 0, n_products = 0;
+    int64_t n_reused = 0;  // Strassen operands read from the planes of A
     std::vector<Family> families;       // [0] = plain digits of A (if used)
     std::vector<OpDesc> ops;
     std::vector<OpTerm> terms;

@@ -57,10 +57,10 @@ int main(int argc, char **argv) {
         }
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
-                "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f\n",
+                "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld\n",
                 P.cutoff, P.depth, P.slices, (long long)P.n_panels, (long long)P.n_blocks,
                 (long long)P.n_products, P.tasks.size(), (long long)covered, (long long)overlap,
                 P.cterms.size(), P.ops.size(), P.families.size(), (long long)P.workspace_bytes, s_leaf,
-                s_plain);
+                s_plain, (long long)P.n_reused);
     return 0;
 }
