@@ -277,7 +277,7 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     out[3] = P.n_panels;
     out[4] = P.n_blocks;
     out[5] = P.n_products;
-    out[6] = static_cast<int64_t>(P.tasks.size());
+    out[6] = P.n_tiles;
     out[7] = P.workspace_bytes;
     out[8] = static_cast<int64_t>(P.leaf_madds);
     out[9] = static_cast<int64_t>(P.plain_madds);
@@ -300,7 +300,9 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
     if (ranges_overlap(A, ((m - 1) * lda + n) * es, C, ((n - 1) * ldc + n) * es)) return ATA_ERR_INVALID;
 
     int status = ATA_OK;
-    CachedPlan *cp = get_plan(h, params_for(h->cfg, m, n, lda, ldc, dtype), &status);
+    PlanParams pp = params_for(h->cfg, m, n, lda, ldc, dtype);
+    pp.num_ctas = h->num_sms;
+    CachedPlan *cp = get_plan(h, pp, &status);
     if (!cp) return status;
     const Plan &P = cp->plan;
     int rc = ensure_workspace(h, static_cast<size_t>(P.workspace_bytes));

@@ -17,6 +17,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <numeric>
+#include <queue>
 
 namespace ata {
 namespace {
@@ -327,6 +330,33 @@ struct Builder {
         }
     }
 
+    // Leaf K-steps of the lower triangle of a w-wide panel under the default
+    // (middle) splits with classical off-diagonal blocks: the cost model used
+    // to place a Strassen split.
+    int64_t panel_steps(int64_t w) const {
+        const int64_t ks = ceil_div(P.p.m, KSTEP);
+        if (w <= P.cutoff || w <= 1) {
+            int64_t t = 0;
+            for (int64_t J = 0; J < ceil_div(w, TILE_M); ++J) {
+                const int64_t rows = std::min<int64_t>(TILE_M, w - J * TILE_M);
+                t += std::min<int64_t>(ceil_div(w, TILE_N), (J * TILE_M + rows - 1) / TILE_N + 1);
+            }
+            return t * ks;
+        }
+        const int64_t n1 = (w / (2 * SPLIT_ALIGN)) * SPLIT_ALIGN;
+        if (n1 == 0) return panel_steps(P.cutoff);
+        return panel_steps(n1) + panel_steps(w - n1) + ceil_div(w - n1, TILE_M) * ceil_div(n1, TILE_N) * ks;
+    }
+
+    int64_t strassen_steps(int64_t p, int64_t q, int d) const {
+        int64_t rn, pn, qn, prods = 1;
+        split_regions(P.p.m, d, &rn);
+        split_regions(p, d, &pn);
+        split_regions(q, d, &qn);
+        for (int l = 0; l < d; ++l) prods *= 7;
+        return prods * ceil_div(pn, TILE_M) * ceil_div(qn, TILE_N) * ceil_div(rn, KSTEP);
+    }
+
     void recurse(int64_t c0, int64_t w) {
         if (w <= P.cutoff || w <= 1) {
             diag_panel(c0, w);
@@ -340,10 +370,27 @@ struct Builder {
             diag_panel(c0, w);
             return;
         }
+        // Where C21 goes to Strassen, move the split (within w/8 of the
+        // middle) to the point with the fewest predicted leaf steps: product
+        // blocks that are whole multiples of the 128 x 96 tile waste nothing.
+        const int d0 = block_depth(n2, n1);
+        if (digits && P.p.split_search && d0 > 0) {
+            int64_t best = -1, best_n1 = n1;
+            for (int64_t c = ((w / 2 - w / 8) / SPLIT_ALIGN) * SPLIT_ALIGN; c <= w / 2 + w / 8; c += SPLIT_ALIGN) {
+                if (c < (int64_t(1) << d0) || w - c < (int64_t(1) << d0)) continue;
+                const int64_t cost = panel_steps(c) + panel_steps(w - c) + strassen_steps(w - c, c, d0);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    best_n1 = c;
+                }
+            }
+            n1 = best_n1;
+            n2 = w - n1;
+        }
         recurse(c0, n1);
         recurse(c0 + n1, n2);
         P.n_blocks++;
-        int d = block_depth(n2, n1);
+        int d = digits && P.p.split_search ? d0 : block_depth(n2, n1);
         if (d == 0)
             classical_block(c0 + n1, n2, c0, n1);
         else
@@ -352,6 +399,39 @@ struct Builder {
 };
 
 }  // namespace
+
+// Longest-first greedy assignment of the tiles to the leaf's G persistent
+// CTAs, laid out so that the kernel's round-robin walk (task i on CTA i % G)
+// realises it; CTAs with fewer tiles get empty fillers (klen = 0, nothing
+// stored).  Equal-length tiles keep their generation order across CTAs, so
+// tiles that run at the same time still share operand panels in L2.
+void balance_tasks(Plan &P, int G) {
+    constexpr int64_t TASK_OVERHEAD_STEPS = 3;  // final drains and stores
+    const size_t n = P.tasks.size();
+    std::vector<size_t> order(n);
+    std::iota(order.begin(), order.end(), size_t(0));
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return P.tasks[a].klen > P.tasks[b].klen; });
+    using Load = std::pair<int64_t, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < G; ++b) heap.push({0, b});
+    std::vector<std::vector<size_t>> per(G);
+    for (size_t i : order) {
+        Load l = heap.top();
+        heap.pop();
+        per[l.second].push_back(i);
+        l.first += ceil_div(P.tasks[i].klen, KSTEP) + TASK_OVERHEAD_STEPS;
+        heap.push(l);
+    }
+    size_t rounds = 0;
+    for (const auto &v : per) rounds = std::max(rounds, v.size());
+    LeafTask filler{};
+    filler.kind = OUT_C_F64;
+    std::vector<LeafTask> out(rounds * G, filler);
+    for (int b = 0; b < G; ++b)
+        for (size_t r = 0; r < per[b].size(); ++r) out[r * G + b] = P.tasks[per[b][r]];
+    P.tasks.swap(out);
+}
 
 int default_slices(int mode, int64_t m) {
     (void)m;
@@ -412,6 +492,10 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
                  pp.n);
     }
     if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
+
+    P.n_tiles = static_cast<int64_t>(P.tasks.size());
+    if (B.digits && pp.num_ctas > 1 && P.tasks.size() > static_cast<size_t>(pp.num_ctas))
+        balance_tasks(P, pp.num_ctas);
 
     // Every digit-family tile must start on a column block: the leaf loads
     // whole 1 KB images with bulk copies.

@@ -129,6 +129,10 @@ struct PlanParams {
     int slices = 0;          // 0 = auto
     int strassen_min = 0;    // Strassen splits a (sub)block only while both its
                              // sides are >= strassen_min (0 = auto)
+    int split_search = 1;    // 1: place Strassen splits by the leaf-step cost
+                             // model; 0: always split at the aligned middle
+    int num_ctas = 0;        // > 1: lay the tile list out for this many
+                             // persistent leaf CTAs (longest-first balance)
 };
 
 struct Plan {
@@ -136,6 +140,7 @@ struct Plan {
     int cutoff = 0, depth = 0, slices = 0, strassen_min = 0;
     int64_t n_panels = 0, n_blocks = 0, n_products = 0;
     int64_t n_reused = 0;  // Strassen operands read from the planes of A
+    int64_t n_tiles = 0;   // leaf tiles (tasks also holds empty balance fillers)
     std::vector<Family> families;       // [0] = plain digits of A (if used)
     std::vector<OpDesc> ops;
     std::vector<OpTerm> terms;
@@ -159,5 +164,10 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err);
 // Copy the task tables into a contiguous host buffer laid out as
 // plan.t_* describe (size plan.table_bytes).
 void pack_tables(const Plan &plan, std::vector<uint8_t> *buf);
+
+// Reorders plan.tasks for num_ctas persistent leaf CTAs (longest first,
+// greedy least-loaded), padding with empty tasks; make_plan calls it when
+// PlanParams::num_ctas > 1.
+void balance_tasks(Plan &plan, int num_ctas);
 
 }  // namespace ata

@@ -1,9 +1,10 @@
 // Host-only planner inspector (used by the CPU tests): builds the plan for
-//   plan_cli m n mode cutoff depth slices
+//   plan_cli m n mode cutoff depth slices [strassen_min [split_search [num_ctas]]]
 // and prints key=value statistics, including a coverage check that every
 // lower-triangle entry of C is produced exactly once (by a diagonal/classical
 // tile or by one Strassen result sum) and no upper entry is produced.
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -23,6 +24,8 @@ int main(int argc, char **argv) {
     pp.depth = std::atoi(argv[5]);
     pp.slices = std::atoi(argv[6]);
     pp.strassen_min = argc > 7 ? std::atoi(argv[7]) : 1;
+    pp.split_search = argc > 8 ? std::atoi(argv[8]) : 1;
+    pp.num_ctas = argc > 9 ? std::atoi(argv[9]) : 0;
     Plan P;
     std::string err;
     if (!make_plan(pp, &P, &err)) {
@@ -32,6 +35,12 @@ int main(int argc, char **argv) {
     const int64_t n = pp.n, ldc = pp.ldc;
     std::vector<uint8_t> cov(static_cast<size_t>(n * n), 0);
     double s_leaf = 0, s_plain = 0;
+    // K-steps per leaf CTA under the kernel's round-robin walk
+    const int G = pp.num_ctas > 1 ? pp.num_ctas : 152;
+    std::vector<int64_t> cta(G, 0);
+    for (size_t i = 0; i < P.tasks.size(); ++i) cta[i % G] += (P.tasks[i].klen + KSTEP - 1) / KSTEP;
+    int64_t cta_max = 0, cta_sum = 0;
+    for (int64_t v : cta) cta_max = std::max(cta_max, v), cta_sum += v;
     for (const LeafTask &t : P.tasks) {
         if (t.kind == OUT_M_I64 || t.kind == OUT_M_F64) {
             s_leaf += static_cast<double>(t.klen) * t.rows * t.cols;
@@ -57,10 +66,11 @@ int main(int argc, char **argv) {
         }
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
-                "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld\n",
+                "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "
+                "cta_steps_sum=%lld\n",
                 P.cutoff, P.depth, P.slices, (long long)P.n_panels, (long long)P.n_blocks,
-                (long long)P.n_products, P.tasks.size(), (long long)covered, (long long)overlap,
+                (long long)P.n_products, (size_t)P.n_tiles, (long long)covered, (long long)overlap,
                 P.cterms.size(), P.ops.size(), P.families.size(), (long long)P.workspace_bytes, s_leaf,
-                s_plain, (long long)P.n_reused);
+                s_plain, (long long)P.n_reused, (long long)cta_max, (long long)cta_sum);
     return 0;
 }

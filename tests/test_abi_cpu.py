@@ -101,8 +101,9 @@ def plan_cli(lib):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", os.path.dirname(src), src, plan_cpp, "-o", out],
                    check=True)
 
-    def run(m, n, mode, cutoff, depth, slices=0):
-        r = subprocess.run([out, str(m), str(n), str(mode), str(cutoff), str(depth), str(slices)],
+    def run(m, n, mode, cutoff, depth, slices=0, strassen_min=1, split_search=1, num_ctas=0):
+        r = subprocess.run([out, str(m), str(n), str(mode), str(cutoff), str(depth), str(slices),
+                            str(strassen_min), str(split_search), str(num_ctas)],
                            capture_output=True, text=True, check=True)
         return {k: int(v) for k, v in (kv.split("=") for kv in r.stdout.split())}
     return run
@@ -111,9 +112,10 @@ def plan_cli(lib):
 @pytest.mark.parametrize("n,cutoff", [(1024, 256), (2048, 512), (1000, 250), (777, 100)])
 @pytest.mark.parametrize("depth", [0, 1, 2])
 def test_recursion_structure(plan_cli, n, cutoff, depth):
-    P = plan_cli(4096, n, 1, cutoff, depth)
-    # Panels: the leaves of the column recursion; the split point is the
-    # largest multiple of 32 not above w/2 (a panel if that is 0).
+    # With the cost-model split placement off, every split is the aligned
+    # middle: panels are the leaves of that column recursion, the split point
+    # the largest multiple of 32 not above w/2 (a panel if that is 0).
+    P = plan_cli(4096, n, 1, cutoff, depth, split_search=0)
     def split(w):
         return (w // 64) * 32
 
@@ -139,6 +141,34 @@ def test_recursion_structure(plan_cli, n, cutoff, depth):
     assert P["overlap"] == 0
 
 
+@pytest.mark.parametrize("m,n,cutoff,depth,smin", [(4096, 1000, 250, 1, 1), (777, 777, 100, 2, 1),
+                                                    (8192, 8192, 0, 1, 4096), (513, 3001, 300, 3, 64),
+                                                    (64, 16384, 0, 2, 4096)])
+def test_split_search_keeps_coverage(plan_cli, m, n, cutoff, depth, smin):
+    # Moving Strassen splits off the middle changes the tiling (and possibly
+    # the recursion below), never the result: every lower entry is still
+    # produced exactly once and no upper one.
+    for search in (1, 0):
+        P = plan_cli(m, n, 1, cutoff, depth, strassen_min=smin, split_search=search)
+        assert P["covered"] == n * (n + 1) // 2
+        assert P["overlap"] == 0
+
+
+@pytest.mark.parametrize("m,n,depth,smin", [(8192, 8192, 1, 4096), (8192, 8192, 0, 4096),
+                                            (3000, 5000, 2, 512), (100, 640, 1, 64)])
+def test_task_balance_for_persistent_ctas(plan_cli, m, n, depth, smin):
+    # The longest-first layout for 152 CTAs keeps every tile (fillers produce
+    # nothing) and never loads the busiest CTA more than round-robin does.
+    rr = plan_cli(m, n, 1, 0, depth, strassen_min=smin, num_ctas=0)
+    bal = plan_cli(m, n, 1, 0, depth, strassen_min=smin, num_ctas=152)
+    assert bal["tiles"] == rr["tiles"]
+    assert bal["covered"] == n * (n + 1) // 2 and bal["overlap"] == 0
+    assert bal["cta_steps_sum"] == rr["cta_steps_sum"]
+    assert bal["cta_steps_max"] <= rr["cta_steps_max"]
+    # greedy longest-first is within one task of the mean
+    assert bal["cta_steps_max"] <= bal["cta_steps_sum"] / 152 + (m + 15) // 16 + 3
+
+
 @pytest.mark.parametrize("depth", [1, 2, 3])
 def test_strassen_products_and_savings(plan_cli, depth):
     n, cutoff = 8192, 2048
@@ -153,10 +183,10 @@ def test_strassen_products_and_savings(plan_cli, depth):
 def test_combine_terms_match_strassen_counts(plan_cli):
     # depth 1: C11 and C22 have 4 terms, C12 and C21 have 2: 12 result terms
     # per block (the 8 result additions of Section 3.2 plus one term per quadrant).
-    P = plan_cli(8192, 4096, 1, 2048, 1)
+    P = plan_cli(8192, 4096, 1, 2048, 1, split_search=0)
     assert P["blocks"] == 1
     assert P["cterms"] == 12
-    P2 = plan_cli(8192, 4096, 1, 2048, 2)
+    P2 = plan_cli(8192, 4096, 1, 2048, 2, split_search=0)
     assert P2["cterms"] == 144
 
 
