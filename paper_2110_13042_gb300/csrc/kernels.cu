@@ -231,6 +231,86 @@ __device__ __forceinline__ void store_digits(const int64_t (&w)[KSTEP], uint8_t 
 constexpr int PREP_SMEM_OPS = 64;
 constexpr int PREP_SMEM_TERMS = 128;
 
+// sV[kr0 + 4 it][cc] = sum over the op's terms of coef * round(a * 2^sh) for
+// the 16 rows k0 + kr0 + 4 it of column c0 + cc.  NT > 0 (1, 2 or 4 terms; a
+// missing fourth reads nothing): the rows go in groups of 16 / NT, every
+// term's loads of a group are issued before any is used (16 loads in flight
+// per thread whatever the term count), and a group's sums go to shared memory
+// as soon as they are complete.  NT = 0: any count, one term at a time.
+template <int S, int NT, typename T>
+__device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
+                                           const OpDesc &od, const OpTerm *terms, int k0, int c0, int cc,
+                                           int kr0, int64_t (*sV)[PREP_C + 1]) {
+    constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
+    auto fixed = [](T a, int sh) -> int64_t {
+        if constexpr (FastFixed<F, T>::ok)
+            return fixed_of_fast<F>(a, sh);
+        else
+            return fixed_of(a, sh);
+    };
+    const int c = c0 + cc;
+    if constexpr (NT > 0) {
+        constexpr int G = 16 / NT;  // rows per group
+        const T *base[NT];          // element (k0 + kr0, column) of each term
+        int lim[NT], sh[NT], neg[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const bool present = t < od.nterms;
+            const OpTerm tm = present ? terms[od.first_term + t] : OpTerm{};
+            const bool cv = present && c < tm.cols;
+            base[t] = A + (tm.row0 + k0 + kr0) * lda + tm.col0 + c;
+            lim[t] = cv ? tm.rows - k0 - kr0 : 0;  // rows 4 it < lim are inside the term
+            sh[t] = cv ? F - od.t_shift - expo[tm.col0 + c] : 0;
+            neg[t] = tm.coef < 0;
+        }
+#pragma unroll
+        for (int g = 0; g < 16; g += G) {
+            T raw[NT][G];
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    raw[t][j] = 4 * (g + j) < lim[t] ? base[t][4 * (g + j) * lda] : T(0);
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                int64_t v = 0;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const int64_t x = fixed(raw[t][j], sh[t]);
+                    v += neg[t] ? -x : x;
+                }
+                sV[kr0 + 4 * (g + j)][cc] = v;
+            }
+        }
+    } else {
+        // more than four terms (Strassen depth >= 3): groups of four rows,
+        // one term at a time
+#pragma unroll 1
+        for (int g = 0; g < 16; g += 4) {
+            int64_t v[4] = {0, 0, 0, 0};
+            for (int t = 0; t < od.nterms; ++t) {
+                const OpTerm tm = terms[od.first_term + t];
+                const bool cvalid = c < tm.cols;
+                const T *col = A + tm.col0 + c;
+                T raw[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = k0 + kr0 + 4 * (g + j);
+                    raw[j] = (cvalid && k < tm.rows) ? col[(tm.row0 + k) * lda] : T(0);
+                }
+                const int sh = cvalid ? F - od.t_shift - expo[tm.col0 + c] : 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t x = fixed(raw[j], sh);
+                    v[j] += tm.coef > 0 ? x : -x;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sV[kr0 + 4 * (g + j)][cc] = v[j];
+        }
+    }
+}
+
 template <int S, typename T>
 __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                           const OpDesc &od, const OpTerm *terms, int64_t tile,
@@ -239,37 +319,16 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     const int tiles_k = od.K_pitch / PREP_K;
     const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
     const int c0 = static_cast<int>(local / tiles_k) * PREP_C;
-    constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
 
     const int cc = threadIdx.x & 63;
     const int kr0 = threadIdx.x >> 6;
-    int64_t V[16];
-#pragma unroll
-    for (int it = 0; it < 16; ++it) V[it] = 0;
-    for (int t = 0; t < od.nterms; ++t) {
-        const OpTerm tm = terms[od.first_term + t];
-        const int c = c0 + cc;
-        const bool cvalid = c < tm.cols;
-        const T *col = A + tm.col0 + c;
-        T raw[16];
-#pragma unroll
-        for (int it = 0; it < 16; ++it) {
-            const int k = k0 + kr0 + 4 * it;
-            raw[it] = (cvalid && k < tm.rows) ? col[(tm.row0 + k) * lda] : T(0);
-        }
-        const int sh = cvalid ? F - od.t_shift - expo[tm.col0 + c] : 0;
-#pragma unroll
-        for (int it = 0; it < 16; ++it) {
-            int64_t v;
-            if constexpr (FastFixed<F, T>::ok)
-                v = fixed_of_fast<F>(raw[it], sh);
-            else
-                v = fixed_of(raw[it], sh);
-            V[it] += tm.coef > 0 ? v : -v;
-        }
+    switch (od.nterms) {
+        case 1: read_terms<S, 1>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
+        case 2: read_terms<S, 2>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
+        case 3:
+        case 4: read_terms<S, 4>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
+        default: read_terms<S, 0>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
     }
-#pragma unroll
-    for (int it = 0; it < 16; ++it) sV[kr0 + 4 * it][cc] = V[it];
     __syncthreads();
 
     const Family fam = fams.f[od.family];
