@@ -107,10 +107,16 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda,
 /* low(C_i) <- low(A_i^T A_i) for `count` independent problems in one
  * persistent launch.  m, n, lda, ldc: HOST arrays of length count.  A, C:
  * HOST arrays of `count` DEVICE pointers.  Only ATA_F32, ATA_F32_BF16 and
- * ATA_F64_EMU are accepted; every problem is done as plain tiles (no
- * Strassen).  The task table is uploaded from pinned host memory owned by the
- * handle, so the same call is graph-capturable after a first uncaptured call
- * with the same problem set. */
+ * ATA_F64_EMU are accepted (ATA_F64: ATA_ERR_UNSUPPORTED); every problem is
+ * done as plain lower-triangle tiles of its own digit planes (no Strassen),
+ * with the same arithmetic and bits as a depth-0 ata_lower call.  Three
+ * launches serve the whole batch: column exponents, digit planes, and one
+ * persistent leaf launch over all problems' tiles (longest first).  Problems
+ * with n == 0 are skipped and m == 0 zero-fills low(C_i).  The plan and its
+ * task table live in pinned host memory owned by the handle and are reused
+ * while the same problem set (shapes and pointers) comes back, so the call is
+ * graph-capturable after a first uncaptured call with that set.  Errors: as
+ * ata_lower, checked per problem before anything is launched. */
 int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n,
                 const void *const *A, const int64_t *lda, void *const *C,
                 const int64_t *ldc, int dtype, void *stream);

@@ -145,6 +145,23 @@ class Handle:
         return int(load().ata_batched(self._h, count, I64(*ms), I64(*ns), VP(*A_ptrs), I64(*ldas),
                                       VP(*C_ptrs), I64(*ldcs), int(dtype), _stream_ptr(stream)))
 
+    def batched(self, As, Cs, dtype, stream=None):
+        """low(C_i) <- low(A_i^T A_i) for lists of row-major CUDA tensors in one
+        persistent launch (ata_batched)."""
+        if len(As) != len(Cs):
+            raise ValueError("As and Cs must have the same length")
+        for A, C in zip(As, Cs):
+            if (A.dim() == 2 and A.numel() and A.stride(1) != 1) or (C.numel() and C.stride(1) != 1):
+                raise ValueError("A_i and C_i must be row-major with unit column stride")
+        ms = [int(A.shape[0]) for A in As]
+        ns = [int(A.shape[1]) for A in As]
+        ldas = [max(int(A.stride(0)), n, 1) for A, n in zip(As, ns)]
+        ldcs = [max(int(C.stride(0)), n, 1) for C, n in zip(Cs, ns)]
+        rc = self.batched_ptr(ms, ns, [A.data_ptr() for A in As], ldas, [C.data_ptr() for C in Cs], ldcs,
+                              dtype, stream)
+        if rc != 0:
+            raise AtaError(rc, f"ata_batched [{self.last_error()}]")
+
     def set_timing(self, enable: bool = True):
         _check(load().ata_set_timing(self._h, 1 if enable else 0), "ata_set_timing")
 

@@ -33,6 +33,19 @@ struct CachedPlan {
     }
 };
 
+// The plan and pinned task tables of the last batched call (re-used while
+// the same problems, pointers and configuration come back).
+struct CachedBatch {
+    std::vector<int64_t> key;
+    BatchPlan plan;
+    uint8_t *pinned = nullptr;
+    size_t table_bytes = 0;
+    int64_t off_expo = 0, off_probs = 0, off_tasks = 0, off_planes = 0, total = 0;
+    ~CachedBatch() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+};
+
 bool is_f32_mode(int dtype) { return dtype == ATA_F32 || dtype == ATA_F32_BF16; }
 
 bool valid_dtype(int dtype) {
@@ -51,6 +64,7 @@ struct ata_handle_s {
     int *d_status = nullptr;
     const CachedPlan *resident = nullptr;  // whose tables are in the workspace
     std::map<Key, std::unique_ptr<CachedPlan>> plans;
+    std::unique_ptr<CachedBatch> batch;
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -253,6 +267,7 @@ int ata_destroy(ata_handle h) {
     if (!h) return ATA_ERR_INVALID;
     cudaDeviceSynchronize();
     h->plans.clear();
+    h->batch.reset();
     for (cudaEvent_t &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
@@ -377,11 +392,94 @@ int ata_phase_times(ata_handle h, double *out) {
 int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, const void *const *A,
                 const int64_t *lda, void *const *C, const int64_t *ldc, int dtype, void *stream) {
     if (!h || count < 0) return ATA_ERR_INVALID;
+    h->last_error.clear();
     if (count == 0) return ATA_OK;
     if (!m || !n || !A || !lda || !C || !ldc) return ATA_ERR_INVALID;
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
-    (void)stream;
-    return ATA_ERR_UNSUPPORTED;
+    if (dtype == ATA_F64) return fail(h, ATA_ERR_UNSUPPORTED, "batched calls take F64_EMU, F32 or F32_BF16");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool f32 = is_f32_mode(dtype);
+    const size_t es = f32 ? 4 : 8;
+    for (int i = 0; i < count; ++i) {
+        if (m[i] < 0 || n[i] < 0) return ATA_ERR_INVALID;
+        if (n[i] == 0) continue;
+        if (ldc[i] < n[i] || !C[i]) return ATA_ERR_INVALID;
+        if (m[i] == 0) continue;
+        if (lda[i] < n[i] || !A[i]) return ATA_ERR_INVALID;
+        if (ranges_overlap(A[i], ((m[i] - 1) * lda[i] + n[i]) * es, C[i], ((n[i] - 1) * ldc[i] + n[i]) * es))
+            return ATA_ERR_INVALID;
+        if (m[i] > MAX_DIGIT_K) return fail(h, ATA_ERR_UNSUPPORTED, "contraction beyond the exact-accumulation limit");
+    }
+
+    // Plan (and its pinned tables) for this exact problem set.
+    std::vector<int64_t> key;
+    key.reserve(4 + 6 * static_cast<size_t>(count));
+    key.push_back(dtype);
+    key.push_back(h->cfg.slices);
+    key.push_back(h->num_sms);
+    key.push_back(count);
+    for (int i = 0; i < count; ++i) {
+        key.push_back(m[i]);
+        key.push_back(n[i]);
+        key.push_back(lda[i]);
+        key.push_back(ldc[i]);
+        key.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(A[i])));
+        key.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(C[i])));
+    }
+    if (!h->batch || h->batch->key != key) {
+        std::unique_ptr<CachedBatch> cb(new (std::nothrow) CachedBatch());
+        if (!cb) return ATA_ERR_ALLOC;
+        std::string err;
+        if (!make_batch_plan(dtype, h->cfg.slices, h->num_sms, count, m, n, lda, ldc, A, C, &cb->plan, &err))
+            return fail(h, ATA_ERR_INVALID, err.c_str());
+        const BatchPlan &B = cb->plan;
+        auto align = [](int64_t x) { return (x + 1023) & ~int64_t(1023); };
+        const int64_t probs_bytes = static_cast<int64_t>(B.probs.size() * sizeof(BatchProb));
+        const int64_t tasks_bytes = static_cast<int64_t>(B.tasks.size() * sizeof(LeafTask));
+        cb->off_expo = 0;
+        cb->off_probs = align(B.total_cols * 4);
+        cb->off_tasks = cb->off_probs + align(probs_bytes);
+        cb->off_planes = cb->off_tasks + align(tasks_bytes);
+        cb->total = cb->off_planes + align(B.plane_bytes);
+        cb->table_bytes = static_cast<size_t>(cb->off_planes - cb->off_probs);
+        if (cudaMallocHost(reinterpret_cast<void **>(&cb->pinned), cb->table_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, ATA_ERR_ALLOC, "pinned batch tables");
+        }
+        std::memset(cb->pinned, 0, cb->table_bytes);
+        std::memcpy(cb->pinned, B.probs.data(), static_cast<size_t>(probs_bytes));
+        std::memcpy(cb->pinned + (cb->off_tasks - cb->off_probs), B.tasks.data(), static_cast<size_t>(tasks_bytes));
+        cb->key.swap(key);
+        h->batch = std::move(cb);
+    }
+    CachedBatch &cb = *h->batch;
+    const BatchPlan &B = cb.plan;
+    int rc = ensure_workspace(h, static_cast<size_t>(cb.total));
+    if (rc != ATA_OK) return fail(h, rc, "workspace");
+    h->resident = nullptr;  // the batch overwrites the single-call tables
+    uint8_t *ws = h->ws;
+    BatchProb *probs = reinterpret_cast<BatchProb *>(ws + cb.off_probs);
+    int *expo = reinterpret_cast<int *>(ws + cb.off_expo);
+    cudaError_t e = cudaMemcpyAsync(ws + cb.off_probs, cb.pinned, cb.table_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload", e);
+    for (int i = 0; i < count; ++i)
+        if (n[i] > 0 && m[i] == 0 && (e = launch_zero_lower(C[i], n[i], ldc[i], f32, s)) != cudaSuccess)
+            return fail(h, ATA_ERR_CUDA, "zero fill", e);
+    if ((e = launch_batched_expo(B, probs, f32, expo, h->d_status, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "batched exponents", e);
+    if ((e = launch_batched_prep(B, probs, f32, expo, ws + cb.off_planes, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "batched digit prep", e);
+    LeafParams lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.tasks = reinterpret_cast<const LeafTask *>(ws + cb.off_tasks);
+    lp.ntasks = static_cast<int>(B.tasks.size());
+    lp.expo = expo;
+    lp.status = h->d_status;
+    lp.probs = probs;
+    lp.batch_planes = ws + cb.off_planes;
+    if ((e = launch_leaf_tc_raw(B.slices, lp, lp.ntasks, h->num_sms, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "batched leaf", e);
+    return ATA_OK;
 }
 
 int ata_sync(ata_handle h, void *stream) {

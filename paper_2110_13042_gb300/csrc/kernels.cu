@@ -88,12 +88,10 @@ __global__ void __launch_bounds__(256) colmax_kernel(const T *__restrict__ A, in
     if (mx) atomicMax(colmax + j, mx);
 }
 
-// e_j = smallest integer with max_i |a_ij| < 2^e_j (0 for a zero column).
+// e_j = smallest integer with max_i |a_ij| < 2^e_j (0 for a zero column),
+// from the bits b of max_i |a_ij|; a non-finite column sets *status.
 template <typename T>
-__global__ void expo_kernel(const unsigned long long *colmax, int64_t n, int *expo, int *status) {
-    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const unsigned long long b = colmax[j];
+__device__ __forceinline__ int column_exponent(unsigned long long b, int *status) {
     int e = 0;
     if (sizeof(T) == 8) {
         const int eb = static_cast<int>(b >> 52);
@@ -115,7 +113,14 @@ __global__ void expo_kernel(const unsigned long long *colmax, int64_t n, int *ex
         else
             e = eb - 126;
     }
-    expo[j] = e;
+    return e;
+}
+
+template <typename T>
+__global__ void expo_kernel(const unsigned long long *colmax, int64_t n, int *expo, int *status) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    expo[j] = column_exponent<T>(colmax[j], status);
 }
 
 // -------------------------------------------------------- operand prep --
@@ -314,7 +319,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
 template <int S, typename T>
 __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                           const OpDesc &od, const OpTerm *terms, int64_t tile,
-                                          const Families &fams, uint8_t *ws, int64_t (*sV)[PREP_C + 1]) {
+                                          const Family &fam, uint8_t *ws, int64_t (*sV)[PREP_C + 1]) {
     const int64_t local = tile - od.tile_base;
     const int tiles_k = od.K_pitch / PREP_K;
     const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
@@ -331,7 +336,6 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     }
     __syncthreads();
 
-    const Family fam = fams.f[od.family];
     const int64_t ncb = fam.cols / BLOCK_COLS;
     const int c = threadIdx.x & 63;    // operand column within the tile
     const int ks = threadIdx.x >> 6;   // contraction step within the tile
@@ -370,7 +374,66 @@ __global__ void __launch_bounds__(256, 3) prep_digits_kernel(const T *__restrict
     const OpTerm *tt = cached ? s_terms : terms;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const OpDesc od = o[find_desc(o, nops, tile)];
-        prep_tile<S, T>(A, lda, expo, od, tt, tile, fams, ws, sV);
+        prep_tile<S, T>(A, lda, expo, od, tt, tile, fams.f[od.family], ws, sV);
+    }
+}
+
+// Batched calls: the prep tiles of all problems in one persistent grid.  A
+// block walks its tiles in increasing order and keeps a cursor on the
+// problem table (prefix prep_base), so locating a tile's problem costs one
+// binary search per block.
+template <int S, typename T>
+__global__ void __launch_bounds__(256, 3) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
+                                                              const int *__restrict__ expo, int64_t ntiles,
+                                                              uint8_t *planes) {
+    __shared__ int64_t sV[PREP_K][PREP_C + 1];
+    int64_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    int64_t lo = 0, hi = count - 1;  // last problem with prep_base <= tile
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (probs[mid].prep_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int64_t pi = lo;
+    for (; tile < ntiles; tile += gridDim.x) {
+        while (pi + 1 < count && probs[pi + 1].prep_base <= tile) ++pi;
+        const BatchProb &bp = probs[pi];
+        OpDesc od{};
+        od.nterms = 1;
+        od.K_pitch = static_cast<int32_t>(bp.K_pitch);
+        od.P_pad = static_cast<int32_t>(bp.P_pad);
+        od.tile_base = bp.prep_base;
+        const OpTerm term{0, 0, static_cast<int32_t>(bp.m), static_cast<int32_t>(bp.n), 1, 0};
+        Family fam{};
+        fam.K_pitch = bp.K_pitch;
+        fam.cols = bp.ncb * BLOCK_COLS;
+        fam.offset = bp.plane_off;
+        prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, expo + bp.col_off, od, &term, tile, fam, planes, sV);
+    }
+}
+
+// Batched calls: exponents of every column of every problem.  Block (x, y):
+// problem y (then y + gridDim.y, ...), columns 256 x .. 256 x + 255, all rows.
+template <typename T>
+__global__ void __launch_bounds__(256) batched_expo_kernel(const BatchProb *__restrict__ probs, int64_t count,
+                                                           int *expo, int *status) {
+    for (int64_t pi = blockIdx.y; pi < count; pi += gridDim.y) {
+        const BatchProb &bp = probs[pi];
+        const int64_t j = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x;
+        if (j >= bp.n || bp.m == 0) continue;
+        const T *a = static_cast<const T *>(bp.A) + j;
+        unsigned long long mx = 0;
+        int64_t i = 0;
+        for (; i + 4 <= bp.m; i += 4) {  // four independent loads in flight
+            const unsigned long long b0 = abs_bits(a[(i + 0) * bp.lda]), b1 = abs_bits(a[(i + 1) * bp.lda]);
+            const unsigned long long b2 = abs_bits(a[(i + 2) * bp.lda]), b3 = abs_bits(a[(i + 3) * bp.lda]);
+            mx = max(mx, max(max(b0, b1), max(b2, b3)));
+        }
+        for (; i < bp.m; ++i) mx = max(mx, abs_bits(a[i * bp.lda]));
+        expo[bp.col_off + j] = column_exponent<T>(mx, status);
     }
 }
 
@@ -600,6 +663,42 @@ __global__ void zero_lower_kernel(T *C, int64_t n, int64_t ldc) {
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+cudaError_t launch_batched_expo(const BatchPlan &B, const BatchProb *probs, bool is_f32, int *expo, int *status,
+                                cudaStream_t s) {
+    if (B.count == 0 || B.max_col_chunks == 0) return cudaSuccess;
+    dim3 grid(static_cast<unsigned>(B.max_col_chunks), static_cast<unsigned>(B.count < 65535 ? B.count : 65535));
+    if (is_f32)
+        batched_expo_kernel<float><<<grid, 256, 0, s>>>(probs, B.count, expo, status);
+    else
+        batched_expo_kernel<double><<<grid, 256, 0, s>>>(probs, B.count, expo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_prep(const BatchPlan &B, const BatchProb *probs, bool is_f32, const int *expo,
+                                uint8_t *planes, cudaStream_t s) {
+    if (B.prep_tiles == 0) return cudaSuccess;
+    const unsigned g = prep_grid(B.prep_tiles);
+#define ATA_PREP_B(SS)                                                                                        \
+    case SS:                                                                                                  \
+        if (is_f32)                                                                                           \
+            batched_prep_kernel<SS, float><<<g, 256, 0, s>>>(probs, B.count, expo, B.prep_tiles, planes);    \
+        else                                                                                                  \
+            batched_prep_kernel<SS, double><<<g, 256, 0, s>>>(probs, B.count, expo, B.prep_tiles, planes);   \
+        break;
+    switch (B.slices) {
+        ATA_PREP_B(1)
+        ATA_PREP_B(2)
+        ATA_PREP_B(3)
+        ATA_PREP_B(4)
+        ATA_PREP_B(5)
+        ATA_PREP_B(6)
+        ATA_PREP_B(7)
+        default: return cudaErrorInvalidValue;
+    }
+#undef ATA_PREP_B
+    return cudaGetLastError();
+}
+
 cudaError_t launch_colmax(const void *A, int64_t m, int64_t n, int64_t lda, bool is_f32,
                           unsigned long long *colmax, int *expo, int *status, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * n, s);

@@ -23,10 +23,20 @@ struct LeafParams {
     int64_t lda;
     const double *fam64[MAX_FAMILIES];  // native FP64: family arrays
     int64_t fam_ld[MAX_FAMILIES];
+    const BatchProb *probs;             // batched calls: problem table (else null)
+    const uint8_t *batch_planes;        // batched calls: base of all problems' planes
 };
 
 // Column exponents e_j (smallest e with max_i |a_ij| < 2^e); flags a
 // non-finite column in *status.
+// Batched calls: column exponents of every problem (one block per problem
+// and 256-column chunk), and the digit planes of every problem (persistent
+// grid over all prep tiles).  probs is the device copy of the plan's table.
+cudaError_t launch_batched_expo(const BatchPlan &B, const BatchProb *probs, bool is_f32, int *expo, int *status,
+                                cudaStream_t s);
+cudaError_t launch_batched_prep(const BatchPlan &B, const BatchProb *probs, bool is_f32, const int *expo,
+                                uint8_t *planes, cudaStream_t s);
+
 cudaError_t launch_colmax(const void *A, int64_t m, int64_t n, int64_t lda, bool is_f32,
                           unsigned long long *colmax, int *expo, int *status, cudaStream_t s);
 cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *expo,

@@ -262,10 +262,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 const int nsteps = (t.klen + KSTEP - 1) / KSTEP;
                 // Digit images: ((kstep * S + digit) * ncb + column block) KB; the
                 // tile's TILE_M (TILE_N) columns are 4 (3) consecutive blocks.
-                const uint8_t *ua = p.fam_base[t.fam_u] + static_cast<int64_t>(t.col_u / BLOCK_COLS) * BLOCK_BYTES;
-                const uint8_t *vb = p.fam_base[t.fam_v] + static_cast<int64_t>(t.col_v / BLOCK_COLS) * BLOCK_BYTES;
-                const int64_t ua_step = p.fam_ncb[t.fam_u] * BLOCK_BYTES;  // per digit plane
-                const int64_t vb_step = p.fam_ncb[t.fam_v] * BLOCK_BYTES;
+                const uint8_t *ubase = p.fam_base[t.fam_u], *vbase = p.fam_base[t.fam_v];
+                int64_t uncb = p.fam_ncb[t.fam_u], vncb = p.fam_ncb[t.fam_v];
+                if (p.probs) {  // batched: both operands are the planes of problem t.prob
+                    const BatchProb &bp = p.probs[t.prob];
+                    ubase = vbase = p.batch_planes + bp.plane_off;
+                    uncb = vncb = bp.ncb;
+                }
+                const uint8_t *ua = ubase + static_cast<int64_t>(t.col_u / BLOCK_COLS) * BLOCK_BYTES;
+                const uint8_t *vb = vbase + static_cast<int64_t>(t.col_v / BLOCK_COLS) * BLOCK_BYTES;
+                const int64_t ua_step = uncb * BLOCK_BYTES;  // per digit plane
+                const int64_t vb_step = vncb * BLOCK_BYTES;
                 for (int step = 0; step < nsteps; ++step) {
                     if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, p.status)) {
                         ok = false;
@@ -395,8 +402,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) - t.hbits + t.shift +
                                    (t.eu >= 0 ? p.expo[t.eu + row] : 0);
                     const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
+                    void *cbase = p.probs ? p.probs[t.prob].C : p.C;
                     if (t.kind == OUT_C_F64) {
-                        double *out = static_cast<double *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                        double *out = static_cast<double *>(cbase) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
@@ -404,7 +412,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                 out[col] = static_cast<double>(T[i]) * exp2d(er + (ev ? ev[col] : 0));
                         }
                     } else {
-                        float *out = static_cast<float *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                        float *out = static_cast<float *>(cbase) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
@@ -424,16 +432,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     }
 }
 
+// The shared-memory opt-in of leaf_tc_kernel<S>, set once per device (a
+// later call, e.g. inside a graph capture, needs no attribute change).
+template <int S>
+cudaError_t ensure_leaf_attr() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(leaf_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<S>::SMEM_BYTES);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
 template <int S>
 cudaError_t launch_s(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s) {
     using C = Cfg<S>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             C::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t ea = ensure_leaf_attr<S>();
+    if (ea != cudaSuccess) return ea;
     const int ntasks = static_cast<int>(P.tasks.size());
     const int grid = ntasks < num_sms ? ntasks : num_sms;
     leaf_tc_kernel<S><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(lp);
@@ -473,15 +490,14 @@ cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cud
 
 namespace ata {
 
-// Leaf launch from an explicit task count (used by the allocation-free entry
-// point).  Sets the shared-memory attribute on every call.
+// Leaf launch from an explicit task count (allocation-free and batched entry
+// points).
 cudaError_t launch_leaf_tc_raw(int slices, const LeafParams &lp, int ntasks, int num_sms, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
     const int grid = ntasks < num_sms ? ntasks : num_sms;
 #define ATA_LEAF_RAW(SS)                                                                                     \
     case SS: {                                                                                               \
-        cudaError_t e = cudaFuncSetAttribute(leaf_tc_kernel<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             Cfg<SS>::SMEM_BYTES);                                           \
+        cudaError_t e = ensure_leaf_attr<SS>();                                                              \
         if (e != cudaSuccess) return e;                                                                      \
         leaf_tc_kernel<SS><<<grid, NUM_THREADS, Cfg<SS>::SMEM_BYTES, s>>>(lp);                              \
         return cudaGetLastError();                                                                           \

@@ -20,6 +20,7 @@
 #include <functional>
 #include <numeric>
 #include <queue>
+#include <string>
 
 namespace ata {
 namespace {
@@ -405,13 +406,13 @@ struct Builder {
 // realises it; CTAs with fewer tiles get empty fillers (klen = 0, nothing
 // stored).  Equal-length tiles keep their generation order across CTAs, so
 // tiles that run at the same time still share operand panels in L2.
-void balance_tasks(Plan &P, int G) {
+static void balance_task_list(std::vector<LeafTask> &tasks, int G) {
     constexpr int64_t TASK_OVERHEAD_STEPS = 3;  // final drains and stores
-    const size_t n = P.tasks.size();
+    const size_t n = tasks.size();
     std::vector<size_t> order(n);
     std::iota(order.begin(), order.end(), size_t(0));
     std::stable_sort(order.begin(), order.end(),
-                     [&](size_t a, size_t b) { return P.tasks[a].klen > P.tasks[b].klen; });
+                     [&](size_t a, size_t b) { return tasks[a].klen > tasks[b].klen; });
     using Load = std::pair<int64_t, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int b = 0; b < G; ++b) heap.push({0, b});
@@ -420,7 +421,7 @@ void balance_tasks(Plan &P, int G) {
         Load l = heap.top();
         heap.pop();
         per[l.second].push_back(i);
-        l.first += ceil_div(P.tasks[i].klen, KSTEP) + TASK_OVERHEAD_STEPS;
+        l.first += ceil_div(tasks[i].klen, KSTEP) + TASK_OVERHEAD_STEPS;
         heap.push(l);
     }
     size_t rounds = 0;
@@ -429,8 +430,93 @@ void balance_tasks(Plan &P, int G) {
     filler.kind = OUT_C_F64;
     std::vector<LeafTask> out(rounds * G, filler);
     for (int b = 0; b < G; ++b)
-        for (size_t r = 0; r < per[b].size(); ++r) out[r * G + b] = P.tasks[per[b][r]];
-    P.tasks.swap(out);
+        for (size_t r = 0; r < per[b].size(); ++r) out[r * G + b] = tasks[per[b][r]];
+    tasks.swap(out);
+}
+
+void balance_tasks(Plan &P, int G) { balance_task_list(P.tasks, G); }
+
+bool make_batch_plan(int mode, int slices, int num_ctas, int64_t count, const int64_t *m, const int64_t *n,
+                     const int64_t *lda, const int64_t *ldc, const void *const *A, void *const *C,
+                     BatchPlan *plan, std::string *err) {
+    BatchPlan &B = *plan;
+    B = BatchPlan();
+    if (mode != MODE_F64_EMU && mode != MODE_F32 && mode != MODE_F32_BF16) {
+        if (err) *err = "batched calls take F64_EMU, F32 or F32_BF16";
+        return false;
+    }
+    B.mode = mode;
+    B.slices = slices > 0 ? slices : default_slices(mode, 0);
+    if (B.slices < 1 || B.slices > MAX_SLICES) {
+        if (err) *err = "slices out of range";
+        return false;
+    }
+    B.count = count;
+    B.probs.resize(static_cast<size_t>(count));
+    int64_t col_off = 0, plane_off = 0, prep = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (m[i] < 0 || n[i] < 0 || m[i] > MAX_DIGIT_K || n[i] > (int64_t(1) << 30) ||
+            (n[i] > 0 && (ldc[i] < n[i] || !C[i])) || (n[i] > 0 && m[i] > 0 && (lda[i] < n[i] || !A[i]))) {
+            if (err) *err = "invalid problem " + std::to_string(i);
+            return false;
+        }
+        BatchProb &q = B.probs[static_cast<size_t>(i)];
+        q.A = A[i];
+        q.C = C[i];
+        q.m = m[i];
+        q.n = n[i];
+        q.lda = lda[i];
+        q.ldc = ldc[i];
+        q.col_off = col_off;
+        q.plane_off = plane_off;
+        q.prep_base = prep;
+        if (n[i] == 0 || m[i] == 0) continue;
+        q.K_pitch = round_up(m[i], PREP_K);
+        q.P_pad = round_up(n[i], TILE);
+        const int64_t cols = q.P_pad + TILE;  // tile overhang stays inside the planes
+        q.ncb = cols / BLOCK_COLS;
+        col_off += n[i];
+        plane_off += q.K_pitch * cols * 2 * B.slices;
+        prep += (q.K_pitch / PREP_K) * (q.P_pad / PREP_C);
+        B.max_col_chunks = std::max<int64_t>(B.max_col_chunks, ceil_div(n[i], 256));
+        const int kind = mode == MODE_F64_EMU ? OUT_C_F64 : OUT_C_F32;
+        const int hb = hbits_for(m[i]);
+        for (int64_t J = 0; J < ceil_div(n[i], TILE_M); ++J) {
+            const int64_t rows = std::min<int64_t>(TILE_M, n[i] - J * TILE_M);
+            for (int64_t K = 0; K * TILE_N < n[i] && K * TILE_N <= J * TILE_M + rows - 1; ++K) {
+                const int64_t r0 = J * TILE_M, c0 = K * TILE_N;
+                const int64_t cols_t = std::min<int64_t>(TILE_N, n[i] - c0);
+                LeafTask t{};
+                t.fam_u = t.fam_v = 0;
+                t.col_u = static_cast<int32_t>(r0);
+                t.col_v = static_cast<int32_t>(c0);
+                t.klen = static_cast<int32_t>(m[i]);
+                t.rows = static_cast<int32_t>(rows);
+                t.cols = static_cast<int32_t>(cols_t);
+                t.diag = (c0 + cols_t - 1 > r0) ? 1 : 0;
+                t.diag_off = static_cast<int32_t>(r0 - c0);
+                t.kind = kind;
+                t.eu = static_cast<int32_t>(q.col_off + r0);
+                t.ev = static_cast<int32_t>(q.col_off + c0);
+                t.out_off = r0 * ldc[i] + c0;
+                t.out_ld = ldc[i];
+                t.hbits = hb;
+                t.prob = static_cast<int32_t>(i);
+                B.tasks.push_back(t);
+                B.leaf_madds += static_cast<double>(m[i]) * TILE_M * TILE_N;
+            }
+        }
+    }
+    if (col_off > 0x7FFFFFFF) {
+        if (err) *err = "batch has more than 2^31 columns";
+        return false;
+    }
+    B.total_cols = col_off;
+    B.plane_bytes = plane_off;
+    B.prep_tiles = prep;
+    B.n_tiles = static_cast<int64_t>(B.tasks.size());
+    if (num_ctas > 1 && B.tasks.size() > static_cast<size_t>(num_ctas)) balance_task_list(B.tasks, num_ctas);
+    return true;
 }
 
 int default_slices(int mode, int64_t m) {

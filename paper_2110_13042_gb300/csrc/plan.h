@@ -82,6 +82,21 @@ struct LeafTask {
     int64_t out_ld;         // output leading dimension (elements)
     int32_t hbits;          // extra fraction bits of T for short contractions
     int32_t k0v;            // contraction offset of the column operand (k0: row operand)
+    int32_t prob;           // batched calls: problem index (planes and C of that problem)
+    int32_t pad;
+};
+
+// One problem of a batched call (device table, one entry per problem).
+struct BatchProb {
+    const void *A;          // A_i (device)
+    void *C;                // C_i (device)
+    int64_t m, n, lda, ldc;
+    int64_t col_off;        // first column of this problem in the batch's exponent array
+    int64_t plane_off;      // byte offset of its digit planes in the planes block
+    int64_t ncb;            // 32-column image blocks per digit plane
+    int64_t K_pitch;        // contraction rows of its planes (multiple of PREP_K)
+    int64_t P_pad;          // columns written by prep (multiple of TILE)
+    int64_t prep_base;      // first prep tile of this problem (prefix over problems)
 };
 
 // Extra fraction bits of the leaf's int64 sum for a contraction of K rows:
@@ -156,6 +171,29 @@ struct Plan {
     double leaf_madds = 0, plain_madds = 0;   // per digit pair / per FP64 product
     bool uses_digits() const { return p.mode != MODE_F64; }
 };
+
+// Plan of a batched call: every problem as plain lower-triangle tiles of
+// its own digit planes, all tiles in one task list.
+struct BatchPlan {
+    int mode = MODE_F32;
+    int slices = 0;
+    int64_t count = 0;
+    std::vector<BatchProb> probs;
+    std::vector<LeafTask> tasks;
+    int64_t n_tiles = 0;
+    int64_t total_cols = 0;     // exponent entries
+    int64_t plane_bytes = 0;    // digit planes of all problems
+    int64_t prep_tiles = 0;
+    int64_t max_col_chunks = 0; // max over problems of ceil(n / 256)
+    double leaf_madds = 0;
+};
+
+// Build the batched plan for `count` problems (host arrays m, n, lda, ldc, A,
+// C).  Problems with n == 0 or m == 0 get no tiles (m == 0 is zero-filled by
+// the caller).  Returns false with *err set on invalid input.
+bool make_batch_plan(int mode, int slices, int num_ctas, int64_t count, const int64_t *m, const int64_t *n,
+                     const int64_t *lda, const int64_t *ldc, const void *const *A, void *const *C,
+                     BatchPlan *plan, std::string *err);
 
 // Digits per column for a mode (slices == 0 -> default).
 int default_slices(int mode, int64_t m);

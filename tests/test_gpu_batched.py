@@ -1,0 +1,154 @@
+"""ata_batched (one persistent launch over many problems) against the FP64
+oracle and against one ata_lower call per problem.
+
+Tolerances as in the single-call parity tests (relative to |A|^T|A|):
+F64_EMU <= 1e-13, F32 <= 5e-5, F32_BF16 within the one-digit rounding bound.
+Every problem of a batch is done as plain tiles of the same shape and digit
+arithmetic as a depth-0 ata_lower call, so the two must agree bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_13042_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F64, F64_EMU, F32, F32_BF16 = 0, 1, 2, 4
+
+
+@pytest.fixture(scope="module")
+def ata():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_13042_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def h(ata):
+    hd = ata.Handle(depth=0)
+    yield hd
+    hd.close()
+
+
+def dt(mode):
+    return torch.float32 if mode in (F32, F32_BF16) else torch.float64
+
+
+def make_batch(count, seed, mode, m_range=(1, 700), n_range=(1, 400), extra=()):
+    ms, ns = inputs.batch_shapes(count, seed, m_range, n_range)
+    shapes = [(int(a), int(b)) for a, b in zip(ms, ns)] + list(extra)
+    As = [inputs.uniform(m, n, seed + 17 * i) for i, (m, n) in enumerate(shapes)]
+    if mode in (F32, F32_BF16):
+        As = [a.astype(np.float32) for a in As]
+    return As
+
+
+def to_dev(As, mode):
+    Ad = [torch.from_numpy(np.ascontiguousarray(a)).to(dt(mode)).cuda() for a in As]
+    Cd = [torch.full((a.shape[1], a.shape[1]), float("nan"), dtype=dt(mode), device="cuda") for a in As]
+    return Ad, Cd
+
+
+def bf16_bound(A):
+    A = np.asarray(A, np.float64)
+    m = A.shape[0]
+    mx = np.max(np.abs(A), axis=0) if m else np.zeros(A.shape[1])
+    _, e = np.frexp(mx)
+    sc = np.where(mx > 0, np.ldexp(1.0, e), 0.0)
+    S = np.sum(np.abs(A), axis=0)
+    return 2.0 ** -8 * (sc[:, None] * S[None, :] + S[:, None] * sc[None, :]) + \
+        m * 2.0 ** -16 * sc[:, None] * sc[None, :]
+
+
+def check_against_oracle(A, C, mode):
+    n = A.shape[1]
+    low = np.tril_indices(n)
+    assert np.all(np.isnan(C[np.triu_indices(n, 1)])), "strict upper triangle written"
+    A64 = np.asarray(A, np.float64)
+    ref = oracle.ata_lower(A64)
+    D = oracle.abs_ata_lower(A64)
+    e = np.abs(C[low] - ref[low])
+    if mode == F32_BF16:
+        B = bf16_bound(A)
+        assert np.all(e <= B[low] * (1 + 1e-6) + 1e-30)
+        return
+    d = D[low]
+    assert np.all(e[d == 0] == 0)
+    if np.any(d > 0):
+        tol = 1e-13 if mode == F64_EMU else 5e-5
+        assert float(np.max(e[d > 0] / d[d > 0])) <= tol
+
+
+@pytest.mark.parametrize("mode", [F64_EMU, F32, F32_BF16])
+def test_batched_matches_oracle_and_single_calls(ata, h, mode):
+    extra = [(0, 5), (7, 0), (1, 1), (1, 130), (300, 1), (97, 257)]
+    As = make_batch(60, 11, mode, extra=extra)
+    Ad, Cd = to_dev(As, mode)
+    h.batched(Ad, Cd, mode)
+    assert h.sync() == 0
+    for A, Ct in zip(As, Cd):
+        C = Ct.cpu().numpy().astype(np.float64)
+        if A.shape[1] == 0:
+            continue
+        if A.shape[0] == 0:
+            n = A.shape[1]
+            assert np.all(C[np.tril_indices(n)] == 0) and np.all(np.isnan(C[np.triu_indices(n, 1)]))
+            continue
+        check_against_oracle(A, C, mode)
+    # one ata_lower per problem (depth 0): identical bits
+    single = ata.Handle(depth=0)
+    try:
+        for A, Ab, Cb in zip(As, Ad, Cd):
+            if A.shape[0] == 0 or A.shape[1] == 0:
+                continue
+            Cs = torch.full_like(Cb, float("nan"))
+            single.lower(Ab, Cs, mode)
+            assert single.sync() == 0
+            low = torch.tril_indices(A.shape[1], A.shape[1], device="cuda")
+            assert torch.equal(Cs[low[0], low[1]], Cb[low[0], low[1]])
+    finally:
+        single.close()
+
+
+def test_batched_repeatable_and_graph_capturable(h):
+    mode = F32
+    As = make_batch(40, 3, mode, m_range=(16, 2000), n_range=(8, 600))
+    Ad, Cd = to_dev(As, mode)
+    h.batched(Ad, Cd, mode)
+    assert h.sync() == 0
+    first = [c.clone() for c in Cd]
+    for c in Cd:
+        c.fill_(float("nan"))
+    h.batched(Ad, Cd, mode)  # cached plan: no host work, same bits
+    assert h.sync() == 0
+    for a, b in zip(first, Cd):
+        assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0))
+    # the same call captured in a CUDA graph and replayed
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    for c in Cd:
+        c.fill_(float("nan"))
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        h.batched(Ad, Cd, mode, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert h.sync() == 0
+    for a, b in zip(first, Cd):
+        assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0))
+
+
+def test_batched_errors(ata, h):
+    A = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
+    C = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    assert h.batched_ptr([], [], [], [], [], [], F64_EMU) == 0
+    # native FP64 is not a batched mode
+    assert h.batched_ptr([8], [4], [A.data_ptr()], [4], [C.data_ptr()], [4], F64) == 6
+    # leading dimension below n
+    assert h.batched_ptr([8], [4], [A.data_ptr()], [3], [C.data_ptr()], [4], F64_EMU) == 1
+    # A overlapping C
+    assert h.batched_ptr([8], [4], [A.data_ptr()], [4], [A.data_ptr()], [4], F64_EMU) == 1
+    # unknown dtype
+    assert h.batched_ptr([8], [4], [A.data_ptr()], [4], [C.data_ptr()], [4], 9) == 2
