@@ -159,6 +159,24 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out);
 int ata_set_timing(ata_handle h, int enable);
 int ata_phase_times(ata_handle h, double *out);
 
+/* Autotuning of the planning parameters (the recursion cutoff, Strassen
+ * depth and the smallest block Strassen splits) for one shape.  Candidate
+ * configurations are planned on the host (identical plans are run once),
+ * timed with CUDA events on `stream` using the caller's A and C (C ends up
+ * holding low(A^T A)), and the fastest is stored in the handle's tuning
+ * table under (m, n, dtype).  Later ata_lower / ata_plan_info calls with that
+ * shape use it whenever the handle's configuration leaves cutoff, depth and
+ * strassen_min on auto (0, -1, 0).  Synchronous; budget_ms bounds the total
+ * time spent (candidates are tried cheapest-plan first, plain tiles always).
+ * out (host, may be NULL) receives {cutoff, depth, strassen_min, candidates
+ * timed} of the choice.  Errors: as ata_lower. */
+#define ATA_TUNE_FIELDS 4
+int ata_tune(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc, int dtype,
+             void *stream, double budget_ms, int64_t *out);
+
+/* Forget every tuned shape of the handle. */
+int ata_tune_clear(ata_handle h);
+
 /* Allocation-free variant of ata_lower, for callers that cannot allocate
  * device memory when they need the product (inside a CUDA-graph capture they
  * do not control, under a framework memory pool that forbids side

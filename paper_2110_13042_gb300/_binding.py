@@ -56,9 +56,11 @@ def load():
     L.ata_last_error.restype = ctypes.c_char_p
     L.ata_set_timing.argtypes = [vp, ip]
     L.ata_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.ata_tune.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp, ctypes.c_double, ctypes.POINTER(i64)]
+    L.ata_tune_clear.argtypes = [vp]
     for f in ("ata_create", "ata_set_config", "ata_lower", "ata_batched", "ata_sync",
               "ata_destroy", "ata_plan_info", "ata_version", "ata_set_timing",
-              "ata_phase_times"):
+              "ata_phase_times", "ata_tune", "ata_tune_clear"):
         getattr(L, f).restype = ip
     _lib = L
     return L
@@ -161,6 +163,20 @@ class Handle:
                               dtype, stream)
         if rc != 0:
             raise AtaError(rc, f"ata_batched [{self.last_error()}]")
+
+    def tune(self, A, C, dtype, stream=None, budget_ms: float = 3000.0) -> dict:
+        """ata_tune on row-major CUDA tensors A (m x n) and C (n x n): time the
+        candidate plans, keep the fastest for this shape, leave low(A^T A) in C."""
+        m, n = A.shape
+        out = (ctypes.c_int64 * 4)()
+        rc = int(load().ata_tune(self._h, int(m), int(n), A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0),
+                                 int(dtype), _stream_ptr(stream), float(budget_ms), out))
+        if rc != 0:
+            raise AtaError(rc, f"ata_tune [{self.last_error()}]")
+        return {"cutoff": out[0], "depth": out[1], "strassen_min": out[2], "candidates": out[3]}
+
+    def tune_clear(self):
+        _check(load().ata_tune_clear(self._h), "ata_tune_clear")
 
     def set_timing(self, enable: bool = True):
         _check(load().ata_set_timing(self._h, 1 if enable else 0), "ata_set_timing")

@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -65,6 +66,8 @@ struct ata_handle_s {
     const CachedPlan *resident = nullptr;  // whose tables are in the workspace
     std::map<Key, std::unique_ptr<CachedPlan>> plans;
     std::unique_ptr<CachedBatch> batch;
+    // autotuned {cutoff, depth, strassen_min} per (m, n, dtype)
+    std::map<std::tuple<int64_t, int64_t, int>, std::tuple<int, int, int>> tuned;
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -158,6 +161,17 @@ int bind_plan(ata_handle h, CachedPlan &cp) {
     cp.ws_generation = h->ws_generation;
     if (h->resident == &cp) h->resident = nullptr;
     return ATA_OK;
+}
+
+// The handle's configuration, with an autotuned choice for (m, n, dtype)
+// applied when cutoff, depth and strassen_min are all on auto.
+ata_config effective_cfg(ata_handle h, int64_t m, int64_t n, int dtype) {
+    ata_config c = h->cfg;
+    if (c.cutoff == 0 && c.strassen_depth == -1 && c.strassen_min == 0) {
+        auto it = h->tuned.find(std::make_tuple(m, n, dtype));
+        if (it != h->tuned.end()) std::tie(c.cutoff, c.strassen_depth, c.strassen_min) = it->second;
+    }
+    return c;
 }
 
 CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
@@ -281,7 +295,7 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
     ata_config cfg{};
     cfg.strassen_depth = -1;
-    if (h) cfg = h->cfg;
+    if (h) cfg = effective_cfg(h, m, n, dtype);
     Plan P;
     std::string err;
     if (!make_plan(params_for(cfg, m, n, n > 0 ? n : 1, n > 0 ? n : 1, dtype), &P, &err))
@@ -315,7 +329,7 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
     if (ranges_overlap(A, ((m - 1) * lda + n) * es, C, ((n - 1) * ldc + n) * es)) return ATA_ERR_INVALID;
 
     int status = ATA_OK;
-    PlanParams pp = params_for(h->cfg, m, n, lda, ldc, dtype);
+    PlanParams pp = params_for(effective_cfg(h, m, n, dtype), m, n, lda, ldc, dtype);
     pp.num_ctas = h->num_sms;
     CachedPlan *cp = get_plan(h, pp, &status);
     if (!cp) return status;
@@ -364,6 +378,98 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
         return fail(h, ATA_ERR_CUDA, "combine launch", e);
     mark(4);
     if (h->timing) h->timed = true;
+    return ATA_OK;
+}
+
+int ata_tune(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc, int dtype,
+             void *stream, double budget_ms, int64_t *out) {
+    if (!h) return ATA_ERR_INVALID;
+    if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
+    if (m < 0 || n < 0) return ATA_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const ata_config saved = h->cfg;
+    const bool saved_timing = h->timing;
+    h->timing = false;
+    // Candidates, plain tiles first; plans that come out identical are
+    // timed once.
+    struct Cand {
+        int cutoff, depth, smin;
+    };
+    std::vector<Cand> cands{{0, 0, 0}};
+    for (int d = 1; d <= 3; ++d)
+        for (int smin : {4096, 2048, 1024})
+            for (int cut : {0, static_cast<int>(n / 8)}) cands.push_back({cut, d, smin});
+    std::vector<std::tuple<int64_t, int64_t, int64_t, int64_t, int64_t>> seen;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return ATA_ERR_CUDA;
+    }
+    int rc = ATA_OK, timed = 0;
+    float best_ms = -1.f, spent = 0.f;
+    Cand best{0, 0, 0};
+    for (const Cand &c : cands) {
+        ata_config cfg = saved;
+        cfg.cutoff = c.cutoff;
+        cfg.strassen_depth = c.depth;
+        cfg.strassen_min = c.smin;
+        Plan P;
+        std::string err;
+        if (!make_plan(params_for(cfg, m, n, lda, ldc, dtype), &P, &err)) continue;
+        if (c.depth > 0 && P.n_products == 0) continue;  // no block large enough
+        // plan content, not the requested knobs (a depth the blocks cannot
+        // reach plans the same as a smaller one)
+        auto sig = std::make_tuple(P.n_products, P.n_tiles, P.n_blocks, P.n_panels,
+                                   static_cast<int64_t>(P.ops.size()));
+        bool dup = false;
+        for (const auto &x : seen) dup = dup || x == sig;
+        if (dup) continue;
+        seen.push_back(sig);
+        if (timed > 0 && spent > budget_ms) break;
+        h->cfg = cfg;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && rc == ATA_OK; ++rep) {  // first call warms (plan, workspace)
+            if (rep > 0 && cudaEventRecord(e0, s) != cudaSuccess) rc = ATA_ERR_CUDA;
+            if (rc == ATA_OK) rc = ata_lower(h, m, n, A, lda, C, ldc, dtype, stream);
+            if (rc == ATA_OK && rep > 0) {
+                float t = 0.f;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                    rc = ATA_ERR_CUDA;
+                ms = rep == 1 ? t : std::min(ms, t);
+                spent += t;
+            }
+        }
+        if (rc != ATA_OK) break;
+        ++timed;
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cfg = saved;
+    h->timing = saved_timing;
+    if (rc != ATA_OK) return rc;
+    h->tuned[std::make_tuple(m, n, dtype)] = std::make_tuple(best.cutoff, best.depth, best.smin);
+    // leave C holding the product of the chosen configuration
+    rc = ata_lower(h, m, n, A, lda, C, ldc, dtype, stream);
+    if (rc != ATA_OK) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ATA_ERR_CUDA;
+    if (out) {
+        out[0] = best.cutoff;
+        out[1] = best.depth;
+        out[2] = best.smin;
+        out[3] = timed;
+    }
+    return ATA_OK;
+}
+
+int ata_tune_clear(ata_handle h) {
+    if (!h) return ATA_ERR_INVALID;
+    h->tuned.clear();
     return ATA_OK;
 }
 
