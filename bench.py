@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--seed", type=int, default=2110)
-    ap.add_argument("--no-extras", action="store_true", help="skip plain-tiled, e2e, cpu baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain-tiled, e2e, batched, cpu baseline")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (auto plan instead)")
+    ap.add_argument("--tune-budget-ms", type=float, default=3000.0)
+    ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--ref-seconds", type=float, default=4.0, help="CPU seconds per reference step")
     return ap.parse_args()
 
@@ -140,6 +143,46 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def batched_bench(ata, torch, dev, stream, args, timed):
+    """Many independent Gram products: count FP32 problems with m log-uniform
+    in [64, 4096] and n log-uniform in [32, 1024], entries U[-1, 1) drawn on
+    the device from a seeded generator; ata_batched (one persistent launch)
+    against one ata_lower call per matrix."""
+    from paper_2110_13042_gb300 import inputs
+    count = args.batch_count
+    ms, ns = inputs.batch_shapes(count, args.seed, (64, 4096), (32, 1024))
+    ms, ns = [int(v) for v in ms], [int(v) for v in ns]
+    g = torch.Generator(device=dev)
+    g.manual_seed(args.seed)
+    abuf = torch.rand(sum(a * b for a, b in zip(ms, ns)), generator=g, device=dev) * 2 - 1
+    cbuf = torch.empty(sum(b * b for b in ns), device=dev)
+    As, Cs, oa, oc = [], [], 0, 0
+    for a, b in zip(ms, ns):
+        As.append(abuf[oa:oa + a * b].view(a, b))
+        Cs.append(cbuf[oc:oc + b * b].view(b, b))
+        oa += a * b
+        oc += b * b
+    eff = float(sum(a * b * b for a, b in zip(ms, ns)))
+    hb = ata.Handle()
+    ms_b = timed(lambda: hb.batched(As, Cs, ata.ATA_F32, stream), 3, 2)
+    hp = ata.Handle(depth=0)
+
+    def per_matrix():
+        for A, C in zip(As, Cs):
+            hp.lower(A, C, ata.ATA_F32, stream)
+    ms_p = timed(per_matrix, 1, 1)
+    rc = hb.sync(stream) or hp.sync(stream)
+    hb.close()
+    hp.close()
+    if rc:
+        raise RuntimeError(f"batched bench: status {rc}")
+    return {"metric": "batched A_i^T A_i effective TFLOP/s (sum m n^2)", "unit": "TFLOP/s",
+            "value": eff / (ms_b * 1e-3) / 1e12, "ms": ms_b, "problems": count,
+            "workload": f"{count} FP32 problems, m logU[64,4096], n logU[32,1024], U[-1,1) on device (seed {args.seed})",
+            "one_launch_per_matrix": {"value": eff / (ms_p * 1e-3) / 1e12, "ms": ms_p},
+            "a_bytes": int(abuf.numel() * 4), "c_bytes": int(cbuf.numel() * 4)}
 
 
 def cpu_oracle_sample(A_cols_fn, m, n, target_s, threads=0):
@@ -232,8 +275,12 @@ def main():
     A = torch.from_numpy(A_host).to(dev)
     C = torch.zeros((n, n), dtype=tdt, device=dev)
     h = ata.Handle(cutoff=args.cutoff, depth=args.depth, slices=args.slices)
-    info = ata.plan_info(m, n, mode, h)
     stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if args.depth < 0 and args.cutoff == 0 and not args.no_tune:
+        # autotuned plan for this shape (outside every timed region)
+        tuned = h.tune(A, C, mode, stream, budget_ms=args.tune_budget_ms)
+    info = ata.plan_info(m, n, mode, h)
 
     def step():
         h.lower(A, C, mode, stream)
@@ -310,6 +357,7 @@ def main():
                                   "lower triangle of C = A^T A",
                       "mode": args.mode.upper(), "strassen_depth": info["depth"],
                       "cutoff": info["cutoff"], "slices": slices,
+                      "plan": "autotuned (ata_tune)" if tuned else "fixed",
                       "l2": "inputs larger than L2 (A and C 512 MiB each)"},
            "roofline": roof,
            "phases_ms": {"colexp": ph[0], "prep": ph[1], "leaf": ph[2], "combine": ph[3]},
@@ -347,6 +395,7 @@ def main():
         ref, den = oracle.dot_pairs(np.ascontiguousarray(A64[:, j].T), np.ascontiguousarray(A64[:, k].T))
         out["error_vs_oracle"] = {"max_rel_to_absAtA": float(np.max(np.abs(got - ref) / den)),
                                   "samples": 400}
+        out["batched"] = batched_bench(ata, torch, dev, stream, args, timed)
         if rank == 0 and world == 1:
             v, dt, cores, desc = cpu_oracle_sample(
                 lambda nb: np.ascontiguousarray(A64[:, :nb]), m, n, 12.0)

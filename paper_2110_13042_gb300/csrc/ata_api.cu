@@ -197,7 +197,7 @@ CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
         }
         std::memcpy(cp->pinned, cp->tables.data(), cp->tables.size());
     }
-    if (h->plans.size() > 64) h->plans.clear(), h->resident = nullptr;
+    if (h->plans.size() >= 8192) h->plans.clear(), h->resident = nullptr;  // bound the cache
     CachedPlan *raw = cp.get();
     h->plans[key] = std::move(cp);
     return raw;
