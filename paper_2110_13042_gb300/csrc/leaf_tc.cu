@@ -80,7 +80,13 @@ __host__ __device__ constexpr int acc_of(int p, int q) {
 
 // Accumulators due for draining at the end of 64-row chunk `c`.  The most
 // frequently drained accumulator present is in every non-empty mask.
+// With at most 3 digits (the FP32 modes, whose stated bound is 5e-5 or the
+// one-digit rounding bound) only acc0 must stay exact: acc1 and acc2 (weights
+// 2^-9 and 2^-18) are drained with it every 256 rows, where they stay below
+// 2^31 in their units (2 and 3 pairs x 256 rows x 2^16) so the 32-bit
+// conversion still applies, and their FP32 rounding is ~2^-33 relative.
 __device__ __forceinline__ uint32_t due_mask(int c, bool last, int nacc) {
+    if (nacc <= 3) return ((c & 3) == 3 || last) ? (1u << nacc) - 1u : 0u;
     uint32_t m = (1u << 2) | (1u << 3);             // acc2, acc3 every chunk
     if ((c & 1) == 1 || last) m |= 1u << 1;          // acc1 every 2 chunks
     if ((c & 3) == 3 || last) m |= 1u | (1u << 4);   // acc0, acc4 every 4 chunks
@@ -181,25 +187,31 @@ __device__ __forceinline__ bool step_acc(IssueState &st, Shared *sh, uint32_t tm
 }
 
 // Add one drained accumulator (16 columns) into T, kept in units of
-// 2^-(27 + h) of the leading digit product (h extra bits for short K).
-template <int ACC>
+// 2^-(27 + h) of the leading digit product (h extra bits for short K).  The
+// scaled value x is an exact integer (|x| <= 2^24).  WIDE: x * 2^s + T as one
+// widening multiply-add (s <= 30 for acc1..acc3), fewer epilogue instructions;
+// it pays where drains dominate (S <= 3), while for larger S its extra live
+// registers spill and the shift-add form is faster.
+template <int ACC, bool WIDE>
 __device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int h, float fold_scale) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const float v = __uint_as_float(r[i]);
         if (ACC == 0) {
             T[i] += static_cast<int64_t>(__float2int_rn(v)) << (27 + h);
-        } else if (ACC == 1) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 512.0f)) << (18 + h);
-        } else if (ACC == 2) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 262144.0f)) << (9 + h);
-        } else if (ACC == 3) {
-            T[i] += static_cast<int64_t>(__float2int_rn(v * 134217728.0f)) << h;
-        } else {
+        } else if (ACC == 4) {
             // |acc4| * 2^(27 + h) < 2^27 (p + q >= 6 terms over <= 256 rows,
             // h <= 9), so the 32-bit conversion is exact in range; the
             // 64-bit one runs at a small fraction of its rate.
             T[i] += static_cast<int64_t>(__float2int_rn(v * fold_scale));
+        } else {
+            constexpr float sc = ACC == 1 ? 512.0f : ACC == 2 ? 262144.0f : 134217728.0f;
+            constexpr int s0 = ACC == 1 ? 18 : ACC == 2 ? 9 : 0;
+            const int x = __float2int_rn(v * sc);
+            if constexpr (WIDE)
+                T[i] += static_cast<int64_t>(x) * static_cast<int64_t>(1 << (s0 + h));
+            else
+                T[i] += static_cast<int64_t>(x) << (s0 + h);
         }
     }
 }
@@ -207,7 +219,7 @@ __device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int 
 // Drain one accumulator: both TMEM loads are issued before a single wait,
 // and the accumulator is handed back to the MMA issuer before the (longer)
 // conversion work.
-template <int ACC>
+template <int ACC, bool WIDE>
 __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh,
                                           int h, float fold_scale) {
     static_assert(EPI_COLS == 32, "two 16-column loads");
@@ -217,8 +229,8 @@ __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase
     tmem_ld_wait();
     tc_fence_before();
     mbar_arrive(&sh->acce[ACC]);
-    absorb<ACC>(T, r0, h, fold_scale);
-    absorb<ACC>(T + 16, r1, h, fold_scale);
+    absorb<ACC, WIDE>(T, r0, h, fold_scale);
+    absorb<ACC, WIDE>(T + 16, r1, h, fold_scale);
 }
 
 template <int S>
@@ -380,11 +392,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 }
                 accf_phase ^= 1u;
                 tc_fence_after();
-                if (due & 16u) drain_one<4>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 1u) drain_one<0>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 2u) drain_one<1>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 4u) drain_one<2>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 8u) drain_one<3>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 16u) drain_one<4, (S <= 3)>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 1u) drain_one<0, (S <= 3)>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 2u) drain_one<1, (S <= 3)>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 4u) drain_one<2, (S <= 3)>(T, tbase, colbase, sh, h, fold_scale);
+                if (due & 8u) drain_one<3, (S <= 3)>(T, tbase, colbase, sh, h, fold_scale);
             }
             if (!ok) break;
             const LeafTask t = p.tasks[ti];
