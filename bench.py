@@ -19,8 +19,10 @@ and value = total work of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -143,6 +145,26 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def leaf_traffic(mode, m, n, depth, slices):
+    """DRAM bytes per leaf launch from the committed ncu summary, when it was
+    taken on this configuration and on the current leaf sources; else None."""
+    if (mode, m, n, depth, slices) != (1, 8192, 8192, 1, 6):
+        return None
+    try:
+        with open(os.path.join(ROOT, "profiles", "leaf_tc_s6_n8192_depth1_dram.md")) as f:
+            text = f.read()
+    except OSError:
+        return None
+    mt = re.search(r"traffic_bytes_per_launch: (\d+) sources: ([0-9a-f]+)", text)
+    if not mt:
+        return None
+    h = hashlib.sha256()
+    for name in ("leaf_tc.cu", "ptx.cuh", "plan.cpp"):
+        with open(os.path.join(ROOT, "paper_2110_13042_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return int(mt.group(1)) if h.hexdigest()[:16] == mt.group(2) else None
 
 
 def batched_bench(ata, torch, dev, stream, args, timed):
@@ -346,7 +368,8 @@ def main():
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         roof = {"bound": "tensor", "kernel": f"leaf_tc_kernel<{slices}> (tcgen05 BF16)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": leaf_traffic(mode, m, n, info["depth"], slices),
+                "traffic_unit": "DRAM bytes per leaf launch (ncu, profiles/)",
                 "peak_source": f"{src} bf16 dense sustained",
                 "work": f"{pairs} digit pairs x 2 x {info['leaf_madds']} tile multiply-adds"}
 
