@@ -137,3 +137,47 @@ def hadamard(m: int, n: int) -> np.ndarray:
     while H.shape[0] < m:
         H = np.block([[H, H], [H, -H]])
     return H[:, :n] * 2.0 ** (-k)
+
+
+# ------------------------------------------------------------ on-device --
+# Inputs of several GB are drawn on the GPU from torch's seeded Philox
+# generator (same distributions as above, different streams): the parity
+# tests pull the sampled columns back from the device copy, so the oracle
+# sees exactly the values the library saw.
+
+def _torch_gen(seed: int, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def device_uniform(m: int, n: int, seed: int, device, dtype=None):
+    """i.i.d. U[-1, 1) entries on ``device``."""
+    import torch
+    g = _torch_gen(seed, device)
+    return torch.rand((m, n), generator=g, device=device, dtype=dtype or torch.float64) * 2 - 1
+
+
+def device_column_scaled_normal(m: int, n: int, seed: int, device, dtype=None):
+    """N(0,1) entries with column j scaled by 10^U(-3,3), on ``device``."""
+    import torch
+    dt = dtype or torch.float64
+    g = _torch_gen(seed, device)
+    scale = 10.0 ** (torch.rand(n, generator=g, device=device, dtype=torch.float64) * 6 - 3)
+    A = torch.randn((m, n), generator=g, device=device, dtype=torch.float64)
+    A.mul_(scale[None, :])
+    return A.to(dt)
+
+
+def device_low_rank_stressed(m: int, n: int, seed: int, device, rank: int = 16, magnitude: float = 1e4,
+                             dtype=None):
+    """U[-1,1) + magnitude * (G1 G2^T) / 4 with G1 (m x rank), G2 (n x rank)
+    i.i.d. N(0,1), on ``device``."""
+    import torch
+    g = _torch_gen(seed, device)
+    A = torch.rand((m, n), generator=g, device=device, dtype=torch.float64) * 2 - 1
+    G1 = torch.randn((m, rank), generator=g, device=device, dtype=torch.float64)
+    G2 = torch.randn((n, rank), generator=g, device=device, dtype=torch.float64)
+    A.addmm_(G1, G2.T, alpha=magnitude / 4.0)
+    return A.to(dtype or torch.float64)
