@@ -195,6 +195,20 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 lanes x 16 columns of zeros into TMEM (warp-wide, this warp's lanes).
+__device__ __forceinline__ void tmem_st_zero_32x32b_x16(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor (tcgen05 format) for a K-major operand tile
 // stored with the 64-byte swizzle: rows of 64 bytes (32 BF16 along K), 8-row
 // core-matrix groups 512 bytes apart.  The tile must start on a 512-byte
