@@ -236,16 +236,17 @@ __device__ __forceinline__ void store_digits(const int64_t (&w)[KSTEP], uint8_t 
 constexpr int PREP_SMEM_OPS = 64;
 constexpr int PREP_SMEM_TERMS = 128;
 
-// sV[kr0 + 4 it][cc] = sum over the op's terms of coef * round(a * 2^sh) for
-// the 16 rows k0 + kr0 + 4 it of column c0 + cc.  NT > 0 (1, 2 or 4 terms; a
-// missing fourth reads nothing): the rows go in groups of 16 / NT, every
-// term's loads of a group are issued before any is used (16 loads in flight
-// per thread whatever the term count), and a group's sums go to shared memory
-// as soon as they are complete.  NT = 0: any count, one term at a time.
+// sV[it][cc] = sum over the op's terms of coef * round(a * 2^sh) for the 16
+// rows k0 + it of column c0 + cc (one thread per column; a warp loads 32
+// consecutive columns of a row).  NT > 0 (1, 2 or 4 terms; a missing fourth
+// reads nothing): the rows go in groups of 16 / NT, every term's loads of a
+// group are issued before any is used (16 loads in flight per thread whatever
+// the term count), and a group's sums go to shared memory as soon as they are
+// complete.  NT = 0: any count, groups of four rows, one term at a time.
 template <int S, int NT, typename T>
 __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                            const OpDesc &od, const OpTerm *terms, int k0, int c0, int cc,
-                                           int kr0, int64_t (*sV)[PREP_C + 1]) {
+                                           int64_t (*sV)[PREP_TC + 1]) {
     constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
     auto fixed = [](T a, int sh) -> int64_t {
         if constexpr (FastFixed<F, T>::ok)
@@ -255,27 +256,26 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
     };
     const int c = c0 + cc;
     if constexpr (NT > 0) {
-        constexpr int G = 16 / NT;  // rows per group
-        const T *base[NT];          // element (k0 + kr0, column) of each term
+        constexpr int G = PREP_TK / NT;  // rows per group
+        const T *base[NT];               // element (k0, column) of each term
         int lim[NT], sh[NT], neg[NT];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const bool present = t < od.nterms;
             const OpTerm tm = present ? terms[od.first_term + t] : OpTerm{};
             const bool cv = present && c < tm.cols;
-            base[t] = A + (tm.row0 + k0 + kr0) * lda + tm.col0 + c;
-            lim[t] = cv ? tm.rows - k0 - kr0 : 0;  // rows 4 it < lim are inside the term
+            base[t] = A + (tm.row0 + k0) * lda + tm.col0 + c;
+            lim[t] = cv ? tm.rows - k0 : 0;  // rows it < lim are inside the term
             sh[t] = cv ? F - od.t_shift - expo[tm.col0 + c] : 0;
             neg[t] = tm.coef < 0;
         }
 #pragma unroll
-        for (int g = 0; g < 16; g += G) {
+        for (int g = 0; g < PREP_TK; g += G) {
             T raw[NT][G];
 #pragma unroll
             for (int t = 0; t < NT; ++t)
 #pragma unroll
-                for (int j = 0; j < G; ++j)
-                    raw[t][j] = 4 * (g + j) < lim[t] ? base[t][4 * (g + j) * lda] : T(0);
+                for (int j = 0; j < G; ++j) raw[t][j] = (g + j) < lim[t] ? base[t][(g + j) * lda] : T(0);
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 int64_t v = 0;
@@ -284,14 +284,12 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                     const int64_t x = fixed(raw[t][j], sh[t]);
                     v += neg[t] ? -x : x;
                 }
-                sV[kr0 + 4 * (g + j)][cc] = v;
+                sV[g + j][cc] = v;
             }
         }
     } else {
-        // more than four terms (Strassen depth >= 3): groups of four rows,
-        // one term at a time
 #pragma unroll 1
-        for (int g = 0; g < 16; g += 4) {
+        for (int g = 0; g < PREP_TK; g += 4) {
             int64_t v[4] = {0, 0, 0, 0};
             for (int t = 0; t < od.nterms; ++t) {
                 const OpTerm tm = terms[od.first_term + t];
@@ -300,7 +298,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                 T raw[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int k = k0 + kr0 + 4 * (g + j);
+                    const int k = k0 + g + j;
                     raw[j] = (cvalid && k < tm.rows) ? col[(tm.row0 + k) * lda] : T(0);
                 }
                 const int sh = cvalid ? F - od.t_shift - expo[tm.col0 + c] : 0;
@@ -311,47 +309,48 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) sV[kr0 + 4 * (g + j)][cc] = v[j];
+            for (int j = 0; j < 4; ++j) sV[g + j][cc] = v[j];
         }
     }
 }
 
+// One 16 x 256 prep tile of an operand: read phase (above), then each thread
+// writes its column's 32-byte image row of every digit plane as two 16-byte
+// stores; a warp fills one 1 KB image per digit and a tile 8 KB runs.
 template <int S, typename T>
 __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                           const OpDesc &od, const OpTerm *terms, int64_t tile,
-                                          const Family &fam, uint8_t *ws, int64_t (*sV)[PREP_C + 1]) {
+                                          const Family &fam, uint8_t *ws, int64_t (*sV)[PREP_TC + 1]) {
     const int64_t local = tile - od.tile_base;
-    const int tiles_k = od.K_pitch / PREP_K;
-    const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
-    const int c0 = static_cast<int>(local / tiles_k) * PREP_C;
-
-    const int cc = threadIdx.x & 63;
-    const int kr0 = threadIdx.x >> 6;
+    const int tiles_k = od.K_pitch / PREP_TK;
+    const int k0 = static_cast<int>(local % tiles_k) * PREP_TK;
+    const int c0 = static_cast<int>(local / tiles_k) * PREP_TC;
+    const int cc = threadIdx.x;  // column within the tile
     switch (od.nterms) {
-        case 1: read_terms<S, 1>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
-        case 2: read_terms<S, 2>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
+        case 1: read_terms<S, 1>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
+        case 2: read_terms<S, 2>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
         case 3:
-        case 4: read_terms<S, 4>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
-        default: read_terms<S, 0>(A, lda, expo, od, terms, k0, c0, cc, kr0, sV); break;
+        case 4: read_terms<S, 4>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
+        default: read_terms<S, 0>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
     }
     __syncthreads();
 
-    const int64_t ncb = fam.cols / BLOCK_COLS;
-    const int c = threadIdx.x & 63;    // operand column within the tile
-    const int ks = threadIdx.x >> 6;   // contraction step within the tile
-    const int r = c & (BLOCK_COLS - 1);
-    constexpr int64_t CADD = [] {
-        int64_t v = 0;
-        for (int j = 0; j < S - 1; ++j) v += int64_t(256) << (DIGIT_BITS * j);
-        return v;
-    }();
-    int64_t w[KSTEP];
+    if (c0 + cc < od.P_pad) {
+        const int64_t ncb = fam.cols / BLOCK_COLS;
+        const int r = cc & (BLOCK_COLS - 1);
+        constexpr int64_t CADD = [] {
+            int64_t v = 0;
+            for (int j = 0; j < S - 1; ++j) v += int64_t(256) << (DIGIT_BITS * j);
+            return v;
+        }();
+        int64_t w[KSTEP];
 #pragma unroll
-    for (int i = 0; i < KSTEP; ++i) w[i] = sV[ks * KSTEP + i][c] + CADD;
-    const int64_t kstep = (k0 / KSTEP) + ks;
-    const int64_t cblk = (od.out_col + c0 + c) / BLOCK_COLS;
-    uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
-    store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
+        for (int i = 0; i < KSTEP; ++i) w[i] = sV[i][cc] + CADD;
+        const int64_t kstep = k0 / KSTEP;
+        const int64_t cblk = (od.out_col + c0 + cc) / BLOCK_COLS;
+        uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
+        store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
+    }
     __syncthreads();  // sV is reused by the block's next tile
 }
 
@@ -361,7 +360,7 @@ __global__ void __launch_bounds__(256, 3) prep_digits_kernel(const T *__restrict
                                                              const OpDesc *__restrict__ ops, int nops,
                                                              const OpTerm *__restrict__ terms, int nterms,
                                                              int64_t ntiles, Families fams, uint8_t *ws) {
-    __shared__ int64_t sV[PREP_K][PREP_C + 1];
+    __shared__ int64_t sV[PREP_TK][PREP_TC + 1];
     __shared__ OpDesc s_ops[PREP_SMEM_OPS];
     __shared__ OpTerm s_terms[PREP_SMEM_TERMS];
     const bool cached = nops <= PREP_SMEM_OPS && nterms <= PREP_SMEM_TERMS;
@@ -386,7 +385,7 @@ template <int S, typename T>
 __global__ void __launch_bounds__(256, 3) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
                                                               const int *__restrict__ expo, int64_t ntiles,
                                                               uint8_t *planes) {
-    __shared__ int64_t sV[PREP_K][PREP_C + 1];
+    __shared__ int64_t sV[PREP_TK][PREP_TC + 1];
     int64_t tile = blockIdx.x;
     if (tile >= ntiles) return;
     int64_t lo = 0, hi = count - 1;  // last problem with prep_base <= tile

@@ -71,7 +71,7 @@ Layout layout_for(int64_t m, int64_t n, int slices) {
     L.fam.plane_elems = L.fam.cols * L.fam.K_pitch;
     L.planes = take(L.fam.plane_elems * 2 * slices);
     L.fam.offset = L.planes;
-    L.prep_tiles = (L.fam.K_pitch / PREP_K) * (p_pad / PREP_C);
+    L.prep_tiles = prep_tiles_for(true, L.fam.K_pitch, p_pad);
     L.total = off;
     return L;
 }

@@ -477,7 +477,7 @@ bool make_batch_plan(int mode, int slices, int num_ctas, int64_t count, const in
         q.ncb = cols / BLOCK_COLS;
         col_off += n[i];
         plane_off += q.K_pitch * cols * 2 * B.slices;
-        prep += (q.K_pitch / PREP_K) * (q.P_pad / PREP_C);
+        prep += prep_tiles_for(true, q.K_pitch, q.P_pad);
         B.max_col_chunks = std::max<int64_t>(B.max_col_chunks, ceil_div(n[i], 256));
         const int kind = mode == MODE_F64_EMU ? OUT_C_F64 : OUT_C_F32;
         const int hb = hbits_for(m[i]);
@@ -616,7 +616,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     P.prep_tiles = 0;
     for (OpDesc &o : P.ops) {
         o.tile_base = P.prep_tiles;
-        P.prep_tiles += (o.K_pitch / PREP_K) * (o.P_pad / PREP_C);
+        P.prep_tiles += prep_tiles_for(B.digits, o.K_pitch, o.P_pad);
     }
     P.t_ops = 0;
     P.t_terms = round_up(P.t_ops + static_cast<int64_t>(P.ops.size() * sizeof(OpDesc)), 256);

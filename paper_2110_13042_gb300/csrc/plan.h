@@ -24,8 +24,12 @@ constexpr int64_t MAX_DIGIT_K = int64_t(1) << 19;  // keeps |T| < 2^63
 constexpr int BLOCK_COLS = 32;   // digit-plane image: 32 columns x KSTEP rows = 1 KB
 constexpr int BLOCK_BYTES = BLOCK_COLS * KSTEP * 2;
 constexpr int SPLIT_ALIGN = 32;  // AtA column splits are multiples of this
-constexpr int PREP_K = 64;       // prep tile: contraction rows
-constexpr int PREP_C = 64;       // prep tile: columns
+constexpr int PREP_K = 64;       // contraction pitch unit; native-FP64 prep tile rows
+constexpr int PREP_C = 64;       // native-FP64 prep tile columns
+// Digit-plane prep tile: 16 contraction rows (one K step) x 256 columns, so
+// a tile reads 2 KB row segments of A and writes 8 KB image runs per digit.
+constexpr int PREP_TK = KSTEP;
+constexpr int PREP_TC = 256;
 constexpr int MAX_FAMILIES = 6;  // operand families (tensor maps) per launch
 constexpr int MAX_SLICES = 7;
 
@@ -98,6 +102,11 @@ struct BatchProb {
     int64_t P_pad;          // columns written by prep (multiple of TILE)
     int64_t prep_base;      // first prep tile of this problem (prefix over problems)
 };
+
+// Prep tiles of one operand of K_pitch rows and P_pad columns.
+inline int64_t prep_tiles_for(bool digits, int64_t K_pitch, int64_t P_pad) {
+    return digits ? (K_pitch / PREP_TK) * ((P_pad + PREP_TC - 1) / PREP_TC) : (K_pitch / PREP_K) * (P_pad / PREP_C);
+}
 
 // Extra fraction bits of the leaf's int64 sum for a contraction of K rows:
 // T is kept in units of 2^-(T_FRAC + h) of the leading digit product, which
