@@ -355,7 +355,7 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
 }
 
 template <int S, typename T>
-__global__ void __launch_bounds__(256, 3) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
                                                              const int *__restrict__ expo,
                                                              const OpDesc *__restrict__ ops, int nops,
                                                              const OpTerm *__restrict__ terms, int nterms,
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(256, 3) prep_digits_kernel(const T *__restrict
 // problem table (prefix prep_base), so locating a tile's problem costs one
 // binary search per block.
 template <int S, typename T>
-__global__ void __launch_bounds__(256, 3) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
+__global__ void __launch_bounds__(256, 4) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
                                                               const int *__restrict__ expo, int64_t ntiles,
                                                               uint8_t *planes) {
     __shared__ int64_t sV[PREP_TK][PREP_TC + 1];
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) batched_expo_kernel(const BatchProb *__re
     }
 }
 
-// Persistent grid: three 256-thread blocks per SM (register bound).
+// Persistent grid: four 256-thread blocks per SM (64 registers each).
 static unsigned prep_grid(int64_t ntiles) {
     static int sms[64] = {};
     int dev = 0;
@@ -446,7 +446,7 @@ static unsigned prep_grid(int64_t ntiles) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         sms[dev] = n > 0 ? n : 1;
     }
-    const int64_t cap = 3 * static_cast<int64_t>(sms[dev]);
+    const int64_t cap = 4 * static_cast<int64_t>(sms[dev]);
     return static_cast<unsigned>(ntiles < cap ? ntiles : cap);
 }
 
