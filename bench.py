@@ -64,6 +64,16 @@ def parse():
 
 # ------------------------------------------------------------------ utils --
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: whole-job throughput is total work over it."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -321,12 +331,7 @@ def main():
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / k
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / k, dist, dev)
 
     clocks = ClockSampler(local)
     for _ in range(args.warmup):
@@ -435,11 +440,7 @@ def main():
         e2e_run(args.steps)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms_e2e = e0.elapsed_time(e1) / args.steps
-        if dist:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
         out["e2e"] = {"value": world * eff / (ms_e2e * 1e-3) / 1e12, "unit": UNIT,
                       "h2d_bytes_per_step": A_host.nbytes, "d2h_bytes_per_step": C.numel() * C.element_size(),
                       "ms_per_step": ms_e2e, "pipelined": "2 buffers, copy stream"}
