@@ -236,9 +236,9 @@ __device__ __forceinline__ void store_digits(const int64_t (&w)[KSTEP], uint8_t 
 constexpr int PREP_SMEM_OPS = 64;
 constexpr int PREP_SMEM_TERMS = 128;
 
-// sV[it][cc] = sum over the op's terms of coef * round(a * 2^sh) for the 16
-// rows k0 + it of column c0 + cc (one thread per column; a warp loads 32
-// consecutive columns of a row).  NT > 0 (1, 2 or 4 terms; a missing fourth
+// sv[it * ld] = sum over the op's terms of coef * round(a * 2^sh) for the 16
+// rows k0 + it of column c0 + cc (one thread per column and 16-row group; a
+// warp loads 32 consecutive columns of a row).  NT > 0 (1, 2 or 4 terms; a missing fourth
 // reads nothing): the rows go in groups of 16 / NT, every term's loads of a
 // group are issued before any is used (16 loads in flight per thread whatever
 // the term count), and a group's sums go to shared memory as soon as they are
@@ -246,7 +246,7 @@ constexpr int PREP_SMEM_TERMS = 128;
 template <int S, int NT, typename T>
 __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                            const OpDesc &od, const OpTerm *terms, int k0, int c0, int cc,
-                                           int64_t (*sV)[PREP_TC + 1]) {
+                                           int64_t *sv, int ld) {
     constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
     auto fixed = [](T a, int sh) -> int64_t {
         if constexpr (FastFixed<F, T>::ok)
@@ -284,7 +284,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                     const int64_t x = fixed(raw[t][j], sh[t]);
                     v += neg[t] ? -x : x;
                 }
-                sV[g + j][cc] = v;
+                sv[(g + j) * ld] = v;
             }
         }
     } else {
@@ -309,29 +309,36 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) sV[g + j][cc] = v[j];
+            for (int j = 0; j < 4; ++j) sv[(g + j) * ld] = v[j];
         }
     }
 }
 
-// One 16 x 256 prep tile of an operand: read phase (above), then each thread
-// writes its column's 32-byte image row of every digit plane as two 16-byte
-// stores; a warp fills one 1 KB image per digit and a tile 8 KB runs.
+// One prep tile of an operand: (4096 / tc) contraction rows x tc columns,
+// tc = 2^lgtc in {64, 128, 256}.  Thread t owns column t mod tc and the
+// 16-row group (one K step) t / tc: it reads that column segment (above) and
+// writes its 32-byte image row of every digit plane as two 16-byte stores,
+// so a warp fills one 1 KB image per digit.
+constexpr int PREP_SV = 4096 + 256;  // shared sums: (4096 / tc) x (tc + 1) entries at most
+
 template <int S, typename T>
 __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                           const OpDesc &od, const OpTerm *terms, int64_t tile,
-                                          const Family &fam, uint8_t *ws, int64_t (*sV)[PREP_TC + 1]) {
+                                          const Family &fam, uint8_t *ws, int64_t *sV, int lgtc) {
+    const int tc = 1 << lgtc, tk = 4096 >> lgtc, ld = tc + 1;
     const int64_t local = tile - od.tile_base;
-    const int tiles_k = od.K_pitch / PREP_TK;
-    const int k0 = static_cast<int>(local % tiles_k) * PREP_TK;
-    const int c0 = static_cast<int>(local / tiles_k) * PREP_TC;
-    const int cc = threadIdx.x;  // column within the tile
+    const int tiles_k = od.K_pitch / tk;
+    const int k0 = static_cast<int>(local % tiles_k) * tk;
+    const int c0 = static_cast<int>(local / tiles_k) * tc;
+    const int cc = threadIdx.x & (tc - 1);  // column within the tile
+    const int rg = threadIdx.x >> lgtc;     // 16-row group (K step) within the tile
+    int64_t *sv = sV + rg * KSTEP * ld + cc;
     switch (od.nterms) {
-        case 1: read_terms<S, 1>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
-        case 2: read_terms<S, 2>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
+        case 1: read_terms<S, 1>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 2: read_terms<S, 2>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
         case 3:
-        case 4: read_terms<S, 4>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
-        default: read_terms<S, 0>(A, lda, expo, od, terms, k0, c0, cc, sV); break;
+        case 4: read_terms<S, 4>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        default: read_terms<S, 0>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
     }
     __syncthreads();
 
@@ -345,8 +352,8 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
         }();
         int64_t w[KSTEP];
 #pragma unroll
-        for (int i = 0; i < KSTEP; ++i) w[i] = sV[i][cc] + CADD;
-        const int64_t kstep = k0 / KSTEP;
+        for (int i = 0; i < KSTEP; ++i) w[i] = sv[i * ld] + CADD;
+        const int64_t kstep = k0 / KSTEP + rg;
         const int64_t cblk = (od.out_col + c0 + cc) / BLOCK_COLS;
         uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
         store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
                                                              const OpDesc *__restrict__ ops, int nops,
                                                              const OpTerm *__restrict__ terms, int nterms,
                                                              int64_t ntiles, Families fams, uint8_t *ws) {
-    __shared__ int64_t sV[PREP_TK][PREP_TC + 1];
+    __shared__ int64_t sV[PREP_SV];
     __shared__ OpDesc s_ops[PREP_SMEM_OPS];
     __shared__ OpTerm s_terms[PREP_SMEM_TERMS];
     const bool cached = nops <= PREP_SMEM_OPS && nterms <= PREP_SMEM_TERMS;
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     const OpTerm *tt = cached ? s_terms : terms;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const OpDesc od = o[find_desc(o, nops, tile)];
-        prep_tile<S, T>(A, lda, expo, od, tt, tile, fams.f[od.family], ws, sV);
+        prep_tile<S, T>(A, lda, expo, od, tt, tile, fams.f[od.family], ws, sV, 8);  // 16 x 256 tiles
     }
 }
 
@@ -385,7 +392,7 @@ template <int S, typename T>
 __global__ void __launch_bounds__(256, 4) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
                                                               const int *__restrict__ expo, int64_t ntiles,
                                                               uint8_t *planes) {
-    __shared__ int64_t sV[PREP_TK][PREP_TC + 1];
+    __shared__ int64_t sV[PREP_SV];
     int64_t tile = blockIdx.x;
     if (tile >= ntiles) return;
     int64_t lo = 0, hi = count - 1;  // last problem with prep_base <= tile
@@ -410,29 +417,43 @@ __global__ void __launch_bounds__(256, 4) batched_prep_kernel(const BatchProb *_
         fam.K_pitch = bp.K_pitch;
         fam.cols = bp.ncb * BLOCK_COLS;
         fam.offset = bp.plane_off;
-        prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, expo + bp.col_off, od, &term, tile, fam, planes, sV);
+        const int lgtc = bp.tc == 64 ? 6 : (bp.tc == 128 ? 7 : 8);
+        prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, expo + bp.col_off, od, &term, tile, fam, planes, sV,
+                        lgtc);
     }
 }
 
 // Batched calls: exponents of every column of every problem.  Block (x, y):
-// problem y (then y + gridDim.y, ...), columns 256 x .. 256 x + 255, all rows.
+// problem y (then y + gridDim.y, ...), columns 64 x .. 64 x + 63; the four
+// warps of each column pair split the rows and combine their maxima in
+// shared memory (narrow problems waste no 256-column blocks).
 template <typename T>
 __global__ void __launch_bounds__(256) batched_expo_kernel(const BatchProb *__restrict__ probs, int64_t count,
                                                            int *expo, int *status) {
+    __shared__ unsigned long long smax[4][64];
+    const int cl = threadIdx.x & 63, rg = threadIdx.x >> 6;
     for (int64_t pi = blockIdx.y; pi < count; pi += gridDim.y) {
         const BatchProb &bp = probs[pi];
-        const int64_t j = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x;
-        if (j >= bp.n || bp.m == 0) continue;
-        const T *a = static_cast<const T *>(bp.A) + j;
+        const int64_t j = static_cast<int64_t>(blockIdx.x) * 64 + cl;
+        if (static_cast<int64_t>(blockIdx.x) * 64 >= bp.n || bp.m == 0) continue;  // block-uniform
         unsigned long long mx = 0;
-        int64_t i = 0;
-        for (; i + 4 <= bp.m; i += 4) {  // four independent loads in flight
-            const unsigned long long b0 = abs_bits(a[(i + 0) * bp.lda]), b1 = abs_bits(a[(i + 1) * bp.lda]);
-            const unsigned long long b2 = abs_bits(a[(i + 2) * bp.lda]), b3 = abs_bits(a[(i + 3) * bp.lda]);
-            mx = max(mx, max(max(b0, b1), max(b2, b3)));
+        if (j < bp.n) {
+            const T *a = static_cast<const T *>(bp.A) + j;
+            int64_t i = rg;
+            for (; i + 12 < bp.m; i += 16) {  // four independent loads in flight
+                const unsigned long long b0 = abs_bits(a[(i + 0) * bp.lda]), b1 = abs_bits(a[(i + 4) * bp.lda]);
+                const unsigned long long b2 = abs_bits(a[(i + 8) * bp.lda]), b3 = abs_bits(a[(i + 12) * bp.lda]);
+                mx = max(mx, max(max(b0, b1), max(b2, b3)));
+            }
+            for (; i < bp.m; i += 4) mx = max(mx, abs_bits(a[i * bp.lda]));
         }
-        for (; i < bp.m; ++i) mx = max(mx, abs_bits(a[i * bp.lda]));
-        expo[bp.col_off + j] = column_exponent<T>(mx, status);
+        smax[rg][cl] = mx;
+        __syncthreads();
+        if (rg == 0 && j < bp.n) {
+            const unsigned long long m = max(max(smax[0][cl], smax[1][cl]), max(smax[2][cl], smax[3][cl]));
+            expo[bp.col_off + j] = column_exponent<T>(m, status);
+        }
+        __syncthreads();
     }
 }
 

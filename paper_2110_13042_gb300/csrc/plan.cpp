@@ -472,13 +472,18 @@ bool make_batch_plan(int mode, int slices, int num_ctas, int64_t count, const in
         q.prep_base = prep;
         if (n[i] == 0 || m[i] == 0) continue;
         q.K_pitch = round_up(m[i], PREP_K);
-        q.P_pad = round_up(n[i], TILE);
-        const int64_t cols = q.P_pad + TILE;  // tile overhang stays inside the planes
+        // Only columns < n feed stored outputs: prep writes whole image
+        // blocks up to n; the leaf's tile overhang reads (unwritten) memory
+        // that stays inside the allocation and only reaches rows and columns
+        // that are not stored.
+        q.P_pad = round_up(n[i], BLOCK_COLS);
+        q.tc = batch_tile_cols(q.P_pad);
+        const int64_t cols = round_up(n[i], TILE) + TILE;
         q.ncb = cols / BLOCK_COLS;
         col_off += n[i];
         plane_off += q.K_pitch * cols * 2 * B.slices;
-        prep += prep_tiles_for(true, q.K_pitch, q.P_pad);
-        B.max_col_chunks = std::max<int64_t>(B.max_col_chunks, ceil_div(n[i], 256));
+        prep += batch_prep_tiles(q.K_pitch, q.P_pad, q.tc);
+        B.max_col_chunks = std::max<int64_t>(B.max_col_chunks, ceil_div(n[i], 64));
         const int kind = mode == MODE_F64_EMU ? OUT_C_F64 : OUT_C_F32;
         const int hb = hbits_for(m[i]);
         for (int64_t J = 0; J < ceil_div(n[i], TILE_M); ++J) {

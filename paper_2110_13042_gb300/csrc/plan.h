@@ -99,9 +99,26 @@ struct BatchProb {
     int64_t plane_off;      // byte offset of its digit planes in the planes block
     int64_t ncb;            // 32-column image blocks per digit plane
     int64_t K_pitch;        // contraction rows of its planes (multiple of PREP_K)
-    int64_t P_pad;          // columns written by prep (multiple of TILE)
+    int64_t P_pad;          // columns written by prep: n rounded up to an image block
     int64_t prep_base;      // first prep tile of this problem (prefix over problems)
+    int32_t tc;             // prep tile columns for this problem (64, 128 or 256)
+    int32_t pad;
 };
+
+// Batched problems: the prep tile width (64, 128 or 256 columns, with 4096 /
+// width rows) that wastes the fewest columns on P_pad, and its tile count.
+inline int batch_tile_cols(int64_t P_pad) {
+    int best = 256;
+    int64_t best_cols = ((P_pad + 255) / 256) * 256;
+    for (int tc : {128, 64}) {
+        const int64_t c = ((P_pad + tc - 1) / tc) * tc;
+        if (c < best_cols) best = tc, best_cols = c;
+    }
+    return best;
+}
+inline int64_t batch_prep_tiles(int64_t K_pitch, int64_t P_pad, int tc) {
+    return (K_pitch / (4096 / tc)) * ((P_pad + tc - 1) / tc);
+}
 
 // Prep tiles of one operand of K_pitch rows and P_pad columns.
 inline int64_t prep_tiles_for(bool digits, int64_t K_pitch, int64_t P_pad) {
@@ -193,7 +210,7 @@ struct BatchPlan {
     int64_t total_cols = 0;     // exponent entries
     int64_t plane_bytes = 0;    // digit planes of all problems
     int64_t prep_tiles = 0;
-    int64_t max_col_chunks = 0; // max over problems of ceil(n / 256)
+    int64_t max_col_chunks = 0; // max over problems of ceil(n / 64) (exponent blocks)
     double leaf_madds = 0;
 };
 
