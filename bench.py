@@ -36,9 +36,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "A^T A effective TFLOP/s (m·n² eq.) vs plain tiled AtA on GB300 at stated error"
 UNIT = "TFLOP/s"
-MODES = {"f64": 0, "f64_emu": 1, "f32": 2, "f32_bf16": 4}
+MODES = {"f64": 0, "f64_emu": 1, "f32": 2, "f32_bf16": 4, "f32_fp8": 5}
 DTYPE_DESC = {0: "f64 (DMMA)", 1: "bf16 digits x fp32 acc -> int64 (fp64-accurate)",
-              2: "bf16 digits x fp32 acc -> int64 (fp32-accurate)", 4: "bf16 x fp32"}
+              2: "bf16 digits x fp32 acc -> int64 (fp32-accurate)", 4: "bf16 x fp32",
+              5: "e4m3 x fp32"}
 
 
 def parse():
@@ -299,7 +300,7 @@ def main():
     from paper_2110_13042_gb300 import inputs
 
     m, n, mode = args.m, args.n, MODES[args.mode]
-    f32 = mode in (2, 4)
+    f32 = mode in (2, 4, 5)
     tdt = torch.float32 if f32 else torch.float64
     A_host = inputs.uniform(m, n, args.seed + rank)
     if f32:
@@ -371,11 +372,16 @@ def main():
         leaf_flops = 2.0 * pairs * info["leaf_madds"]
         achieved = leaf_flops / (ph[2] * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-        roof = {"bound": "tensor", "kernel": f"leaf_tc_kernel<{slices}> (tcgen05 BF16)",
+        kname, psrc = f"leaf_tc_kernel<{slices}> (tcgen05 BF16)", f"{src} bf16 dense sustained"
+        if mode == 5:
+            # FP8 contraction: the measured BF16 peak x the nominal FP8 / BF16 ratio (4.5 / 2.25)
+            peak *= 2.0
+            kname, psrc = "leaf_tc_kernel<1, F8> (tcgen05 E4M3)", f"{src} bf16 dense sustained x 2 (nominal fp8/bf16)"
+        roof = {"bound": "tensor", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": leaf_traffic(mode, m, n, info["depth"], slices),
                 "traffic_unit": "DRAM bytes per leaf launch (ncu, profiles/)",
-                "peak_source": f"{src} bf16 dense sustained",
+                "peak_source": psrc,
                 "work": f"{pairs} digit pairs x 2 x {info['leaf_madds']} tile multiply-adds"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

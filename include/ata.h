@@ -67,7 +67,18 @@ typedef enum {
     ATA_F32 = 2,
     /* float in/out; one BF16 digit (8 bits per column, power-of-two column
      * scaling), FP32 tensor-core accumulation. Low precision. */
-    ATA_F32_BF16 = 4
+    ATA_F32_BF16 = 4,
+    /* float in/out; one FP8 E4M3 product (kind::f8f6f4 tensor cores).  Each
+     * column is scaled by a power of two so that its largest entry is below
+     * 2^8 (E4M3 saturates at 448), every entry (or exact Strassen operand
+     * sum) is rounded to nearest-even E4M3, and the products are summed in
+     * FP32: in the tensor core over 512 contraction rows, then in the
+     * epilogue's FP32 registers.  Strassen result sums are formed in FP64.
+     * Low precision: componentwise error <= (2u + u^2) (|A|^T|A|)_jk plus
+     * subnormal and accumulation terms, u = 2^-4, at Strassen depth 0.
+     * ata_batched answers ATA_ERR_UNSUPPORTED and ata_lower_noalloc
+     * ATA_ERR_DTYPE for this mode. */
+    ATA_F32_FP8 = 5
 } ata_dtype;
 
 /* Planning parameters.  Zero (or -1 for strassen_depth) selects the
@@ -107,7 +118,7 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda,
 /* low(C_i) <- low(A_i^T A_i) for `count` independent problems in one
  * persistent launch.  m, n, lda, ldc: HOST arrays of length count.  A, C:
  * HOST arrays of `count` DEVICE pointers.  Only ATA_F32, ATA_F32_BF16 and
- * ATA_F64_EMU are accepted (ATA_F64: ATA_ERR_UNSUPPORTED); every problem is
+ * ATA_F64_EMU are accepted (ATA_F64, ATA_F32_FP8: ATA_ERR_UNSUPPORTED); every problem is
  * done as plain lower-triangle tiles of its own digit planes (no Strassen),
  * with the same arithmetic and bits as a depth-0 ata_lower call.  Three
  * launches serve the whole batch: column exponents, digit planes, and one

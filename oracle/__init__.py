@@ -16,6 +16,10 @@ Functions (all FP64; A is m x n row-major, C is n x n row-major):
 * ``ata_recursive(A, cutoff, depth)`` the AtA recursion of Algorithm 1 with
                               textbook Strassen; returns (low C, counts).
 * ``strassen_atb(A, B, depth)`` Strassen C = A^T B alone.
+
+``oracle.fp8`` (plain numpy) is the reference of the FP8 mode: E4M3
+rounding from the format definition, the exact product of the quantised
+columns, and the mode's error bounds.
 """
 from __future__ import annotations
 

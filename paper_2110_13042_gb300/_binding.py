@@ -11,7 +11,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-ATA_F64, ATA_F64_EMU, ATA_F32, ATA_F32_BF16 = 0, 1, 2, 4
+ATA_F64, ATA_F64_EMU, ATA_F32, ATA_F32_BF16, ATA_F32_FP8 = 0, 1, 2, 4, 5
 STATUS = {0: "ATA_OK", 1: "ATA_ERR_INVALID", 2: "ATA_ERR_DTYPE", 3: "ATA_ERR_ALLOC",
           4: "ATA_ERR_CUDA", 5: "ATA_ERR_TIMEOUT", 6: "ATA_ERR_UNSUPPORTED"}
 PLAN_FIELDS = ("cutoff", "depth", "slices", "panels", "blocks", "products", "tiles",

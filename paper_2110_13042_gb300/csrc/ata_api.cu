@@ -47,10 +47,11 @@ struct CachedBatch {
     }
 };
 
-bool is_f32_mode(int dtype) { return dtype == ATA_F32 || dtype == ATA_F32_BF16; }
+bool is_f32_mode(int dtype) { return dtype == ATA_F32 || dtype == ATA_F32_BF16 || dtype == ATA_F32_FP8; }
 
 bool valid_dtype(int dtype) {
-    return dtype == ATA_F64 || dtype == ATA_F64_EMU || dtype == ATA_F32 || dtype == ATA_F32_BF16;
+    return dtype == ATA_F64 || dtype == ATA_F64_EMU || dtype == ATA_F32 || dtype == ATA_F32_BF16 ||
+           dtype == ATA_F32_FP8;
 }
 
 }  // namespace
@@ -502,7 +503,8 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
     if (count == 0) return ATA_OK;
     if (!m || !n || !A || !lda || !C || !ldc) return ATA_ERR_INVALID;
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
-    if (dtype == ATA_F64) return fail(h, ATA_ERR_UNSUPPORTED, "batched calls take F64_EMU, F32 or F32_BF16");
+    if (dtype == ATA_F64 || dtype == ATA_F32_FP8)
+        return fail(h, ATA_ERR_UNSUPPORTED, "batched calls take F64_EMU, F32 or F32_BF16");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool f32 = is_f32_mode(dtype);
     const size_t es = f32 ? 4 : 8;

@@ -8,6 +8,7 @@
 // digit extraction, result sums) is done in 64-bit INTEGER arithmetic on a
 // fixed-point representation; FP64 is used only to form the final values.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cstdint>
 
 #include "kernels.h"
@@ -243,11 +244,11 @@ constexpr int PREP_SMEM_TERMS = 128;
 // group are issued before any is used (16 loads in flight per thread whatever
 // the term count), and a group's sums go to shared memory as soon as they are
 // complete.  NT = 0: any count, groups of four rows, one term at a time.
-template <int S, int NT, typename T>
+template <int S, int NT, typename T, bool F8>
 __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                            const OpDesc &od, const OpTerm *terms, int k0, int c0, int cc,
                                            int64_t *sv, int ld) {
-    constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
+    constexpr int F = F8 ? FP8_FIX : DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
     auto fixed = [](T a, int sh) -> int64_t {
         if constexpr (FastFixed<F, T>::ok)
             return fixed_of_fast<F>(a, sh);
@@ -321,7 +322,21 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
 // so a warp fills one 1 KB image per digit.
 constexpr int PREP_SV = 4096 + 256;  // shared sums: (4096 / tc) x (tc + 1) entries at most
 
-template <int S, typename T>
+// E4M3 code of V * 2^(FP8_TOP - FP8_FIX), rounded to nearest even: V is
+// first rounded to odd at FP32's 24 bits (truncate, then set the last bit if
+// anything was dropped), which keeps the final rounding to E4M3's 4 bits (or
+// its subnormal grid) exact (Boldo and Melquiond, "Emulation of FMA and
+// correctly rounded sums: proved algorithms using rounding to odd", 2008).
+// |V| <= 2^FP8_FIX, so the scaled value stays below 2^FP8_TOP.
+__device__ __forceinline__ uint32_t e4m3_of_fixed(int64_t V) {
+    const unsigned long long mag = V < 0 ? 0ull - static_cast<unsigned long long>(V) : static_cast<unsigned long long>(V);
+    float f = __ull2float_rz(mag);
+    if (__float2ull_rz(f) != mag) f = __uint_as_float(__float_as_uint(f) | 1u);
+    f *= __uint_as_float(static_cast<unsigned>(127 + FP8_TOP - FP8_FIX) << 23);
+    return static_cast<uint32_t>(__nv_cvt_float_to_fp8(V < 0 ? -f : f, __NV_SATFINITE, __NV_E4M3));
+}
+
+template <int S, typename T, bool F8 = false>
 __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
                                           const OpDesc &od, const OpTerm *terms, int64_t tile,
                                           const Family &fam, uint8_t *ws, int64_t *sV, int lgtc) {
@@ -334,15 +349,34 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     const int rg = threadIdx.x >> lgtc;     // 16-row group (K step) within the tile
     int64_t *sv = sV + rg * KSTEP * ld + cc;
     switch (od.nterms) {
-        case 1: read_terms<S, 1>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
-        case 2: read_terms<S, 2>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 1: read_terms<S, 1, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 2: read_terms<S, 2, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
         case 3:
-        case 4: read_terms<S, 4>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
-        default: read_terms<S, 0>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 4: read_terms<S, 4, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        default: read_terms<S, 0, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
     }
     __syncthreads();
 
-    if (c0 + cc < od.P_pad) {
+    if constexpr (F8) {
+        // One E4M3 plane: the thread's 16 rows are one 16-byte half of its
+        // column's 32-byte image row (rows 32 ks .. 32 ks + 31); half h sits
+        // at 16-byte slot h ^ swz.
+        if (c0 + cc < od.P_pad) {
+            const int64_t ncb = fam.cols / BLOCK_COLS;
+            const int r = cc & (BLOCK_COLS - 1);
+            const int kk = k0 + rg * KSTEP;
+            const int64_t cblk = (od.out_col + c0 + cc) / BLOCK_COLS;
+            uint32_t pk[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                pk[i] = e4m3_of_fixed(sv[(4 * i) * ld]) | (e4m3_of_fixed(sv[(4 * i + 1) * ld]) << 8) |
+                        (e4m3_of_fixed(sv[(4 * i + 2) * ld]) << 16) | (e4m3_of_fixed(sv[(4 * i + 3) * ld]) << 24);
+            const int slot = ((kk / KSTEP) & 1) ^ ((r >> 2) & 1);
+            uint8_t *dst = ws + fam.offset + (static_cast<int64_t>(kk / KSTEP8) * ncb + cblk) * BLOCK_BYTES + r * 32 +
+                           slot * 16;
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    } else if (c0 + cc < od.P_pad) {
         const int64_t ncb = fam.cols / BLOCK_COLS;
         const int r = cc & (BLOCK_COLS - 1);
         constexpr int64_t CADD = [] {
@@ -361,7 +395,7 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     __syncthreads();  // sV is reused by the block's next tile
 }
 
-template <int S, typename T>
+template <int S, typename T, bool F8 = false>
 __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
                                                              const int *__restrict__ expo,
                                                              const OpDesc *__restrict__ ops, int nops,
@@ -380,7 +414,8 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     const OpTerm *tt = cached ? s_terms : terms;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const OpDesc od = o[find_desc(o, nops, tile)];
-        prep_tile<S, T>(A, lda, expo, od, tt, tile, fams.f[od.family], ws, sV, 8);  // 16 x 256 tiles
+        // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
+        prep_tile<S, T, F8>(A, lda, expo, od, tt, tile, fams.f[od.family], ws, sV, F8 ? 7 : 8);
     }
 }
 
@@ -578,9 +613,10 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
 }
 
 // Native FP64 result sums (fixed term order), then the column scales.
+template <typename TOut>
 __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
-                                                          const double *__restrict__ M, double *C,
+                                                          const double *__restrict__ M, TOut *C,
                                                           int64_t ldc, const int *__restrict__ expo) {
     __shared__ CombTerm st[MAX_CTERMS];
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
@@ -602,7 +638,7 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__rest
             const double v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
             sum = ct.coef > 0 ? sum + v : sum - v;
         }
-        C[d.c_off + static_cast<int64_t>(row) * ldc + col] = sum * exp2i(expo[d.e_row0 + row] + ec);
+        C[d.c_off + static_cast<int64_t>(row) * ldc + col] = static_cast<TOut>(sum * exp2i(expo[d.e_row0 + row] + ec));
     }
 }
 
@@ -754,7 +790,10 @@ static void prep_digits_dispatch(const Plan &P, const void *A, bool is_f32, cons
     const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
     const unsigned g = prep_grid(P.prep_tiles);
     const int nops = static_cast<int>(P.ops.size()), nterms = static_cast<int>(P.terms.size());
-    if (is_f32)
+    if (S == 1 && P.p.mode == MODE_F32_FP8)  // FP8 mode: float A, one E4M3 plane
+        prep_digits_kernel<1, float, true><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo, ops,
+                                                              nops, terms, nterms, P.prep_tiles, F, ws);
+    else if (is_f32)
         prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo, ops, nops,
                                                         terms, nterms, P.prep_tiles, F, ws);
     else
@@ -803,8 +842,11 @@ cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, 
     const unsigned g = static_cast<unsigned>(P.comb_tiles);
     const int nd = static_cast<int>(P.combs.size());
     if (P.p.mode == MODE_F64)
-        combine_f64_kernel<<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
-                                              static_cast<double *>(C), P.p.ldc, expo);
+        combine_f64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
+                                                      static_cast<double *>(C), P.p.ldc, expo);
+    else if (P.p.mode == MODE_F32_FP8)  // FP8 products are FP32 sums, stored as double
+        combine_f64_kernel<float><<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
+                                                     static_cast<float *>(C), P.p.ldc, expo);
     else if (P.p.mode == MODE_F64_EMU)
         combine_i64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
                                                       static_cast<double *>(C), P.p.ldc, expo);

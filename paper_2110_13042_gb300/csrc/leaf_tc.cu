@@ -42,6 +42,7 @@
 // All mbarrier waits are bounded (ptx.cuh).
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.h"
 #include "ptx.cuh"
@@ -59,6 +60,7 @@ constexpr int MAX_ACC = 5;
 constexpr int MAX_STAGES = 10;
 constexpr uint32_t IDESC = idesc_bf16_f32(TILE_M, TILE_N);
 constexpr uint32_t IDESC2 = idesc_bf16_f32(TILE_M, 2 * TILE_N);
+constexpr uint32_t IDESC8 = idesc_e4m3_f32(TILE_M, TILE_N);
 
 template <int S>
 struct Cfg {
@@ -295,9 +297,31 @@ __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase
     absorb<ACC, WIDE>(T + 16, r1, h, fold_scale);
 }
 
-template <int S>
+// FP8 mode: drain the single accumulator (FP32 partial sums of E4M3
+// products over the chunk) into the thread's FP32 sums, zeroing it.
+__device__ __forceinline__ void drain_f8(float (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh) {
+    uint32_t r0[16], r1[16];
+    tmem_ld_32x32b_x16(tbase + colbase, r0);
+    tmem_ld_32x32b_x16(tbase + colbase + 16, r1);
+    tmem_ld_wait();
+    tmem_st_zero_32x32b_x16(tbase + colbase);
+    tmem_st_zero_32x32b_x16(tbase + colbase + 16);
+    tmem_st_wait();
+    tc_fence_before();
+    mbar_arrive(&sh->acce[0]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        T[i] += __uint_as_float(r0[i]);
+        T[16 + i] += __uint_as_float(r1[i]);
+    }
+}
+
+// F8: one E4M3 plane per operand (S == 1), K steps of 32 rows, FP32 sums.
+template <int S, bool F8 = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_constant__ LeafParams p) {
     using C = Cfg<S>;
+    static_assert(!F8 || S == 1, "the FP8 mode has one plane");
+    constexpr int KS = F8 ? KSTEP8 : KSTEP;  // contraction rows per K step
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     Shared *sh = reinterpret_cast<Shared *>(smem + C::STAGES * C::STAGE_BYTES);
@@ -333,7 +357,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             bool ok = true;
             for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
                 const LeafTask t = p.tasks[ti];
-                const int nsteps = (t.klen + KSTEP - 1) / KSTEP;
+                const int nsteps = (t.klen + KS - 1) / KS;
                 // Digit images: ((kstep * S + digit) * ncb + column block) KB; the
                 // tile's TILE_M (TILE_N) columns are 4 (3) consecutive blocks.
                 const uint8_t *ubase = p.fam_base[t.fam_u], *vbase = p.fam_base[t.fam_v];
@@ -357,7 +381,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     for (int kk = 0; kk < cnt; ++kk) {
                         uint8_t *a_dst = smem + stage * C::STAGE_BYTES + kk * C::STEP_BYTES;
                         uint8_t *b_dst = a_dst + S * A_SLICE_BYTES;
-                        const int64_t ku = (t.k0 / KSTEP) + s0 + kk, kv = (t.k0v / KSTEP) + s0 + kk;
+                        const int64_t ku = (t.k0 / KS) + s0 + kk, kv = (t.k0v / KS) + s0 + kk;
 #pragma unroll
                         for (int q = 0; q < S; ++q) {
                             bulk_load(a_dst + q * A_SLICE_BYTES, ua + (ku * S + q) * ua_step, A_SLICE_BYTES,
@@ -387,7 +411,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             bool ready = false;  // the current stage's full barrier was already seen complete
             const uint32_t smem_base = smem_u32(smem);
             for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
-                const int nsteps = (p.tasks[ti].klen + KSTEP - 1) / KSTEP;
+                const int nsteps = (p.tasks[ti].klen + KS - 1) / KS;
                 for (int s0 = 0; s0 < nsteps; s0 += C::KPS) {
                     const int cnt = nsteps - s0 < C::KPS ? nsteps - s0 : C::KPS;
                     if (!ready && !mbar_wait(&sh->full[stage], phase, abort_flag, p.status)) {
@@ -410,7 +434,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                 ok = wait_drained<C::NACC>(st, ~0x0Cu, sh, abort_flag, p.status);
                                 if (!ok) break;
                             }
-                            issue_group<S, false>(tmem, da0, db0);
+                            if constexpr (F8)
+                                umma_f8(tmem, da0, db0, IDESC8, 1u);
+                            else
+                                issue_group<S, false>(tmem, da0, db0);
                             if (st.pending & 0x0Cu) {
                                 ok = wait_drained<C::NACC>(st, 0x0Cu, sh, abort_flag, p.status);
                                 if (!ok) break;
@@ -469,11 +496,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
         for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
             // Only the chunk count stays live across the K loop; the rest of
             // the task record is re-read for the store (register budget).
-            const int nsteps = (p.tasks[ti].klen + KSTEP - 1) / KSTEP;
+            const int nsteps = (p.tasks[ti].klen + KS - 1) / KS;
             const int nchunks = (nsteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
             const int h = p.tasks[ti].hbits;
             const float fold_scale = __uint_as_float(static_cast<unsigned>(127 + 27 + h) << 23);
-            int64_t T[EPI_COLS];
+            using Sum = typename std::conditional<F8, float, int64_t>::type;
+            Sum T[EPI_COLS];
 #pragma unroll
             for (int i = 0; i < EPI_COLS; ++i) T[i] = 0;
             for (int c = 0; c < nchunks; ++c) {
@@ -486,15 +514,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 }
                 accf_phase ^= 1u;
                 tc_fence_after();
-                if (due & 16u) drain_one<4, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 1u) drain_one<0, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 2u) drain_one<1, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 4u) drain_one<2, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                if (due & 8u) drain_one<3, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                if constexpr (F8) {
+                    drain_f8(T, tbase, colbase, sh);
+                } else {
+                    if (due & 16u) drain_one<4, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 1u) drain_one<0, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 2u) drain_one<1, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 4u) drain_one<2, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 8u) drain_one<3, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                }
             }
             if (!ok) break;
             const LeafTask t = p.tasks[ti];
-            if (row < t.rows) {
+            if constexpr (F8) {
+                // T holds sum_k q_u q_v of E4M3 values scaled by 2^(FP8_TOP - t - e)
+                if (row < t.rows) {
+                    const int lim0 = t.diag ? min(t.cols, row + t.diag_off + 1) : t.cols;
+                    const int lim = lim0 < 0 ? 0 : lim0;
+                    if (t.kind == OUT_M_F64) {  // Strassen product, in units of the scaled columns
+                        double *out = static_cast<double *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                        const double sc = exp2d(t.shift - 2 * FP8_TOP);
+#pragma unroll
+                        for (int i = 0; i < EPI_COLS; ++i) {
+                            const int col = colbase + i;
+                            if (col < lim) out[col] = static_cast<double>(T[i]) * sc;
+                        }
+                    } else {
+                        const int er = -2 * FP8_TOP + t.shift + (t.eu >= 0 ? p.expo[t.eu + row] : 0);
+                        const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
+                        float *out = static_cast<float *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+#pragma unroll
+                        for (int i = 0; i < EPI_COLS; ++i) {
+                            const int col = colbase + i;
+                            if (col < lim) out[col] = T[i] * exp2f_(er + (ev ? ev[col] : 0));
+                        }
+                    }
+                }
+            } else if (row < t.rows) {
                 const int lim0 = t.diag ? min(t.cols, row + t.diag_off + 1) : t.cols;
                 const int lim = lim0 < 0 ? 0 : lim0;
                 if (t.kind == OUT_M_I64) {
@@ -540,26 +596,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
 
 // The shared-memory opt-in of leaf_tc_kernel<S>, set once per device (a
 // later call, e.g. inside a graph capture, needs no attribute change).
-template <int S>
+template <int S, bool F8 = false>
 cudaError_t ensure_leaf_attr() {
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(leaf_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<S>::SMEM_BYTES);
+    e = cudaFuncSetAttribute(leaf_tc_kernel<S, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<S>::SMEM_BYTES);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }
 
-template <int S>
+template <int S, bool F8 = false>
 cudaError_t launch_s(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s) {
     using C = Cfg<S>;
-    cudaError_t ea = ensure_leaf_attr<S>();
+    cudaError_t ea = ensure_leaf_attr<S, F8>();
     if (ea != cudaSuccess) return ea;
     const int ntasks = static_cast<int>(P.tasks.size());
     const int grid = ntasks < num_sms ? ntasks : num_sms;
-    leaf_tc_kernel<S><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(lp);
+    leaf_tc_kernel<S, F8><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(lp);
     return cudaGetLastError();
 }
 
@@ -580,6 +637,7 @@ int leaf_tc_smem_bytes(int slices) {
 
 cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s) {
     if (P.tasks.empty()) return cudaSuccess;
+    if (P.p.mode == MODE_F32_FP8) return launch_s<1, true>(P, lp, num_sms, s);
     switch (P.slices) {
         case 1: return launch_s<1>(P, lp, num_sms, s);
         case 2: return launch_s<2>(P, lp, num_sms, s);

@@ -81,10 +81,13 @@ int log2_ceil(int64_t x) {
 struct Builder {
     Plan &P;
     bool digits;
+    bool fp8;    // one E4M3 plane per operand, FP32 accumulation
+    int kalign;  // contraction rows of one leaf K step
     bool reuse_quadrants = true;
     int64_t prod_elems = 0;
 
-    explicit Builder(Plan &p) : P(p), digits(p.p.mode != MODE_F64) {}
+    explicit Builder(Plan &p)
+        : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)) {}
 
     int family_for(int64_t K_nominal) {
         int64_t Kp = round_up(std::max<int64_t>(K_nominal, 1), PREP_K);
@@ -140,7 +143,7 @@ struct Builder {
             t.ev = static_cast<int32_t>(c0);
         }
         t.shift = 0;
-        t.hbits = hbits_for(P.p.m);
+        t.hbits = fp8 ? 0 : hbits_for(P.p.m);
         t.out_off = r0 * P.p.ldc + c0;
         t.out_ld = P.p.ldc;
         P.tasks.push_back(t);
@@ -199,7 +202,7 @@ struct Builder {
             const int64_t f0_cols = round_up(std::max<int64_t>(P.p.n, 1), TILE) + TILE;
             const bool rows_ok = t.rows == rn || (t.row0 + t.rows == P.p.m && t.row0 + rn <= f0.K_pitch);
             const bool cols_ok = t.cols == nominal_cols || t.col0 + t.cols == P.p.n;
-            if (t.row0 % KSTEP == 0 && t.col0 % BLOCK_COLS == 0 && rows_ok && cols_ok &&
+            if (t.row0 % kalign == 0 && t.col0 % BLOCK_COLS == 0 && rows_ok && cols_ok &&
                 t.col0 + round_up(nominal_cols, TILE) <= f0_cols) {
                 P.n_reused++;
                 return {0, t.col0, t.row0, 0};
@@ -251,8 +254,10 @@ struct Builder {
             }
             Operand U = operand(fam, ut, pn, rn), V = operand(fam, vt, qn, rn);
             // Product unit: 2^(-43 - h + t_u + t_v); the combine sees it as
-            // 2^(-43 + shift) with shift = t_u + t_v - h.
-            const int hb = hbits_for(rn);
+            // 2^(-43 + shift) with shift = t_u + t_v - h.  (FP8: the leaf
+            // writes the product in units of the scaled columns, shift =
+            // t_u + t_v.)
+            const int hb = fp8 ? 0 : hbits_for(rn);
             int shift = U.t_shift + V.t_shift - hb;
             prod_shift[r] = shift;
             prod_off[r] = prod_elems;
@@ -271,7 +276,7 @@ struct Builder {
                     t.rows = static_cast<int32_t>(std::min<int64_t>(TILE_M, pn - J * TILE_M));
                     t.cols = static_cast<int32_t>(std::min<int64_t>(TILE_N, qn - K * TILE_N));
                     t.diag = 0;
-                    t.kind = digits ? OUT_M_I64 : OUT_M_F64;
+                    t.kind = digits && !fp8 ? OUT_M_I64 : OUT_M_F64;
                     t.shift = shift;
                     t.hbits = hb;
                     t.eu = t.ev = -1;
@@ -313,7 +318,7 @@ struct Builder {
                 for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
                     smin = std::min(smin, P.cterms[i].shift);
                 c.rshift = 0;
-                if (digits) {
+                if (digits && !fp8) {
                     for (;;) {
                         double bound = 0;
                         for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
@@ -530,6 +535,7 @@ int default_slices(int mode, int64_t m) {
         case MODE_F64_EMU: return 6;
         case MODE_F32: return 3;
         case MODE_F32_BF16: return 1;
+        case MODE_F32_FP8: return 1;
         default: return 0;
     }
 }
@@ -548,12 +554,13 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         return false;
     }
     if (pp.mode != MODE_F64 && pp.mode != MODE_F64_EMU && pp.mode != MODE_F32 &&
-        pp.mode != MODE_F32_BF16) {
+        pp.mode != MODE_F32_BF16 && pp.mode != MODE_F32_FP8) {
         if (err) *err = "unknown mode";
         return false;
     }
     P.slices = pp.slices > 0 ? pp.slices : default_slices(pp.mode, pp.m);
     if (pp.mode == MODE_F64) P.slices = 0;
+    if (pp.mode == MODE_F32_FP8) P.slices = 1;  // one E4M3 plane whatever the digit setting
     if (pp.mode != MODE_F64 && (P.slices < 1 || P.slices > MAX_SLICES)) {
         if (err) *err = "slices out of range";
         return false;
@@ -592,8 +599,8 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     // whole 1 KB images with bulk copies.
     if (B.digits) {
         for (const LeafTask &t : P.tasks) {
-            if (t.col_u % BLOCK_COLS != 0 || t.col_v % BLOCK_COLS != 0 || t.k0 % KSTEP != 0 ||
-                t.k0v % KSTEP != 0) {
+            if (t.col_u % BLOCK_COLS != 0 || t.col_v % BLOCK_COLS != 0 || t.k0 % B.kalign != 0 ||
+                t.k0v % B.kalign != 0) {
                 if (err) *err = "internal: leaf tile not aligned to a digit-image block";
                 return false;
             }
@@ -612,7 +619,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     for (Family &f : P.families) {
         f.cols += TILE;  // padding: a leaf box may extend up to TILE columns past the last operand
         f.plane_elems = f.cols * f.K_pitch;
-        int64_t bytes = B.digits ? f.plane_elems * 2 * P.slices : f.plane_elems * 8;
+        int64_t bytes = B.fp8 ? f.plane_elems : B.digits ? f.plane_elems * 2 * P.slices : f.plane_elems * 8;
         f.offset = take(bytes);
     }
     P.product_bytes = B.prod_elems * 8;
@@ -621,7 +628,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     P.prep_tiles = 0;
     for (OpDesc &o : P.ops) {
         o.tile_base = P.prep_tiles;
-        P.prep_tiles += prep_tiles_for(B.digits, o.K_pitch, o.P_pad);
+        P.prep_tiles += prep_tiles_for(B.digits, o.K_pitch, o.P_pad, B.fp8);
     }
     P.t_ops = 0;
     P.t_terms = round_up(P.t_ops + static_cast<int64_t>(P.ops.size() * sizeof(OpDesc)), 256);

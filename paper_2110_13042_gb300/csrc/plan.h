@@ -33,7 +33,22 @@ constexpr int PREP_TC = 256;
 constexpr int MAX_FAMILIES = 6;  // operand families (tensor maps) per launch
 constexpr int MAX_SLICES = 7;
 
-enum Mode : int { MODE_F64 = 0, MODE_F64_EMU = 1, MODE_F32 = 2, MODE_F32_BF16 = 4 };
+enum Mode : int { MODE_F64 = 0, MODE_F64_EMU = 1, MODE_F32 = 2, MODE_F32_BF16 = 4, MODE_F32_FP8 = 5 };
+
+// FP8 mode: one E4M3 plane per operand.  A column scaled by 2^(FP8_TOP - e)
+// has |value| < 2^FP8_TOP <= 448 (E4M3's largest finite value), so no value
+// saturates.  An operand sum is first formed exactly in fixed point with
+// FP8_FIX fraction bits (every FP32 entry at or above 2^-18 of its column
+// scale, i.e. every entry that does not round to zero, is exact there),
+// then rounded once to E4M3.  One K step of an FP8 plane is 32 contraction
+// rows (the 32-byte image row holds 32 one-byte values).
+constexpr int FP8_TOP = 8;
+constexpr int FP8_FIX = 47;
+constexpr int KSTEP8 = 32;
+// FP8 prep tiles: 32 contraction rows (one FP8 K step) x 128 columns.
+constexpr int PREP8_TK = KSTEP8;
+constexpr int PREP8_TC = 128;
+inline int kstep_rows(int mode) { return mode == MODE_F32_FP8 ? KSTEP8 : KSTEP; }
 
 // One term of a (possibly summed) Strassen operand: a sub-block of A.
 struct OpTerm {
@@ -52,6 +67,8 @@ struct OpTerm {
 // 32 columns x 16 contraction rows in exactly the order the leaf kernel's
 // shared memory needs them (K-major rows of 32 bytes, 32-byte swizzle;
 // image (kstep, digit, colblock) at ((kstep * S + digit) * ncb + colblock) KB),
+// or one E4M3 plane of 1 KB images of 32 columns x 32 rows (FP8 mode,
+// image (kstep, colblock) at (kstep * ncb + colblock) KB),
 // or one FP64 array ([k][col], row-major) for the native FP64 mode.
 struct OpDesc {
     int32_t family;
@@ -121,7 +138,8 @@ inline int64_t batch_prep_tiles(int64_t K_pitch, int64_t P_pad, int tc) {
 }
 
 // Prep tiles of one operand of K_pitch rows and P_pad columns.
-inline int64_t prep_tiles_for(bool digits, int64_t K_pitch, int64_t P_pad) {
+inline int64_t prep_tiles_for(bool digits, int64_t K_pitch, int64_t P_pad, bool fp8 = false) {
+    if (fp8) return (K_pitch / PREP8_TK) * ((P_pad + PREP8_TC - 1) / PREP8_TC);
     return digits ? (K_pitch / PREP_TK) * ((P_pad + PREP_TC - 1) / PREP_TC) : (K_pitch / PREP_K) * (P_pad / PREP_C);
 }
 
@@ -139,7 +157,7 @@ enum OutKind : int {
     OUT_C_F64 = 0,   // double into C, scaled by 2^(e_row + e_col)
     OUT_C_F32 = 1,   // float into C, scaled by 2^(e_row + e_col)
     OUT_M_I64 = 2,   // exact int64 partial into the product workspace
-    OUT_M_F64 = 3    // double into the product workspace (native FP64)
+    OUT_M_F64 = 3    // double into the product workspace (native FP64, FP8)
 };
 
 // One Strassen result sum: region of C = sum_r coef_r * M_r (clipped).

@@ -82,7 +82,7 @@ def lower_tiles(n):
 
 
 @pytest.mark.parametrize("n", [1, 64, 128, 129, 255, 1000, 4096])
-@pytest.mark.parametrize("mode", [1, 2, 4])
+@pytest.mark.parametrize("mode", [1, 2, 4, 5])
 def test_plain_plan_is_all_lower_tiles(lib, n, mode):
     h = None
     info = lib.plan_info(300, n, mode, h)
@@ -195,3 +195,20 @@ def test_invalid_parameters_rejected(plan_cli):
         plan_cli(10, 10, 3, 0, 0)      # unknown mode
     with pytest.raises(subprocess.CalledProcessError):
         plan_cli(10, 10, 1, 0, 0, 9)   # too many digits
+
+
+@pytest.mark.parametrize("m,n,depth", [(1056, 2048, 1), (1000, 1024, 1), (531, 777, 2), (4099, 2048, 2)])
+def test_fp8_plan(plan_cli, m, n, depth):
+    """FP8 mode: the same tiles and Strassen products as one BF16 digit, one
+    byte per plane element (smaller workspace), and Strassen quadrants read
+    from the planes of A only where their row offset falls on a 32-row FP8
+    K step (a 16-row offset that a BF16 plane could serve is not enough)."""
+    r8 = plan_cli(m, n, 5, n // 4, depth)
+    rb = plan_cli(m, n, 4, n // 4, depth)
+    assert r8["slices"] == 1
+    for k in ("tiles", "products", "covered", "overlap", "cterms", "strassen_leaf_madds"):
+        assert r8[k] == rb[k], k
+    assert r8["workspace"] < rb["workspace"]
+    assert r8["reused"] <= rb["reused"]
+    if (m + 1) // 2 % 32 == 16:
+        assert r8["reused"] < rb["reused"]
