@@ -424,6 +424,41 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     // Probe the next stage now; the test's latency hides
                     // behind this stage's MMA issue.
                     ready = mbar_test_wait(&sh->full[nstage], nphase);
+                    if constexpr (C::KPS == CHUNK_STEPS && S == 1) {
+                        // One digit: a stage is exactly one drain chunk, so
+                        // the drain bookkeeping runs once per stage and the
+                        // stage's MMAs go out back to back from descriptors
+                        // built once (per-step bookkeeping in the issuing
+                        // thread measured ~275 cycles against a 56-cycle MMA).
+                        if (st.pending) {
+                            ok = wait_drained<C::NACC>(st, ~0u, sh, abort_flag, p.status);
+                            if (!ok) break;
+                        }
+                        const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
+                        const uint64_t da0 = sdesc_kmajor_sw32(a_base);
+                        const uint64_t db0 = sdesc_kmajor_sw32(a_base + A_SLICE_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < C::KPS; ++kk) {
+                            if (kk < cnt) {
+                                const uint64_t off = static_cast<uint64_t>(kk * (C::STEP_BYTES >> 4));
+                                if constexpr (F8)
+                                    umma_f8(tmem, da0 + off, db0 + off, IDESC8, 1u);
+                                else
+                                    umma_f16(tmem, da0 + off, db0 + off, IDESC, 1u);
+                            }
+                        }
+                        const uint32_t due = due_mask(s0 / CHUNK_STEPS, s0 + cnt >= nsteps, C::NACC);
+                        if (due) {  // hand the accumulator to the epilogue
+                            umma_commit(&sh->accf);
+                            st.pending |= due;
+                        }
+                        umma_commit(&sh->empty[stage]);
+                        if (++stage == C::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
+                    }
                     for (int kk = 0; kk < cnt; ++kk) {
                         const int step = s0 + kk;
                         const uint32_t a_base = smem_base + stage * C::STAGE_BYTES + kk * C::STEP_BYTES;
