@@ -64,11 +64,13 @@ constexpr uint32_t IDESC8 = idesc_e4m3_f32(TILE_M, TILE_N);
 
 template <int S>
 struct Cfg {
-    // K steps per pipeline stage.  With one digit a step is a single MMA and
-    // stages of 4 steps (one wait and one commit for all) measured 9% faster;
-    // for 2 and 3 digits 2-step stages measured slower (fewer stages in the
-    // ring), so they keep one step per stage.
-    static constexpr int KPS = S == 1 ? 4 : 1;
+    // K steps per pipeline stage.  Up to 3 digits the issuing thread does
+    // its bookkeeping once per stage (see the issuer), so longer stages pay:
+    // measured at 8192^2, one digit 8 steps (-38% leaf time against 1-step
+    // bookkeeping), two and three digits 4 steps (-24% / -19%, although only
+    // 2-4 stages fit).  From 4 digits on, drains fall inside 16-step spans
+    // and every step is a stage.
+    static constexpr int KPS = S == 1 ? 8 : S <= 3 ? 4 : 1;
     static constexpr int STEP_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);
     static constexpr int STAGE_BYTES = KPS * STEP_BYTES;
     static constexpr int STAGES_FIT = 229000 / STAGE_BYTES;
@@ -424,41 +426,48 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     // Probe the next stage now; the test's latency hides
                     // behind this stage's MMA issue.
                     ready = mbar_test_wait(&sh->full[nstage], nphase);
-                    if constexpr (C::KPS == CHUNK_STEPS && S == 1) {
-                        // One digit: a stage is exactly one drain chunk, so
-                        // the drain bookkeeping runs once per stage and the
-                        // stage's MMAs go out back to back from descriptors
-                        // built once (per-step bookkeeping in the issuing
-                        // thread measured ~275 cycles against a 56-cycle MMA).
-                        if (st.pending) {
-                            ok = wait_drained<C::NACC>(st, ~0u, sh, abort_flag, p.status);
-                            if (!ok) break;
-                        }
+                    if constexpr (S <= 3) {
+                        static_assert((4 * CHUNK_STEPS) % C::KPS == 0, "every 16-step drain point ends a stage");
+                        // At most 3 digits: every accumulator is drained every
+                        // 16 steps, at the end of a stage, so the drain waits
+                        // come before the stage's first step and the due check
+                        // after its last; the stage's MMAs go out back to back
+                        // from descriptors built once.  (Per-step bookkeeping
+                        // in the issuing thread measured ~275 cycles against a
+                        // 56-cycle MMA; the pipe idles meanwhile.)
                         const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
                         const uint64_t da0 = sdesc_kmajor_sw32(a_base);
-                        const uint64_t db0 = sdesc_kmajor_sw32(a_base + A_SLICE_BYTES);
+                        const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
 #pragma unroll
                         for (int kk = 0; kk < C::KPS; ++kk) {
                             if (kk < cnt) {
                                 const uint64_t off = static_cast<uint64_t>(kk * (C::STEP_BYTES >> 4));
+                                if (kk == 0 && (st.pending & ~0x0Cu)) {
+                                    ok = wait_drained<C::NACC>(st, ~0x0Cu, sh, abort_flag, p.status);
+                                    if (!ok) break;
+                                }
                                 if constexpr (F8)
                                     umma_f8(tmem, da0 + off, db0 + off, IDESC8, 1u);
                                 else
-                                    umma_f16(tmem, da0 + off, db0 + off, IDESC, 1u);
+                                    issue_group<S, false>(tmem, da0 + off, db0 + off);
+                                if (kk == 0 && (st.pending & 0x0Cu)) {
+                                    ok = wait_drained<C::NACC>(st, 0x0Cu, sh, abort_flag, p.status);
+                                    if (!ok) break;
+                                }
+                                issue_group<S, true>(tmem, da0 + off, db0 + off);
                             }
                         }
-                        const uint32_t due = due_mask(s0 / CHUNK_STEPS, s0 + cnt >= nsteps, C::NACC);
-                        if (due) {  // hand the accumulator to the epilogue
+                        if (!ok) break;
+                        const int end = s0 + cnt;  // drains fall on 16-step boundaries and task ends
+                        const uint32_t due =
+                            (end % (4 * CHUNK_STEPS) == 0 || end >= nsteps)
+                                ? due_mask((end - 1) / CHUNK_STEPS, end >= nsteps, C::NACC)
+                                : 0u;
+                        if (due) {  // hand the accumulators to the epilogue
                             umma_commit(&sh->accf);
                             st.pending |= due;
                         }
-                        umma_commit(&sh->empty[stage]);
-                        if (++stage == C::STAGES) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
-                        continue;
-                    }
+                    } else {
                     for (int kk = 0; kk < cnt; ++kk) {
                         const int step = s0 + kk;
                         const uint32_t a_base = smem_base + stage * C::STAGE_BYTES + kk * C::STEP_BYTES;
@@ -497,6 +506,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                             st.pending |= due;
                             if constexpr (!GROUPED) st.fresh |= due;
                         }
+                    }
                     }
                     if (!ok) break;
                     umma_commit(&sh->empty[stage]);
