@@ -421,11 +421,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         break;
                     }
                     tc_fence_after();
-                    const int nstage = stage + 1 == C::STAGES ? 0 : stage + 1;
-                    const uint32_t nphase = nstage == 0 ? phase ^ 1u : phase;
-                    // Probe the next stage now; the test's latency hides
-                    // behind this stage's MMA issue.
-                    ready = mbar_test_wait(&sh->full[nstage], nphase);
+                    // Up to 3 digits, probe the next stage now (the test's
+                    // latency hides behind this stage's MMA issue); with one
+                    // step per stage (4+ digits) it measured 1% slower at 6.
+                    if constexpr (S <= 3) {
+                        const int nstage = stage + 1 == C::STAGES ? 0 : stage + 1;
+                        const uint32_t nphase = nstage == 0 ? phase ^ 1u : phase;
+                        ready = mbar_test_wait(&sh->full[nstage], nphase);
+                    }
                     if constexpr (S <= 3) {
                         static_assert((4 * CHUNK_STEPS) % C::KPS == 0, "every 16-step drain point ends a stage");
                         // At most 3 digits: every accumulator is drained every
