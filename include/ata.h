@@ -115,6 +115,20 @@ int ata_set_config(ata_handle h, const ata_config *cfg);
 int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda,
               void *C, int64_t ldc, int dtype, void *stream);
 
+/* low(C) <- alpha low(A^T A) + beta low(C): the BLAS ?syrk semantics of the
+ * paper's Section 3.1 (Algorithm 1 takes alpha and accumulates into C; the
+ * text applies beta by scaling C first).  Arguments, layout, ownership and
+ * errors as ata_lower, which is the case alpha = 1, beta = 0 (bit-identical
+ * results).  alpha and beta are applied where each entry of C is stored
+ * (FP64 arithmetic for the F64 modes, FP32 for the F32 modes): c <- alpha*v
+ * + beta*c, one extra rounding each.  beta == 0: C is not read (NaN or Inf
+ * there do not propagate).  alpha == 0 or m == 0: low(C) <- beta low(C)
+ * without touching A (beta == 1: nothing happens).  Non-finite alpha or
+ * beta: ATA_ERR_INVALID.  The strict upper triangle is never read or
+ * written. */
+int ata_syrk(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, int64_t lda,
+             double beta, void *C, int64_t ldc, int dtype, void *stream);
+
 /* low(C_i) <- low(A_i^T A_i) for `count` independent problems in one
  * persistent launch.  m, n, lda, ldc: HOST arrays of length count.  A, C:
  * HOST arrays of `count` DEVICE pointers.  Only ATA_F32, ATA_F32_BF16 and

@@ -50,6 +50,7 @@ def load():
     L.ata_status_string.argtypes = [ip]
     L.ata_status_string.restype = ctypes.c_char_p
     L.ata_plan_info.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64)]
+    L.ata_syrk.argtypes = [vp, i64, i64, ctypes.c_double, vp, i64, ctypes.c_double, vp, i64, ip, vp]
     L.ata_lower_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, ip, vp]
     L.ata_lower_noalloc.restype = ip
     L.ata_last_error.argtypes = [vp]
@@ -58,7 +59,7 @@ def load():
     L.ata_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.ata_tune.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp, ctypes.c_double, ctypes.POINTER(i64)]
     L.ata_tune_clear.argtypes = [vp]
-    for f in ("ata_create", "ata_set_config", "ata_lower", "ata_batched", "ata_sync",
+    for f in ("ata_create", "ata_set_config", "ata_lower", "ata_syrk", "ata_batched", "ata_sync",
               "ata_destroy", "ata_plan_info", "ata_version", "ata_set_timing",
               "ata_phase_times", "ata_tune", "ata_tune_clear"):
         getattr(L, f).restype = ip
@@ -139,6 +140,20 @@ class Handle:
         rc = self.lower_ptr(m, n, A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0), dtype, stream)
         if rc != 0:
             raise AtaError(rc, f"ata_lower [{self.last_error()}]")
+
+    def syrk_ptr(self, m, n, alpha, A_ptr, lda, beta, C_ptr, ldc, dtype, stream=None) -> int:
+        """Raw ata_syrk call; returns the status code (no exception)."""
+        return int(load().ata_syrk(self._h, int(m), int(n), float(alpha), A_ptr, int(lda), float(beta), C_ptr,
+                                   int(ldc), int(dtype), _stream_ptr(stream)))
+
+    def syrk(self, A, C, dtype, alpha=1.0, beta=0.0, stream=None):
+        """low(C) <- alpha low(A^T A) + beta low(C) for row-major CUDA tensors."""
+        m, n = A.shape
+        if A.stride(1) != 1 or C.stride(1) != 1:
+            raise ValueError("A and C must be row-major with unit column stride")
+        rc = self.syrk_ptr(m, n, alpha, A.data_ptr(), A.stride(0), beta, C.data_ptr(), C.stride(0), dtype, stream)
+        if rc != 0:
+            raise AtaError(rc, f"ata_syrk [{self.last_error()}]")
 
     def batched_ptr(self, ms, ns, A_ptrs, ldas, C_ptrs, ldcs, dtype, stream=None) -> int:
         count = len(ms)

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -147,7 +148,7 @@ int bind_plan(ata_handle h, CachedPlan &cp) {
     if (cp.ws_generation == h->ws_generation) return ATA_OK;
     const Plan &P = cp.plan;
     LeafParams &lp = cp.lp;
-    std::memset(&lp, 0, sizeof(lp));
+    lp = LeafParams{};  // zeros, alpha = 1, beta = 0
     if (P.uses_digits()) {
         for (size_t f = 0; f < P.families.size(); ++f) {
             lp.fam_base[f] = h->ws + P.families[f].offset;
@@ -314,18 +315,25 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     return ATA_OK;
 }
 
-int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
-              int dtype, void *stream) {
+namespace {
+
+// low(C) <- alpha low(A^T A) + beta low(C) (ata_lower: alpha = 1, beta = 0).
+int lower_impl(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, int64_t lda, double beta, void *C,
+               int64_t ldc, int dtype, void *stream) {
     if (!h) return ATA_ERR_INVALID;
     h->last_error.clear();
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
     if (m < 0 || n < 0) return ATA_ERR_INVALID;
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return ATA_ERR_INVALID;
     if (n == 0) return ATA_OK;
     if (ldc < n || !C) return ATA_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool f32 = is_f32_mode(dtype);
     const size_t es = f32 ? 4 : 8;
-    if (m == 0) return launch_zero_lower(C, n, ldc, f32, s) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
+    if (m == 0 || alpha == 0.0) {  // no product term: low(C) <- beta low(C)
+        if (beta == 1.0) return ATA_OK;
+        return launch_scale_lower(C, n, ldc, f32, beta, s) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
+    }
     if (lda < n || !A) return ATA_ERR_INVALID;
     if (ranges_overlap(A, ((m - 1) * lda + n) * es, C, ((n - 1) * ldc + n) * es)) return ATA_ERR_INVALID;
 
@@ -372,14 +380,28 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, vo
     lp.status = h->d_status;
     lp.A64 = static_cast<const double *>(A);
     lp.lda = lda;
+    lp.alpha = alpha;
+    lp.beta = beta;
     e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
     if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "leaf launch", e);
     mark(3);
-    if ((e = launch_combine(P, tables, ws + P.off_products, C, expo, s)) != cudaSuccess)
+    if ((e = launch_combine(P, tables, ws + P.off_products, C, expo, alpha, beta, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "combine launch", e);
     mark(4);
     if (h->timing) h->timed = true;
     return ATA_OK;
+}
+
+}  // namespace
+
+int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
+              int dtype, void *stream) {
+    return lower_impl(h, m, n, 1.0, A, lda, 0.0, C, ldc, dtype, stream);
+}
+
+int ata_syrk(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, int64_t lda, double beta, void *C,
+             int64_t ldc, int dtype, void *stream) {
+    return lower_impl(h, m, n, alpha, A, lda, beta, C, ldc, dtype, stream);
 }
 
 int ata_tune(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc, int dtype,
@@ -571,14 +593,14 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
     cudaError_t e = cudaMemcpyAsync(ws + cb.off_probs, cb.pinned, cb.table_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload", e);
     for (int i = 0; i < count; ++i)
-        if (n[i] > 0 && m[i] == 0 && (e = launch_zero_lower(C[i], n[i], ldc[i], f32, s)) != cudaSuccess)
+        if (n[i] > 0 && m[i] == 0 && (e = launch_scale_lower(C[i], n[i], ldc[i], f32, 0.0, s)) != cudaSuccess)
             return fail(h, ATA_ERR_CUDA, "zero fill", e);
     if ((e = launch_batched_expo(B, probs, f32, expo, h->d_status, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched exponents", e);
     if ((e = launch_batched_prep(B, probs, f32, expo, ws + cb.off_planes, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched digit prep", e);
     LeafParams lp;
-    std::memset(&lp, 0, sizeof(lp));
+    lp = LeafParams{};  // zeros, alpha = 1, beta = 0
     lp.tasks = reinterpret_cast<const LeafTask *>(ws + cb.off_tasks);
     lp.ntasks = static_cast<int>(B.tasks.size());
     lp.expo = expo;

@@ -571,7 +571,8 @@ template <typename TOut>
 __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
                                                           const int64_t *__restrict__ M, TOut *C,
-                                                          int64_t ldc, const int *__restrict__ expo) {
+                                                          int64_t ldc, const int *__restrict__ expo, double alpha,
+                                                          double beta) {
     __shared__ CombTerm st[MAX_CTERMS];
     __shared__ int s_min;
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
@@ -603,12 +604,11 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
             sum += ct.coef > 0 ? v : -v;
         }
         const int x = -(T_FRAC + 2 * DIGIT_TOP_BITS) + smin + d.rshift + expo[d.e_row0 + row] + ec;
-        if (sizeof(TOut) == 8)
-            C[d.c_off + static_cast<int64_t>(row) * ldc + col] =
-                static_cast<TOut>(static_cast<double>(sum) * exp2i(x));
+        TOut *c = C + d.c_off + static_cast<int64_t>(row) * ldc + col;
+        if constexpr (sizeof(TOut) == 8)
+            store_scaled(c, static_cast<double>(sum) * exp2i(x), alpha, beta);
         else
-            C[d.c_off + static_cast<int64_t>(row) * ldc + col] =
-                static_cast<TOut>(__ll2float_rn(sum) * exp2f_i(x));
+            store_scaled(c, __ll2float_rn(sum) * exp2f_i(x), alpha, beta);
     }
 }
 
@@ -617,7 +617,8 @@ template <typename TOut>
 __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
                                                           const double *__restrict__ M, TOut *C,
-                                                          int64_t ldc, const int *__restrict__ expo) {
+                                                          int64_t ldc, const int *__restrict__ expo, double alpha,
+                                                          double beta) {
     __shared__ CombTerm st[MAX_CTERMS];
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
     const int nt = d.nterms < MAX_CTERMS ? d.nterms : MAX_CTERMS;
@@ -638,7 +639,8 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__rest
             const double v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
             sum = ct.coef > 0 ? sum + v : sum - v;
         }
-        C[d.c_off + static_cast<int64_t>(row) * ldc + col] = static_cast<TOut>(sum * exp2i(expo[d.e_row0 + row] + ec));
+        store_scaled(C + d.c_off + static_cast<int64_t>(row) * ldc + col,
+                     static_cast<TOut>(sum * exp2i(expo[d.e_row0 + row] + ec)), alpha, beta);
     }
 }
 
@@ -702,18 +704,23 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int col = wn + 8 * fn + 2 * (lane & 3) + h;
-                if (row < t.rows && col < t.cols && (!t.diag || col <= row + t.diag_off))
-                    out[static_cast<int64_t>(row) * t.out_ld + col] = acc[fm][fn][h];
+                if (row < t.rows && col < t.cols && (!t.diag || col <= row + t.diag_off)) {
+                    double *o = out + static_cast<int64_t>(row) * t.out_ld + col;
+                    if (t.kind == OUT_M_F64)
+                        *o = acc[fm][fn][h];
+                    else
+                        store_scaled(o, acc[fm][fn][h], p.alpha, p.beta);
+                }
             }
         }
     }
 }
 
 template <typename T>
-__global__ void zero_lower_kernel(T *C, int64_t n, int64_t ldc) {
+__global__ void scale_lower_kernel(T *C, int64_t n, int64_t ldc, double beta) {
     const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t j = blockIdx.y + static_cast<int64_t>(blockIdx.z) * 65535;
-    if (j < n && k <= j) C[j * ldc + k] = T(0);
+    if (j < n && k <= j) C[j * ldc + k] = beta != 0.0 ? static_cast<T>(beta * C[j * ldc + k]) : T(0);
 }
 
 }  // namespace
@@ -835,7 +842,7 @@ cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s)
 }
 
 cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
-                           const int *expo, cudaStream_t s) {
+                           const int *expo, double alpha, double beta, cudaStream_t s) {
     if (P.combs.empty() || P.comb_tiles == 0) return cudaSuccess;
     const CombDesc *d = reinterpret_cast<const CombDesc *>(tables + P.t_combs);
     const CombTerm *t = reinterpret_cast<const CombTerm *>(tables + P.t_cterms);
@@ -843,27 +850,27 @@ cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, 
     const int nd = static_cast<int>(P.combs.size());
     if (P.p.mode == MODE_F64)
         combine_f64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
-                                                      static_cast<double *>(C), P.p.ldc, expo);
+                                                      static_cast<double *>(C), P.p.ldc, expo, alpha, beta);
     else if (P.p.mode == MODE_F32_FP8)  // FP8 products are FP32 sums, stored as double
         combine_f64_kernel<float><<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
-                                                     static_cast<float *>(C), P.p.ldc, expo);
+                                                     static_cast<float *>(C), P.p.ldc, expo, alpha, beta);
     else if (P.p.mode == MODE_F64_EMU)
         combine_i64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
-                                                      static_cast<double *>(C), P.p.ldc, expo);
+                                                      static_cast<double *>(C), P.p.ldc, expo, alpha, beta);
     else
         combine_i64_kernel<float><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
-                                                     static_cast<float *>(C), P.p.ldc, expo);
+                                                     static_cast<float *>(C), P.p.ldc, expo, alpha, beta);
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_lower(void *C, int64_t n, int64_t ldc, bool is_f32, cudaStream_t s) {
+cudaError_t launch_scale_lower(void *C, int64_t n, int64_t ldc, bool is_f32, double beta, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     dim3 grid(static_cast<unsigned>((n + 255) / 256), static_cast<unsigned>(n < 65535 ? n : 65535),
               static_cast<unsigned>((n + 65534) / 65535));
     if (is_f32)
-        zero_lower_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(C), n, ldc);
+        scale_lower_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(C), n, ldc, beta);
     else
-        zero_lower_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(C), n, ldc);
+        scale_lower_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(C), n, ldc, beta);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ struct LeafParams {
     int64_t fam_ld[MAX_FAMILIES];
     const BatchProb *probs;             // batched calls: problem table (else null)
     const uint8_t *batch_planes;        // batched calls: base of all problems' planes
+    double alpha = 1.0;                 // stores into C: alpha * product + beta * C
+    double beta = 0.0;                  // (beta == 0: C is not read)
 };
 
 // Column exponents e_j (smallest e with max_i |a_ij| < 2^e); flags a
@@ -44,8 +46,9 @@ cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *ex
 cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s);
 cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s);
 cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
-                           const int *expo, cudaStream_t s);
-cudaError_t launch_zero_lower(void *C, int64_t n, int64_t ldc, bool is_f32, cudaStream_t s);
+                           const int *expo, double alpha, double beta, cudaStream_t s);
+// low(C) <- beta * low(C) (beta == 0: zeros, C not read).
+cudaError_t launch_scale_lower(void *C, int64_t n, int64_t ldc, bool is_f32, double beta, cudaStream_t s);
 // Launches from explicit tables (allocation-free entry point).
 cudaError_t launch_prep_digits_raw(int slices, const void *A, bool is_f32, int64_t lda, const int *expo,
                                    const OpDesc *ops, int nops, const OpTerm *terms, const Family &fam0,

@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
-                            if (col < lim) out[col] = T[i] * exp2f_(er + (ev ? ev[col] : 0));
+                            if (col < lim) store_scaled(out + col, T[i] * exp2f_(er + (ev ? ev[col] : 0)), p.alpha, p.beta);
                         }
                     }
                 }
@@ -619,14 +619,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
                             if (col < lim)
-                                out[col] = static_cast<double>(T[i]) * exp2d(er + (ev ? ev[col] : 0));
+                                store_scaled(out + col, static_cast<double>(T[i]) * exp2d(er + (ev ? ev[col] : 0)),
+                                             p.alpha, p.beta);
                         }
                     } else {
                         float *out = static_cast<float *>(cbase) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
-                            if (col < lim) out[col] = __ll2float_rn(T[i]) * exp2f_(er + (ev ? ev[col] : 0));
+                            if (col < lim)
+                                store_scaled(out + col, __ll2float_rn(T[i]) * exp2f_(er + (ev ? ev[col] : 0)), p.alpha,
+                                             p.beta);
                         }
                     }
                 }

@@ -173,7 +173,7 @@ extern "C" int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t ld
     const bool f32 = dtype != ATA_F64_EMU;
     const size_t es = f32 ? 4 : 8;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (m == 0) return launch_zero_lower(C, n, ldc, f32, s) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
+    if (m == 0) return launch_scale_lower(C, n, ldc, f32, 0.0, s) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
     if (lda < n || !A) return ATA_ERR_INVALID;
     {
         const uintptr_t a = reinterpret_cast<uintptr_t>(A), c = reinterpret_cast<uintptr_t>(C);
@@ -209,7 +209,7 @@ extern "C" int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t ld
         cudaSuccess)
         return ATA_ERR_CUDA;
     LeafParams lp;
-    std::memset(&lp, 0, sizeof(lp));
+    lp = LeafParams{};  // zeros, alpha = 1, beta = 0
     lp.fam_base[0] = ws + L.fam.offset;
     lp.fam_ncb[0] = L.fam.cols / BLOCK_COLS;
     lp.tasks = tasks;

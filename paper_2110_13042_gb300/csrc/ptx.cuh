@@ -25,6 +25,18 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// ------------------------------------------------------------ C stores
+// c <- alpha * v + beta * c; with beta == 0 the old value is not read (so a
+// NaN left in C does not propagate), and alpha == 1, beta == 0 stores v as is.
+__device__ __forceinline__ void store_scaled(double *c, double v, double alpha, double beta) {
+    const double r = alpha * v;
+    *c = beta != 0.0 ? fma(beta, *c, r) : r;
+}
+__device__ __forceinline__ void store_scaled(float *c, float v, double alpha, double beta) {
+    const float r = static_cast<float>(alpha) * v;
+    *c = beta != 0.0 ? fmaf(static_cast<float>(beta), *c, r) : r;
+}
+
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
