@@ -106,7 +106,8 @@ __device__ __forceinline__ uint32_t due_mask(int c, bool last, int nacc) {
 struct Shared {
     uint64_t full[MAX_STAGES];
     uint64_t empty[MAX_STAGES];
-    uint64_t accf;
+    uint64_t accf;   // due accumulators handed to the epilogue (the second issuer's: accf2)
+    uint64_t accf2;
     uint64_t acce[MAX_ACC];
     uint32_t tmem_base;
     int abort_flag;
@@ -190,7 +191,7 @@ __device__ __forceinline__ void issue_group(uint32_t tmem, uint64_t da0, uint64_
             constexpr int ACC = acc_of(P, Q);
             constexpr bool has_next = P + Q + 1 <= S + 1;
             constexpr int NEXT = has_next ? acc_of(P, Q + 1) : -1;
-            constexpr bool merge = has_next && NEXT == ACC + 1 && (in_b(ACC) || !in_b(NEXT));
+            constexpr bool merge = has_next && NEXT == ACC + 1 && in_b(ACC) == in_b(NEXT);
             const uint64_t da = da0 + static_cast<uint64_t>((P - 1) * (A_SLICE_BYTES >> 4));
             const uint64_t db = db0 + static_cast<uint64_t>((Q - 1) * (B_SLICE_BYTES >> 4));
             if constexpr (in_b(ACC) == GB) umma_f16(tmem + ACC * TILE_N, da, db, merge ? IDESC2 : IDESC, 1u);
@@ -324,6 +325,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     using C = Cfg<S>;
     static_assert(!F8 || S == 1, "the FP8 mode has one plane");
     constexpr int KS = F8 ? KSTEP8 : KSTEP;  // contraction rows per K step
+    // 5+ digits: two issuing threads, warp 1 for accumulators 4, 0, 1 and
+    // warp 2 for 2, 3 (the ones drained every chunk), so a drain wait on 2 or
+    // 3 stalls only the second while the first keeps the tensor core fed.
+    constexpr bool DUAL = S >= 5;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     Shared *sh = reinterpret_cast<Shared *>(smem + C::STAGES * C::STAGE_BYTES);
@@ -334,9 +339,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            mbar_init(&sh->empty[s], DUAL ? 2 : 1);  // every issuer releases the stage
         }
         mbar_init(&sh->accf, 1);
+        mbar_init(&sh->accf2, 1);
         for (int a = 0; a < MAX_ACC; ++a) mbar_init(&sh->acce[a], NUM_EPI);
         sh->abort_flag = 0;
         fence_mbar_init();
@@ -399,6 +405,60 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 }
             }
             if (!ok) spin_ns(2000000);  // let copies already in flight land
+        }
+    } else if (DUAL && (warp == 1 || warp == 2)) {
+        // ----------------------------------- two MMA issuers (5+ digits) --
+        if (lane == 0) {
+            const bool gb = warp == 2;                  // accumulators 2, 3
+            const uint32_t mine = gb ? 0x0Cu : 0x13u;
+            uint64_t *my_accf = gb ? &sh->accf2 : &sh->accf;
+            int stage = 0;
+            uint32_t phase = 0;
+            IssueState st{0u, 0u, mine};  // every accumulator starts fresh
+            bool ok = true;
+            const uint32_t smem_base = smem_u32(smem);
+            for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
+                const int nsteps = (p.tasks[ti].klen + KS - 1) / KS;
+                for (int step = 0; step < nsteps; ++step) {
+                    if (!mbar_wait(&sh->full[stage], phase, abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
+                    const uint64_t da0 = sdesc_kmajor_sw32(a_base);
+                    const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
+                    if (((st.pending | st.fresh) & mine) == 0u) {
+                        if (gb)
+                            issue_group<S, true>(tmem, da0, db0);
+                        else
+                            issue_group<S, false>(tmem, da0, db0);
+                    } else if (gb) {
+                        ok = step_acc<S, 2>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                             step_acc<S, 3>(st, sh, tmem, da0, db0, abort_flag, p.status);
+                    } else {
+                        ok = step_acc<S, 4>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                             step_acc<S, 0>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
+                             step_acc<S, 1>(st, sh, tmem, da0, db0, abort_flag, p.status);
+                    }
+                    if (!ok) break;
+                    const bool last = step == nsteps - 1;
+                    const uint32_t due = (last || (step % CHUNK_STEPS) == CHUNK_STEPS - 1)
+                                             ? due_mask(step / CHUNK_STEPS, last, C::NACC) & mine
+                                             : 0u;
+                    if (due) {  // hand this issuer's due accumulators to the epilogue
+                        umma_commit(my_accf);
+                        st.pending |= due;
+                        st.fresh |= due;
+                    }
+                    umma_commit(&sh->empty[stage]);
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) spin_ns(2000000);  // let MMAs already issued retire
         }
     } else if (warp == 1) {
         // ------------------------------------------------- MMA issuer --
@@ -528,7 +588,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
         const int row = 32 * q + lane;               // tile row == TMEM lane
         const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16);
         const int colbase = EPI_COLS * third;
-        uint32_t accf_phase = 0;
+        uint32_t accf_phase = 0, accf2_phase = 0;
         bool ok = true;
         constexpr bool ZERO = S <= 4;  // the grouped issue path (see issue_group)
         if constexpr (ZERO) {
@@ -556,6 +616,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 const bool last = c == nchunks - 1;
                 const uint32_t due = due_mask(c, last, C::NACC);
                 if (!due) continue;
+                if constexpr (DUAL) {
+                    // the first issuer's accumulators (4, 0, 1), then the second's (2, 3)
+                    if (due & ~0x0Cu) {
+                        if (!mbar_wait(&sh->accf, accf_phase, abort_flag, p.status)) {
+                            ok = false;
+                            break;
+                        }
+                        accf_phase ^= 1u;
+                        tc_fence_after();
+                        if (due & 16u) drain_one<4, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (due & 1u) drain_one<0, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (due & 2u) drain_one<1, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                    }
+                    if (due & 0x0Cu) {
+                        if (!mbar_wait(&sh->accf2, accf2_phase, abort_flag, p.status)) {
+                            ok = false;
+                            break;
+                        }
+                        accf2_phase ^= 1u;
+                        tc_fence_after();
+                        if (due & 4u) drain_one<2, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (due & 8u) drain_one<3, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                    }
+                    continue;
+                }
                 if (!mbar_wait(&sh->accf, accf_phase, abort_flag, p.status)) {
                     ok = false;
                     break;

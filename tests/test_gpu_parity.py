@@ -266,3 +266,22 @@ def test_8192_square_sampled(h, mode, depth):
     err = np.max(np.abs(C[j, k] - vals) / dens)
     assert err <= TOL[mode], err
     assert np.all(np.triu(C, 1) == 0)
+
+
+@pytest.mark.parametrize("slices", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("depth", [0, 1])
+def test_every_digit_count(h, slices, depth):
+    """F64_EMU with S digits (F = 8 + 9 (S - 1) fraction bits per column): the
+    error stays within 8 units of the digit representation, 2^(3 - F) of
+    (|A|^T|A|)_jk (floored at 1e-14: the int64 sum and its final rounding), and
+    small integers are exact for every S."""
+    A = inputs.uniform(700, 333, seed=40 + slices)
+    ref, D = reference(A)
+    C = run(h, A, F64_EMU, cutoff=80, depth=depth, slices=slices)
+    tol = max(2.0 ** (3 - (8 + 9 * (slices - 1))), 1e-14)
+    assert rel_err(C, ref, D) <= tol
+    assert upper_untouched(C)
+    Ai = inputs.integer_valued(531, 277, seed=9)
+    Ci = run(h, Ai, F64_EMU, cutoff=70, depth=depth, slices=slices)
+    low = np.tril_indices(277)
+    assert np.array_equal(Ci[low], reference(Ai)[0][low])
