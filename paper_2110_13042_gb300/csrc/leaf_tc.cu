@@ -26,19 +26,22 @@
 // Pipeline (one CTA per SM, persistent over a static round-robin task list):
 //   warp 0       TMA producer: per stage and digit, one bulk copy of the
 //                operand rows' 4 KB (A) and 3 KB (B) pre-swizzled images.
-//   warp 1       TMEM allocator + single-thread tcgen05.mma issuer.
+//   warp 1       TMEM allocator + single-thread tcgen05.mma issuer; with
+//                5+ digits warps 1, 2, 3 each issue the MMAs of their own
+//                accumulators ({4}, {0, 1}, {2, 3}).
 //   warps 4..15  epilogue: tcgen05.ld drains, int64 accumulation, stores
 //                (3 warps per TMEM lane quadrant, 32 columns each).
-//   (warps 2, 3 idle: 16 warps keep the 4 SM sub-partitions balanced at
-//    4 warps each, a budget of 128 registers per thread.)
-// The issuer and the epilogue visit the accumulators in the same fixed order
+//   (16 warps keep the 4 SM sub-partitions balanced at 4 warps each, a
+//    budget of 128 registers per thread; warps 2, 3 are idle below 5 digits.)
+// The issuers and the epilogue visit the accumulators in the same fixed order
 // (4, 0, 1, 2, 3): the ones drained every chunk come last, so the tensor core
 // keeps working on the others while they are drained.
-// The tensor core queues almost nothing ahead, so every instruction the
-// issuing thread spends between MMAs idles it.  Steps with no accumulator
-// pending or fresh (three in four) therefore take a branch-free path that
-// merges pairs with adjacent accumulators into N = 192 MMAs and probes the
-// next stage's barrier without blocking.
+// The tensor core queues only a few instructions, so every instruction an
+// issuing thread spends between MMAs can idle it (measured: the issuing
+// thread, not memory or the MMA rate, bounds the leaf).  Steps with no
+// accumulator pending or fresh take a branch-free path that merges pairs
+// with adjacent accumulators of the same issuer into N = 192 MMAs; up to 3
+// digits the bookkeeping runs once per multi-step stage.
 // All mbarrier waits are bounded (ptx.cuh).
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -106,8 +109,7 @@ __device__ __forceinline__ uint32_t due_mask(int c, bool last, int nacc) {
 struct Shared {
     uint64_t full[MAX_STAGES];
     uint64_t empty[MAX_STAGES];
-    uint64_t accf;   // due accumulators handed to the epilogue (the second issuer's: accf2)
-    uint64_t accf2;
+    uint64_t accf[3];  // due accumulators handed to the epilogue, one barrier per issuer
     uint64_t acce[MAX_ACC];
     uint32_t tmem_base;
     int abort_flag;
@@ -173,6 +175,41 @@ __device__ __forceinline__ void issue_fast(uint32_t tmem, uint64_t da0, uint64_t
 
 // Accumulators 2 and 3 are the ones drained every 64 rows.
 __host__ __device__ constexpr bool in_b(int acc) { return acc == 2 || acc == 3; }
+
+// Several issuing threads (5+ digits): the issuer that owns an accumulator.
+// Two: {4, 0, 1}, {2, 3}.  Three: {4}, {0, 1}, {2, 3}.
+template <int NI>
+__host__ __device__ constexpr int issuer_of(int acc) {
+    return NI == 2 ? (in_b(acc) ? 1 : 0) : (acc == 4 ? 0 : (acc <= 1 ? 1 : 2));
+}
+template <int NI>
+__host__ __device__ constexpr uint32_t issuer_mask(int g) {
+    uint32_t m = 0;
+    for (int a = 0; a < MAX_ACC; ++a)
+        if (issuer_of<NI>(a) == g) m |= 1u << a;
+    return m;
+}
+
+// Every pair whose accumulator belongs to issuer G, with (p, q), (p, q + 1)
+// sharing one N = 192 MMA when their accumulators are adjacent and both G's.
+template <int S, int NI, int G, int P = 1, int Q = 1>
+__device__ __forceinline__ void issue_own(uint32_t tmem, uint64_t da0, uint64_t db0) {
+    if constexpr (P <= S) {
+        if constexpr (P + Q <= S + 1) {
+            constexpr int ACC = acc_of(P, Q);
+            constexpr bool has_next = P + Q + 1 <= S + 1;
+            constexpr int NEXT = has_next ? acc_of(P, Q + 1) : -1;
+            constexpr bool own = issuer_of<NI>(ACC) == G;
+            constexpr bool merge = own && has_next && NEXT == ACC + 1 && issuer_of<NI>(NEXT) == G;
+            const uint64_t da = da0 + static_cast<uint64_t>((P - 1) * (A_SLICE_BYTES >> 4));
+            const uint64_t db = db0 + static_cast<uint64_t>((Q - 1) * (B_SLICE_BYTES >> 4));
+            if constexpr (own) umma_f16(tmem + ACC * TILE_N, da, db, merge ? IDESC2 : IDESC, 1u);
+            issue_own<S, NI, G, P, Q + (merge ? 2 : 1)>(tmem, da0, db0);
+        } else {
+            issue_own<S, NI, G, P + 1, 1>(tmem, da0, db0);
+        }
+    }
+}
 
 // With at most 4 digits every K step takes one path (no first-write case:
 // the epilogue zeroes an accumulator when it drains it), in two groups.
@@ -244,6 +281,17 @@ __device__ __forceinline__ bool step_acc(IssueState &st, Shared *sh, uint32_t tm
         st.fresh &= ~bit;
         return true;
     }
+}
+
+// Slow step of issuer G: its accumulators in the order 4, 0, 1, 2, 3.
+template <int S, int NI, int G>
+__device__ __forceinline__ bool step_own(IssueState &st, Shared *sh, uint32_t tmem, uint64_t da0, uint64_t db0,
+                                         volatile int *abort_flag, int *status) {
+    return (issuer_of<NI>(4) != G || step_acc<S, 4>(st, sh, tmem, da0, db0, abort_flag, status)) &&
+           (issuer_of<NI>(0) != G || step_acc<S, 0>(st, sh, tmem, da0, db0, abort_flag, status)) &&
+           (issuer_of<NI>(1) != G || step_acc<S, 1>(st, sh, tmem, da0, db0, abort_flag, status)) &&
+           (issuer_of<NI>(2) != G || step_acc<S, 2>(st, sh, tmem, da0, db0, abort_flag, status)) &&
+           (issuer_of<NI>(3) != G || step_acc<S, 3>(st, sh, tmem, da0, db0, abort_flag, status));
 }
 
 // Add one drained accumulator (16 columns) into T, kept in units of
@@ -325,10 +373,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     using C = Cfg<S>;
     static_assert(!F8 || S == 1, "the FP8 mode has one plane");
     constexpr int KS = F8 ? KSTEP8 : KSTEP;  // contraction rows per K step
-    // 5+ digits: two issuing threads, warp 1 for accumulators 4, 0, 1 and
-    // warp 2 for 2, 3 (the ones drained every chunk), so a drain wait on 2 or
-    // 3 stalls only the second while the first keeps the tensor core fed.
+    // 5+ digits: three issuing threads (warps 1, 2, 3) owning accumulators
+    // {4}, {0, 1}, {2, 3} (issuer_of), so a drain wait stalls only the issuer
+    // of the accumulator being drained while the others keep the tensor core
+    // fed, and the per-step bookkeeping is split between them.  Measured at
+    // 8192^2, S = 6: one issuer 9.81 ms, two 8.87-8.98, three 8.19.
     constexpr bool DUAL = S >= 5;
+    constexpr int NI = DUAL ? 3 : 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     Shared *sh = reinterpret_cast<Shared *>(smem + C::STAGES * C::STAGE_BYTES);
@@ -339,10 +390,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], DUAL ? 2 : 1);  // every issuer releases the stage
+            mbar_init(&sh->empty[s], NI);  // every issuer releases the stage
         }
-        mbar_init(&sh->accf, 1);
-        mbar_init(&sh->accf2, 1);
+        for (int g = 0; g < 3; ++g) mbar_init(&sh->accf[g], 1);
         for (int a = 0; a < MAX_ACC; ++a) mbar_init(&sh->acce[a], NUM_EPI);
         sh->abort_flag = 0;
         fence_mbar_init();
@@ -406,12 +456,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             }
             if (!ok) spin_ns(2000000);  // let copies already in flight land
         }
-    } else if (DUAL && (warp == 1 || warp == 2)) {
-        // ----------------------------------- two MMA issuers (5+ digits) --
+    } else if (DUAL && warp >= 1 && warp <= NI) {
+        // ------------------------------------- NI MMA issuers (5+ digits) --
         if (lane == 0) {
-            const bool gb = warp == 2;                  // accumulators 2, 3
-            const uint32_t mine = gb ? 0x0Cu : 0x13u;
-            uint64_t *my_accf = gb ? &sh->accf2 : &sh->accf;
+            const int g = warp - 1;
+            const uint32_t mine = g == 0 ? issuer_mask<NI>(0) : g == 1 ? issuer_mask<NI>(1) : issuer_mask<NI>(2);
+            uint64_t *my_accf = &sh->accf[g];
             int stage = 0;
             uint32_t phase = 0;
             IssueState st{0u, 0u, mine};  // every accumulator starts fresh
@@ -429,17 +479,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     const uint64_t da0 = sdesc_kmajor_sw32(a_base);
                     const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
                     if (((st.pending | st.fresh) & mine) == 0u) {
-                        if (gb)
-                            issue_group<S, true>(tmem, da0, db0);
+                        if (g == 0)
+                            issue_own<S, NI, 0>(tmem, da0, db0);
+                        else if (g == 1)
+                            issue_own<S, NI, 1>(tmem, da0, db0);
                         else
-                            issue_group<S, false>(tmem, da0, db0);
-                    } else if (gb) {
-                        ok = step_acc<S, 2>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                             step_acc<S, 3>(st, sh, tmem, da0, db0, abort_flag, p.status);
+                            issue_own<S, NI, 2>(tmem, da0, db0);
                     } else {
-                        ok = step_acc<S, 4>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                             step_acc<S, 0>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                             step_acc<S, 1>(st, sh, tmem, da0, db0, abort_flag, p.status);
+                        ok = g == 0   ? step_own<S, NI, 0>(st, sh, tmem, da0, db0, abort_flag, p.status)
+                             : g == 1 ? step_own<S, NI, 1>(st, sh, tmem, da0, db0, abort_flag, p.status)
+                                      : step_own<S, NI, 2>(st, sh, tmem, da0, db0, abort_flag, p.status);
                     }
                     if (!ok) break;
                     const bool last = step == nsteps - 1;
@@ -527,7 +576,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                 ? due_mask((end - 1) / CHUNK_STEPS, end >= nsteps, C::NACC)
                                 : 0u;
                         if (due) {  // hand the accumulators to the epilogue
-                            umma_commit(&sh->accf);
+                            umma_commit(&sh->accf[0]);
                             st.pending |= due;
                         }
                     } else {
@@ -565,7 +614,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                                  ? due_mask(step / CHUNK_STEPS, last, C::NACC)
                                                  : 0u;
                         if (due) {  // hand the due accumulators to the epilogue
-                            umma_commit(&sh->accf);
+                            umma_commit(&sh->accf[0]);
                             st.pending |= due;
                             if constexpr (!GROUPED) st.fresh |= due;
                         }
@@ -588,7 +637,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
         const int row = 32 * q + lane;               // tile row == TMEM lane
         const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16);
         const int colbase = EPI_COLS * third;
-        uint32_t accf_phase = 0, accf2_phase = 0;
+        uint32_t accf_phase = 0;  // bit g: parity of the next wait on accf[g]
         bool ok = true;
         constexpr bool ZERO = S <= 4;  // the grouped issue path (see issue_group)
         if constexpr (ZERO) {
@@ -617,31 +666,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 const uint32_t due = due_mask(c, last, C::NACC);
                 if (!due) continue;
                 if constexpr (DUAL) {
-                    // the first issuer's accumulators (4, 0, 1), then the second's (2, 3)
-                    if (due & ~0x0Cu) {
-                        if (!mbar_wait(&sh->accf, accf_phase, abort_flag, p.status)) {
-                            ok = false;
+                    // issuer by issuer, each issuer's accumulators in the order 4, 0, 1, 2, 3
+                    bool good = true;
+#pragma unroll
+                    for (int gi = 0; gi < NI; ++gi) {
+                        const uint32_t m = issuer_mask<NI>(gi) & due;
+                        if (!m) continue;
+                        if (!mbar_wait(&sh->accf[gi], (accf_phase >> gi) & 1u, abort_flag, p.status)) {
+                            good = false;
                             break;
                         }
-                        accf_phase ^= 1u;
+                        accf_phase ^= 1u << gi;
                         tc_fence_after();
-                        if (due & 16u) drain_one<4, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (due & 1u) drain_one<0, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (due & 2u) drain_one<1, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 16u) drain_one<4, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 1u) drain_one<0, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 2u) drain_one<1, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 4u) drain_one<2, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 8u) drain_one<3, false, false>(T, tbase, colbase, sh, h, fold_scale);
                     }
-                    if (due & 0x0Cu) {
-                        if (!mbar_wait(&sh->accf2, accf2_phase, abort_flag, p.status)) {
-                            ok = false;
-                            break;
-                        }
-                        accf2_phase ^= 1u;
-                        tc_fence_after();
-                        if (due & 4u) drain_one<2, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (due & 8u) drain_one<3, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                    if (!good) {
+                        ok = false;
+                        break;
                     }
                     continue;
                 }
-                if (!mbar_wait(&sh->accf, accf_phase, abort_flag, p.status)) {
+                if (!mbar_wait(&sh->accf[0], accf_phase, abort_flag, p.status)) {
                     ok = false;
                     break;
                 }
