@@ -129,6 +129,22 @@ struct Families {
     Family f[MAX_FAMILIES];
 };
 
+// The operand a prep tile belongs to, and the tile's index within it
+// (interleaved groups: see OpDesc::ilv_n).
+__device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t tile);
+__device__ __forceinline__ int op_of_tile(const OpDesc *ops, int nops, int64_t tile, int64_t *local) {
+    int i = find_desc(ops, nops, tile);
+    const int64_t g = tile - ops[i].tile_base;
+    if (ops[i].ilv_n > 1) {
+        const int first = i - ops[i].ilv_i;
+        i = first + static_cast<int>(g % ops[i].ilv_n);
+        *local = g / ops[first].ilv_n;
+    } else {
+        *local = g;
+    }
+    return i;
+}
+
 __device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t tile) {
     int lo = 0, hi = nops - 1;
     while (lo < hi) {
@@ -413,9 +429,10 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     const OpDesc *o = cached ? s_ops : ops;
     const OpTerm *tt = cached ? s_terms : terms;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const OpDesc od = o[find_desc(o, nops, tile)];
+        int64_t local;
+        const OpDesc od = o[op_of_tile(o, nops, tile, &local)];
         // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
-        prep_tile<S, T, F8>(A, lda, expo, od, tt, tile, fams.f[od.family], ws, sV, F8 ? 7 : 8);
+        prep_tile<S, T, F8>(A, lda, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV, F8 ? 7 : 8);
     }
 }
 
@@ -515,8 +532,8 @@ __global__ void __launch_bounds__(256) prep_f64_kernel(const T *__restrict__ A, 
                                                        const OpTerm *__restrict__ terms,
                                                        Families fams, uint8_t *ws) {
     const int64_t tile = blockIdx.x;
-    const OpDesc od = ops[find_desc(ops, nops, tile)];
-    const int64_t local = tile - od.tile_base;
+    int64_t local;
+    const OpDesc od = ops[op_of_tile(ops, nops, tile, &local)];
     const int tiles_k = od.K_pitch / PREP_K;
     const int k0 = static_cast<int>(local % tiles_k) * PREP_K;
     const int c0 = static_cast<int>(local / tiles_k) * PREP_C;

@@ -624,11 +624,34 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     }
     P.product_bytes = B.prod_elems * 8;
     P.off_products = take(P.product_bytes);
-    // prep tile prefix sums
-    P.prep_tiles = 0;
-    for (OpDesc &o : P.ops) {
-        o.tile_base = P.prep_tiles;
-        P.prep_tiles += prep_tiles_for(B.digits, o.K_pitch, o.P_pad, B.fp8);
+    // Prep tiles: operands of one family and shape are grouped (in order of
+    // first appearance) and share an interleaved tile range (OpDesc::ilv_n).
+    {
+        std::vector<OpDesc> grouped;
+        grouped.reserve(P.ops.size());
+        std::vector<bool> taken(P.ops.size(), false);
+        P.prep_tiles = 0;
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            if (taken[i]) continue;
+            const OpDesc &key = P.ops[i];
+            std::vector<size_t> members;
+            for (size_t j = i; j < P.ops.size(); ++j)
+                if (!taken[j] && P.ops[j].family == key.family && P.ops[j].K_pitch == key.K_pitch &&
+                    P.ops[j].P_pad == key.P_pad) {
+                    members.push_back(j);
+                    taken[j] = true;
+                }
+            const int64_t per = prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
+            for (size_t k = 0; k < members.size(); ++k) {
+                OpDesc o = P.ops[members[k]];
+                o.tile_base = P.prep_tiles;
+                o.ilv_n = static_cast<int32_t>(members.size());
+                o.ilv_i = static_cast<int32_t>(k);
+                grouped.push_back(o);
+            }
+            P.prep_tiles += per * static_cast<int64_t>(members.size());
+        }
+        P.ops.swap(grouped);
     }
     P.t_ops = 0;
     P.t_terms = round_up(P.t_ops + static_cast<int64_t>(P.ops.size() * sizeof(OpDesc)), 256);

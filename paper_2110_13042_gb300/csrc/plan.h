@@ -79,6 +79,13 @@ struct OpDesc {
     int32_t K_pitch;     // contraction rows written (multiple of PREP_K)
     int32_t P_pad;       // columns written (multiple of TILE)
     int64_t tile_base;   // prefix count of prep tiles (flat grid)
+    // Operands of one family and shape share a tile range, interleaved: tile
+    // tile_base + i of the range is tile i / ilv_n of the group's operand
+    // i mod ilv_n, so operand sums that read the same blocks of A read them
+    // at about the same time (L2 hits).  ilv_i: this operand's index in its
+    // group (0 .. ilv_n - 1; ilv_n <= 1: not interleaved).
+    int32_t ilv_n;
+    int32_t ilv_i;
 };
 
 struct Family {
