@@ -578,7 +578,11 @@ __device__ __forceinline__ int find_comb(const CombDesc *d, int nd, int64_t tile
     return lo;
 }
 
-constexpr int MAX_CTERMS = 256;
+// Combine tile of a block: COMB_ROWS x COMB_COLS entries of one region; the
+// thread owns column lane and rows warp + 8 i (i < 8).  Every term's eight
+// loads are issued together, and the term table is read straight from
+// global memory (the same entries for the whole block).
+constexpr int COMB_RPT = COMB_ROWS / 8;  // rows per thread
 
 // Exact Strassen result sums: region = sum_r coef_r * T_r * 2^(shift_r),
 // added in int64 in units of 2^(smin + rshift) (rshift > 0 only when the
@@ -590,74 +594,85 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
                                                           const int64_t *__restrict__ M, TOut *C,
                                                           int64_t ldc, const int *__restrict__ expo, double alpha,
                                                           double beta) {
-    __shared__ CombTerm st[MAX_CTERMS];
-    __shared__ int s_min;
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
-    const int nt = d.nterms < MAX_CTERMS ? d.nterms : MAX_CTERMS;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) st[t] = cterms[d.first_term + t];
-    if (threadIdx.x == 0) s_min = 1 << 20;
-    __syncthreads();
-    if (threadIdx.x < nt) atomicMin(&s_min, st[threadIdx.x].shift);
-    __syncthreads();
-    const int smin = s_min;
     const int64_t local = blockIdx.x - d.tile_base;
-    const int tcols = (d.cols + 31) / 32;
-    const int r0 = static_cast<int>(local / tcols) * 32;
-    const int col = static_cast<int>(local % tcols) * 32 + (threadIdx.x & 31);
+    const int tcols = (d.cols + COMB_COLS - 1) / COMB_COLS;
+    const int r0 = static_cast<int>(local / tcols) * COMB_ROWS + (threadIdx.x >> 5);
+    const int col = static_cast<int>(local % tcols) * COMB_COLS + (threadIdx.x & 31);
     if (col >= d.cols) return;
-    const int ec = expo[d.e_col0 + col];
-    for (int rr = threadIdx.x >> 5; rr < 32; rr += 8) {
-        const int row = r0 + rr;
-        if (row >= d.rows) break;
-        int64_t sum = 0;
-        for (int t = 0; t < nt; ++t) {
-            const CombTerm ct = st[t];
-            int64_t v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
-            const int dsh = ct.shift - smin - d.rshift;
-            if (dsh >= 0)
-                v = v * (int64_t(1) << dsh);
-            else
-                v = (v + (int64_t(1) << (-dsh - 1))) >> (-dsh);
-            sum += ct.coef > 0 ? v : -v;
+    int64_t sum[COMB_RPT];
+#pragma unroll
+    for (int i = 0; i < COMB_RPT; ++i) sum[i] = 0;
+    for (int t = 0; t < d.nterms; ++t) {
+        const CombTerm ct = cterms[d.first_term + t];
+        const int64_t *src = M + ct.src_off + col;
+        int64_t v[COMB_RPT];
+#pragma unroll
+        for (int i = 0; i < COMB_RPT; ++i) {
+            const int row = r0 + 8 * i;
+            v[i] = row < d.rows ? src[static_cast<int64_t>(row) * ct.ld] : 0;
         }
-        const int x = -(T_FRAC + 2 * DIGIT_TOP_BITS) + smin + d.rshift + expo[d.e_row0 + row] + ec;
+        const int dsh = ct.shift - d.smin - d.rshift;
+#pragma unroll
+        for (int i = 0; i < COMB_RPT; ++i) {
+            int64_t x = v[i];
+            if (dsh >= 0)
+                x = x * (int64_t(1) << dsh);
+            else
+                x = (x + (int64_t(1) << (-dsh - 1))) >> (-dsh);
+            sum[i] += ct.coef > 0 ? x : -x;
+        }
+    }
+    const int xc = -(T_FRAC + 2 * DIGIT_TOP_BITS) + d.smin + d.rshift + expo[d.e_col0 + col];
+#pragma unroll
+    for (int i = 0; i < COMB_RPT; ++i) {
+        const int row = r0 + 8 * i;
+        if (row >= d.rows) break;
+        const int x = xc + expo[d.e_row0 + row];
         TOut *c = C + d.c_off + static_cast<int64_t>(row) * ldc + col;
         if constexpr (sizeof(TOut) == 8)
-            store_scaled(c, static_cast<double>(sum) * exp2i(x), alpha, beta);
+            store_scaled(c, static_cast<double>(sum[i]) * exp2i(x), alpha, beta);
         else
-            store_scaled(c, __ll2float_rn(sum) * exp2f_i(x), alpha, beta);
+            store_scaled(c, __ll2float_rn(sum[i]) * exp2f_i(x), alpha, beta);
     }
 }
 
-// Native FP64 result sums (fixed term order), then the column scales.
+// Native FP64 (and FP8-mode) result sums, in the fixed term order, then the
+// column scales.
 template <typename TOut>
 __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
                                                           const double *__restrict__ M, TOut *C,
                                                           int64_t ldc, const int *__restrict__ expo, double alpha,
                                                           double beta) {
-    __shared__ CombTerm st[MAX_CTERMS];
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
-    const int nt = d.nterms < MAX_CTERMS ? d.nterms : MAX_CTERMS;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) st[t] = cterms[d.first_term + t];
-    __syncthreads();
     const int64_t local = blockIdx.x - d.tile_base;
-    const int tcols = (d.cols + 31) / 32;
-    const int r0 = static_cast<int>(local / tcols) * 32;
-    const int col = static_cast<int>(local % tcols) * 32 + (threadIdx.x & 31);
+    const int tcols = (d.cols + COMB_COLS - 1) / COMB_COLS;
+    const int r0 = static_cast<int>(local / tcols) * COMB_ROWS + (threadIdx.x >> 5);
+    const int col = static_cast<int>(local % tcols) * COMB_COLS + (threadIdx.x & 31);
     if (col >= d.cols) return;
-    const int ec = expo[d.e_col0 + col];
-    for (int rr = threadIdx.x >> 5; rr < 32; rr += 8) {
-        const int row = r0 + rr;
-        if (row >= d.rows) break;
-        double sum = 0.0;
-        for (int t = 0; t < nt; ++t) {
-            const CombTerm ct = st[t];
-            const double v = M[ct.src_off + static_cast<int64_t>(row) * ct.ld + col];
-            sum = ct.coef > 0 ? sum + v : sum - v;
+    double sum[COMB_RPT];
+#pragma unroll
+    for (int i = 0; i < COMB_RPT; ++i) sum[i] = 0.0;
+    for (int t = 0; t < d.nterms; ++t) {
+        const CombTerm ct = cterms[d.first_term + t];
+        const double *src = M + ct.src_off + col;
+        double v[COMB_RPT];
+#pragma unroll
+        for (int i = 0; i < COMB_RPT; ++i) {
+            const int row = r0 + 8 * i;
+            v[i] = row < d.rows ? src[static_cast<int64_t>(row) * ct.ld] : 0.0;
         }
+#pragma unroll
+        for (int i = 0; i < COMB_RPT; ++i) sum[i] = ct.coef > 0 ? sum[i] + v[i] : sum[i] - v[i];
+    }
+    const int ec = expo[d.e_col0 + col];
+#pragma unroll
+    for (int i = 0; i < COMB_RPT; ++i) {
+        const int row = r0 + 8 * i;
+        if (row >= d.rows) break;
         store_scaled(C + d.c_off + static_cast<int64_t>(row) * ldc + col,
-                     static_cast<TOut>(sum * exp2i(expo[d.e_row0 + row] + ec)), alpha, beta);
+                     static_cast<TOut>(sum[i] * exp2i(expo[d.e_row0 + row] + ec)), alpha, beta);
     }
 }
 

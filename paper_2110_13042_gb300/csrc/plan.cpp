@@ -329,8 +329,9 @@ struct Builder {
                         c.rshift++;
                     }
                 }
+                c.smin = smin;
                 c.tile_base = P.comb_tiles;
-                P.comb_tiles += ceil_div(c.rows, 32) * ceil_div(c.cols, 32);
+                P.comb_tiles += ceil_div(c.rows, COMB_ROWS) * ceil_div(c.cols, COMB_COLS);
                 P.combs.push_back(c);
             }
         }

@@ -182,10 +182,12 @@ struct CombDesc {
     int32_t e_row0;      // A column of region row 0 (exponent index)
     int32_t e_col0;      // A column of region column 0
     int32_t first_term, nterms;
-    int64_t tile_base;   // prefix count of 32x32 combine tiles
-    int32_t rshift;      // products are summed in units 2^(min shift + rshift)
-    int32_t pad;
+    int64_t tile_base;   // prefix count of combine tiles (COMB_ROWS x COMB_COLS)
+    int32_t rshift;      // products are summed in units 2^(smin + rshift)
+    int32_t smin;        // smallest term shift
 };
+constexpr int COMB_ROWS = 64;  // combine tile: 64 rows x 32 columns, 8 rows per thread
+constexpr int COMB_COLS = 32;
 
 struct PlanParams {
     int64_t m = 0, n = 0, lda = 0, ldc = 0;
