@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (auto plan instead)")
     ap.add_argument("--tune-budget-ms", type=float, default=3000.0)
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched leg (one JSON object; used for its launch-list profile)")
     ap.add_argument("--ref-seconds", type=float, default=4.0, help="CPU seconds per reference step")
     return ap.parse_args()
 
@@ -298,6 +300,24 @@ def main():
     torch.cuda.set_device(dev)
     import paper_2110_13042_gb300 as ata
     from paper_2110_13042_gb300 import inputs
+
+    if args.batched_only:
+        bstream = torch.cuda.current_stream(dev)
+
+        def timed_b(fn, k, w):
+            for _ in range(w):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(bstream)
+            for _ in range(k):
+                fn()
+            e1.record(bstream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / k
+        print(json.dumps(batched_bench(ata, torch, dev, bstream, args, timed_b)))
+        return
 
     m, n, mode = args.m, args.n, MODES[args.mode]
     f32 = mode in (2, 4, 5)
