@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.h"
 #include "ptx.cuh"
@@ -135,10 +136,12 @@ __device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t ti
 __device__ __forceinline__ int op_of_tile(const OpDesc *ops, int nops, int64_t tile, int64_t *local) {
     int i = find_desc(ops, nops, tile);
     const int64_t g = tile - ops[i].tile_base;
-    if (ops[i].ilv_n > 1) {
-        const int first = i - ops[i].ilv_i;
-        i = first + static_cast<int>(g % ops[i].ilv_n);
-        *local = g / ops[first].ilv_n;
+    const int n = ops[i].ilv_n;
+    if (n > 1) {  // tile counts fit 32 bits (checked at launch): 32-bit division
+        const uint32_t g32 = static_cast<uint32_t>(g);
+        const uint32_t q = g32 / static_cast<uint32_t>(n);
+        i = i - ops[i].ilv_i + static_cast<int>(g32 - q * static_cast<uint32_t>(n));
+        *local = q;
     } else {
         *local = g;
     }
@@ -195,14 +198,32 @@ __device__ __forceinline__ int64_t fixed_of_fast(float a, int sh) {
     return (bits >> 31) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
 }
 
+// 32-bit form of fixed_of_fast for FP32 inputs and F <= 29 fraction bits
+// (one to three digits): M 2^(P+1) < 2^31 with P = F - 23 <= 6, and a
+// rounding position past bit 30 leaves |a 2^sh| < 1/2, i.e. 0.  Same result
+// as the 64-bit form.
+template <int F>
+__device__ __forceinline__ int32_t fixed32_of_fast(float a, int sh) {
+    static_assert(F <= 29, "32-bit fixed point");
+    constexpr int P = F - 23 > 0 ? F - 23 : 0;
+    const uint32_t bits = __float_as_uint(a);
+    const int eb = static_cast<int>((bits >> 23) & 0xFF);
+    const uint32_t mant = bits & 0x7FFFFFu;
+    const uint32_t M = eb ? (mant | 0x800000u) : mant;
+    const int s = (eb ? eb - 150 : -149) + sh;
+    const int u = max(P - s, 0);
+    const uint32_t r = u > 30 ? 0u : ((M << (P + 1)) + (1u << u)) >> (u + 1);
+    return (bits >> 31) ? -static_cast<int32_t>(r) : static_cast<int32_t>(r);
+}
+
 // Digit q of w = V + sum_{j < S-1} 256 * 512^j as the BF16-exact float
 // x_q * 2^(-9 (q - 1)).  Adding that constant turns the balanced digits of V
 // into plain 9-bit fields of w: x = field - 256 for the S - 1 low digits, and
 // the top digit x_1 is w >> 9 (S - 1).  Both are built from their bits: the
 // field is or-ed into the mantissa of 2^23 and one exact FMA removes 2^23 + 256
 // and applies the digit's power-of-two scale.
-template <int S, int Q>
-__device__ __forceinline__ float digit_value(int64_t w) {
+template <int S, int Q, typename W>
+__device__ __forceinline__ float digit_value(W w) {
     if constexpr (Q == 0) {
         const int x = static_cast<int>(w >> (DIGIT_BITS * (S - 1)));  // |x| <= 256
         return __int_as_float(0x4B400000 + x) - 12582912.0f;         // 1.5 * 2^23
@@ -214,8 +235,8 @@ __device__ __forceinline__ float digit_value(int64_t w) {
     }
 }
 
-template <int S, int Q>
-__device__ __forceinline__ void store_digit_row(const int64_t (&w)[KSTEP], uint8_t *img_row, int swz) {
+template <int S, int Q, typename W>
+__device__ __forceinline__ void store_digit_row(const W (&w)[KSTEP], uint8_t *img_row, int swz) {
     uint32_t pk[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -227,12 +248,12 @@ __device__ __forceinline__ void store_digit_row(const int64_t (&w)[KSTEP], uint8
     *reinterpret_cast<uint4 *>(img_row + ((swz ^ 1) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
 
-template <int S, int Q = 0>
-__device__ __forceinline__ void store_digits(const int64_t (&w)[KSTEP], uint8_t *row0, int64_t plane_step,
+template <int S, int Q = 0, typename W>
+__device__ __forceinline__ void store_digits(const W (&w)[KSTEP], uint8_t *row0, int64_t plane_step,
                                              int swz) {
     if constexpr (Q < S) {
-        store_digit_row<S, Q>(w, row0 + Q * plane_step, swz);
-        store_digits<S, Q + 1>(w, row0, plane_step, swz);
+        store_digit_row<S, Q, W>(w, row0 + Q * plane_step, swz);
+        store_digits<S, Q + 1, W>(w, row0, plane_step, swz);
     }
 }
 
@@ -265,8 +286,13 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                                            const OpDesc &od, const OpTerm *terms, int k0, int c0, int cc,
                                            int64_t *sv, int ld) {
     constexpr int F = F8 ? FP8_FIX : DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
-    auto fixed = [](T a, int sh) -> int64_t {
-        if constexpr (FastFixed<F, T>::ok)
+    // FP32 input with up to 3 digits: every value and sum fits 32 bits.
+    constexpr bool NARROW = sizeof(T) == 4 && !F8 && F <= 29;
+    using V = typename std::conditional<NARROW, int32_t, int64_t>::type;
+    auto fixed = [](T a, int sh) -> V {
+        if constexpr (NARROW)
+            return fixed32_of_fast<F>(static_cast<float>(a), sh);
+        else if constexpr (FastFixed<F, T>::ok)
             return fixed_of_fast<F>(a, sh);
         else
             return fixed_of(a, sh);
@@ -295,10 +321,10 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                 for (int j = 0; j < G; ++j) raw[t][j] = (g + j) < lim[t] ? base[t][(g + j) * lda] : T(0);
 #pragma unroll
             for (int j = 0; j < G; ++j) {
-                int64_t v = 0;
+                V v = 0;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    const int64_t x = fixed(raw[t][j], sh[t]);
+                    const V x = fixed(raw[t][j], sh[t]);
                     v += neg[t] ? -x : x;
                 }
                 sv[(g + j) * ld] = v;
@@ -307,7 +333,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
     } else {
 #pragma unroll 1
         for (int g = 0; g < PREP_TK; g += 4) {
-            int64_t v[4] = {0, 0, 0, 0};
+            V v[4] = {0, 0, 0, 0};
             for (int t = 0; t < od.nterms; ++t) {
                 const OpTerm tm = terms[od.first_term + t];
                 const bool cvalid = c < tm.cols;
@@ -321,7 +347,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
                 const int sh = cvalid ? F - od.t_shift - expo[tm.col0 + c] : 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int64_t x = fixed(raw[j], sh);
+                    const V x = fixed(raw[j], sh);
                     v[j] += tm.coef > 0 ? x : -x;
                 }
             }
@@ -400,9 +426,11 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
             for (int j = 0; j < S - 1; ++j) v += int64_t(256) << (DIGIT_BITS * j);
             return v;
         }();
-        int64_t w[KSTEP];
+        // up to 3 digits the shifted value fits 32 bits (|V| <= 2^26 + CADD)
+        using W = typename std::conditional<(S <= 3), int32_t, int64_t>::type;
+        W w[KSTEP];
 #pragma unroll
-        for (int i = 0; i < KSTEP; ++i) w[i] = sv[i * ld] + CADD;
+        for (int i = 0; i < KSTEP; ++i) w[i] = static_cast<W>(sv[i * ld]) + static_cast<W>(CADD);
         const int64_t kstep = k0 / KSTEP + rg;
         const int64_t cblk = (od.out_col + c0 + cc) / BLOCK_COLS;
         uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
@@ -430,7 +458,7 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     const OpTerm *tt = cached ? s_terms : terms;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
-        const OpDesc od = o[op_of_tile(o, nops, tile, &local)];
+        const OpDesc &od = o[op_of_tile(o, nops, tile, &local)];  // read where used (register budget)
         // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
         prep_tile<S, T, F8>(A, lda, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV, F8 ? 7 : 8);
     }
