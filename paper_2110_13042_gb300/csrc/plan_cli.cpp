@@ -57,6 +57,48 @@ int main(int argc, char **argv) {
         for (int r = 0; r < d.rows; ++r)
             for (int c = 0; c < d.cols; ++c) cov[(r0 + r) * n + c0 + c]++;
     }
+    // Prep tiles: walk the flat tile range the way the prep kernels map it
+    // (last operand with tile_base <= tile, then the interleaved group) and
+    // check that every tile of every operand is produced exactly once.
+    bool prep_ok = true;
+    int64_t groups = 0;
+    {
+        const bool digits = pp.mode != MODE_F64, fp8 = pp.mode == MODE_F32_FP8;
+        std::vector<std::vector<uint8_t>> seen(P.ops.size());
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            seen[i].assign(static_cast<size_t>(prep_tiles_for(digits, P.ops[i].K_pitch, P.ops[i].P_pad, fp8)), 0);
+            if (P.ops[i].ilv_i == 0) groups++;
+            if (P.ops[i].ilv_n < 1 || P.ops[i].ilv_i >= P.ops[i].ilv_n) prep_ok = false;
+            if (P.ops[i].ilv_i > 0 && (P.ops[i].tile_base != P.ops[i - 1].tile_base ||
+                                       P.ops[i].K_pitch != P.ops[i - 1].K_pitch ||
+                                       P.ops[i].P_pad != P.ops[i - 1].P_pad ||
+                                       P.ops[i].family != P.ops[i - 1].family))
+                prep_ok = false;
+        }
+        for (int64_t tile = 0; tile < P.prep_tiles && prep_ok; ++tile) {
+            size_t i = 0;
+            for (size_t j = 0; j < P.ops.size(); ++j)
+                if (P.ops[j].tile_base <= tile) i = j;
+            const int64_t g = tile - P.ops[i].tile_base;
+            const int64_t nn = P.ops[i].ilv_n;
+            const size_t op = nn > 1 ? i - P.ops[i].ilv_i + static_cast<size_t>(g % nn) : i;
+            const int64_t local = nn > 1 ? g / nn : g;
+            if (local < 0 || local >= static_cast<int64_t>(seen[op].size()) || seen[op][local]++) prep_ok = false;
+        }
+        for (const auto &v : seen)
+            for (uint8_t x : v)
+                if (x != 1) prep_ok = false;
+    }
+    // Combine tiles: COMB_ROWS x COMB_COLS per block, prefix tile_base.
+    bool comb_ok = true;
+    {
+        int64_t expect = 0;
+        for (const CombDesc &d : P.combs) {
+            if (d.tile_base != expect) comb_ok = false;
+            expect += ((d.rows + COMB_ROWS - 1) / COMB_ROWS) * ((d.cols + COMB_COLS - 1) / COMB_COLS);
+        }
+        if (expect != P.comb_tiles) comb_ok = false;
+    }
     int64_t covered = 0, overlap = 0;
     for (int64_t j = 0; j < n; ++j)
         for (int64_t k = 0; k < n; ++k) {
@@ -67,10 +109,11 @@ int main(int argc, char **argv) {
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
                 "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "
-                "cta_steps_sum=%lld\n",
+                "cta_steps_sum=%lld prep_tiles=%lld prep_groups=%lld prep_map_ok=%d comb_map_ok=%d\n",
                 P.cutoff, P.depth, P.slices, (long long)P.n_panels, (long long)P.n_blocks,
                 (long long)P.n_products, (size_t)P.n_tiles, (long long)covered, (long long)overlap,
                 P.cterms.size(), P.ops.size(), P.families.size(), (long long)P.workspace_bytes, s_leaf,
-                s_plain, (long long)P.n_reused, (long long)cta_max, (long long)cta_sum);
+                s_plain, (long long)P.n_reused, (long long)cta_max, (long long)cta_sum, (long long)P.prep_tiles,
+                (long long)groups, prep_ok ? 1 : 0, comb_ok ? 1 : 0);
     return 0;
 }

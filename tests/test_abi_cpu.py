@@ -212,3 +212,17 @@ def test_fp8_plan(plan_cli, m, n, depth):
     assert r8["reused"] <= rb["reused"]
     if (m + 1) // 2 % 32 == 16:
         assert r8["reused"] < rb["reused"]
+
+
+@pytest.mark.parametrize("mode", [1, 2, 0, 5])
+@pytest.mark.parametrize("m,n,depth", [(1000, 1024, 1), (531, 777, 2), (4099, 2048, 2), (300, 900, 3)])
+def test_prep_and_combine_tile_maps(plan_cli, mode, m, n, depth):
+    """Operands of one family and shape share an interleaved tile range: the
+    flat range, mapped the way the prep kernels map it, produces every tile
+    of every operand exactly once; combine tiles (64 x 32) have consistent
+    prefix bases."""
+    r = plan_cli(m, n, mode, max(1, n // 4), depth)
+    assert r["prep_map_ok"] == 1 and r["comb_map_ok"] == 1
+    assert r["prep_groups"] <= r["ops"]
+    if r["products"] > 0:
+        assert r["prep_groups"] < r["ops"]  # Strassen operand sums were grouped
