@@ -149,30 +149,6 @@ __device__ __forceinline__ void issue_pairs(uint32_t d_tmem, uint64_t da0, uint6
     }
 }
 
-// Steady-state step (no accumulator pending or fresh): every pair
-// accumulates, and pairs (p, q), (p, q + 1) whose accumulators are adjacent
-// in TMEM share one N = 192 MMA (their B digit slices are adjacent in shared
-// memory): 15 instructions instead of 21 for S = 6.
-template <int S, int P = 1, int Q = 1>
-__device__ __forceinline__ void issue_fast(uint32_t tmem, uint64_t da0, uint64_t db0) {
-    if constexpr (P <= S) {
-        if constexpr (P + Q <= S + 1) {
-            constexpr int ACC = acc_of(P, Q);
-            const uint64_t da = da0 + static_cast<uint64_t>((P - 1) * (A_SLICE_BYTES >> 4));
-            const uint64_t db = db0 + static_cast<uint64_t>((Q - 1) * (B_SLICE_BYTES >> 4));
-            if constexpr (ACC < MAX_ACC - 1 && P + Q + 1 <= S + 1) {
-                umma_f16(tmem + ACC * TILE_N, da, db, IDESC2, 1u);
-                issue_fast<S, P, Q + 2>(tmem, da0, db0);
-            } else {
-                umma_f16(tmem + ACC * TILE_N, da, db, IDESC, 1u);
-                issue_fast<S, P, Q + 1>(tmem, da0, db0);
-            }
-        } else {
-            issue_fast<S, P + 1, 1>(tmem, da0, db0);
-        }
-    }
-}
-
 // Accumulators 2 and 3 are the ones drained every 64 rows.
 __host__ __device__ constexpr bool in_b(int acc) { return acc == 2 || acc == 3; }
 
@@ -378,8 +354,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     // of the accumulator being drained while the others keep the tensor core
     // fed, and the per-step bookkeeping is split between them.  Measured at
     // 8192^2, S = 6: one issuer 9.81 ms, two 8.87-8.98, three 8.19.
-    constexpr bool DUAL = S >= 5;
-    constexpr int NI = DUAL ? 3 : 1;
+    constexpr bool MULTI = S >= 5;
+    constexpr int NI = MULTI ? 3 : 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     Shared *sh = reinterpret_cast<Shared *>(smem + C::STAGES * C::STAGE_BYTES);
@@ -456,7 +432,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             }
             if (!ok) spin_ns(2000000);  // let copies already in flight land
         }
-    } else if (DUAL && warp >= 1 && warp <= NI) {
+    } else if (MULTI && warp >= 1 && warp <= NI) {
         // ------------------------------------- NI MMA issuers (5+ digits) --
         if (lane == 0) {
             const int g = warp - 1;
@@ -509,126 +485,112 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             }
             if (!ok) spin_ns(2000000);  // let MMAs already issued retire
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------- MMA issuer --
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            constexpr bool GROUPED = S <= 4;
-            // grouped path: every accumulator starts out with the epilogue,
-            // which zeroes it; fast/slow path: every accumulator fresh
-            IssueState st{0u, GROUPED ? (1u << C::NACC) - 1u : 0u, GROUPED ? 0u : 0x1Fu};
-            bool ok = true;
-            bool ready = false;  // the current stage's full barrier was already seen complete
-            const uint32_t smem_base = smem_u32(smem);
-            for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
-                const int nsteps = (p.tasks[ti].klen + KS - 1) / KS;
-                for (int s0 = 0; s0 < nsteps; s0 += C::KPS) {
-                    const int cnt = nsteps - s0 < C::KPS ? nsteps - s0 : C::KPS;
-                    if (!ready && !mbar_wait(&sh->full[stage], phase, abort_flag, p.status)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    // Up to 3 digits, probe the next stage now (the test's
-                    // latency hides behind this stage's MMA issue); with one
-                    // step per stage (4+ digits) it measured 1% slower at 6.
-                    if constexpr (S <= 3) {
-                        const int nstage = stage + 1 == C::STAGES ? 0 : stage + 1;
-                        const uint32_t nphase = nstage == 0 ? phase ^ 1u : phase;
-                        ready = mbar_test_wait(&sh->full[nstage], nphase);
-                    }
-                    if constexpr (S <= 3) {
-                        static_assert((4 * CHUNK_STEPS) % C::KPS == 0, "every 16-step drain point ends a stage");
-                        // At most 3 digits: every accumulator is drained every
-                        // 16 steps, at the end of a stage, so the drain waits
-                        // come before the stage's first step and the due check
-                        // after its last; the stage's MMAs go out back to back
-                        // from descriptors built once.  (Per-step bookkeeping
-                        // in the issuing thread measured ~275 cycles against a
-                        // 56-cycle MMA; the pipe idles meanwhile.)
-                        const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
-                        const uint64_t da0 = sdesc_kmajor_sw32(a_base);
-                        const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
+    } else if (!MULTI && warp == 1) {
+        // ------------------------------------- one MMA issuer (1-4 digits) --
+        if constexpr (!MULTI) {
+            if (lane == 0) {
+                int stage = 0;
+                uint32_t phase = 0;
+                // every accumulator starts out with the epilogue, which zeroes it
+                // (grouped issue path, see issue_group)
+                IssueState st{0u, (1u << C::NACC) - 1u, 0u};
+                bool ok = true;
+                bool ready = false;  // the current stage's full barrier was already seen complete
+                const uint32_t smem_base = smem_u32(smem);
+                for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
+                    const int nsteps = (p.tasks[ti].klen + KS - 1) / KS;
+                    for (int s0 = 0; s0 < nsteps; s0 += C::KPS) {
+                        const int cnt = nsteps - s0 < C::KPS ? nsteps - s0 : C::KPS;
+                        if (!ready && !mbar_wait(&sh->full[stage], phase, abort_flag, p.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        // Up to 3 digits, probe the next stage now (the test's
+                        // latency hides behind this stage's MMA issue); with one
+                        // step per stage (4+ digits) it measured 1% slower at 6.
+                        if constexpr (S <= 3) {
+                            const int nstage = stage + 1 == C::STAGES ? 0 : stage + 1;
+                            const uint32_t nphase = nstage == 0 ? phase ^ 1u : phase;
+                            ready = mbar_test_wait(&sh->full[nstage], nphase);
+                        }
+                        if constexpr (S <= 3) {
+                            static_assert((4 * CHUNK_STEPS) % C::KPS == 0, "every 16-step drain point ends a stage");
+                            // At most 3 digits: every accumulator is drained every
+                            // 16 steps, at the end of a stage, so the drain waits
+                            // come before the stage's first step and the due check
+                            // after its last; the stage's MMAs go out back to back
+                            // from descriptors built once.  (Per-step bookkeeping
+                            // in the issuing thread measured ~275 cycles against a
+                            // 56-cycle MMA; the pipe idles meanwhile.)
+                            const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
+                            const uint64_t da0 = sdesc_kmajor_sw32(a_base);
+                            const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < C::KPS; ++kk) {
-                            if (kk < cnt) {
-                                const uint64_t off = static_cast<uint64_t>(kk * (C::STEP_BYTES >> 4));
-                                if (kk == 0 && (st.pending & ~0x0Cu)) {
+                            for (int kk = 0; kk < C::KPS; ++kk) {
+                                if (kk < cnt) {
+                                    const uint64_t off = static_cast<uint64_t>(kk * (C::STEP_BYTES >> 4));
+                                    if (kk == 0 && (st.pending & ~0x0Cu)) {
+                                        ok = wait_drained<C::NACC>(st, ~0x0Cu, sh, abort_flag, p.status);
+                                        if (!ok) break;
+                                    }
+                                    if constexpr (F8)
+                                        umma_f8(tmem, da0 + off, db0 + off, IDESC8, 1u);
+                                    else
+                                        issue_group<S, false>(tmem, da0 + off, db0 + off);
+                                    if (kk == 0 && (st.pending & 0x0Cu)) {
+                                        ok = wait_drained<C::NACC>(st, 0x0Cu, sh, abort_flag, p.status);
+                                        if (!ok) break;
+                                    }
+                                    issue_group<S, true>(tmem, da0 + off, db0 + off);
+                                }
+                            }
+                            if (!ok) break;
+                            const int end = s0 + cnt;  // drains fall on 16-step boundaries and task ends
+                            const uint32_t due =
+                                (end % (4 * CHUNK_STEPS) == 0 || end >= nsteps)
+                                    ? due_mask((end - 1) / CHUNK_STEPS, end >= nsteps, C::NACC)
+                                    : 0u;
+                            if (due) {  // hand the accumulators to the epilogue
+                                umma_commit(&sh->accf[0]);
+                                st.pending |= due;
+                            }
+                        } else {
+                            for (int kk = 0; kk < cnt; ++kk) {
+                                const int step = s0 + kk;
+                                const uint32_t a_base = smem_base + stage * C::STAGE_BYTES + kk * C::STEP_BYTES;
+                                const uint64_t da0 = sdesc_kmajor_sw32(a_base);
+                                const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
+                                if (st.pending & ~0x0Cu) {
                                     ok = wait_drained<C::NACC>(st, ~0x0Cu, sh, abort_flag, p.status);
                                     if (!ok) break;
                                 }
-                                if constexpr (F8)
-                                    umma_f8(tmem, da0 + off, db0 + off, IDESC8, 1u);
-                                else
-                                    issue_group<S, false>(tmem, da0 + off, db0 + off);
-                                if (kk == 0 && (st.pending & 0x0Cu)) {
+                                issue_group<S, false>(tmem, da0, db0);
+                                if (st.pending & 0x0Cu) {
                                     ok = wait_drained<C::NACC>(st, 0x0Cu, sh, abort_flag, p.status);
                                     if (!ok) break;
                                 }
-                                issue_group<S, true>(tmem, da0 + off, db0 + off);
+                                issue_group<S, true>(tmem, da0, db0);
+                                const bool last = step == nsteps - 1;
+                                const uint32_t due = (last || (step % CHUNK_STEPS) == CHUNK_STEPS - 1)
+                                                         ? due_mask(step / CHUNK_STEPS, last, C::NACC)
+                                                         : 0u;
+                                if (due) {  // hand the due accumulators to the epilogue
+                                    umma_commit(&sh->accf[0]);
+                                    st.pending |= due;
+                                }
                             }
                         }
                         if (!ok) break;
-                        const int end = s0 + cnt;  // drains fall on 16-step boundaries and task ends
-                        const uint32_t due =
-                            (end % (4 * CHUNK_STEPS) == 0 || end >= nsteps)
-                                ? due_mask((end - 1) / CHUNK_STEPS, end >= nsteps, C::NACC)
-                                : 0u;
-                        if (due) {  // hand the accumulators to the epilogue
-                            umma_commit(&sh->accf[0]);
-                            st.pending |= due;
+                        umma_commit(&sh->empty[stage]);
+                        if (++stage == C::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
                         }
-                    } else {
-                    for (int kk = 0; kk < cnt; ++kk) {
-                        const int step = s0 + kk;
-                        const uint32_t a_base = smem_base + stage * C::STAGE_BYTES + kk * C::STEP_BYTES;
-                        const uint64_t da0 = sdesc_kmajor_sw32(a_base);
-                        const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
-                        if constexpr (GROUPED) {
-                            if (st.pending & ~0x0Cu) {
-                                ok = wait_drained<C::NACC>(st, ~0x0Cu, sh, abort_flag, p.status);
-                                if (!ok) break;
-                            }
-                            if constexpr (F8)
-                                umma_f8(tmem, da0, db0, IDESC8, 1u);
-                            else
-                                issue_group<S, false>(tmem, da0, db0);
-                            if (st.pending & 0x0Cu) {
-                                ok = wait_drained<C::NACC>(st, 0x0Cu, sh, abort_flag, p.status);
-                                if (!ok) break;
-                            }
-                            issue_group<S, true>(tmem, da0, db0);
-                        } else if ((st.pending | st.fresh) == 0u) {
-                            issue_fast<S>(tmem, da0, db0);
-                        } else {
-                            ok = step_acc<S, 4>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                                 step_acc<S, 0>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                                 step_acc<S, 1>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                                 step_acc<S, 2>(st, sh, tmem, da0, db0, abort_flag, p.status) &&
-                                 step_acc<S, 3>(st, sh, tmem, da0, db0, abort_flag, p.status);
-                            if (!ok) break;
-                        }
-                        const bool last = step == nsteps - 1;
-                        const uint32_t due = (last || (step % CHUNK_STEPS) == CHUNK_STEPS - 1)
-                                                 ? due_mask(step / CHUNK_STEPS, last, C::NACC)
-                                                 : 0u;
-                        if (due) {  // hand the due accumulators to the epilogue
-                            umma_commit(&sh->accf[0]);
-                            st.pending |= due;
-                            if constexpr (!GROUPED) st.fresh |= due;
-                        }
-                    }
-                    }
-                    if (!ok) break;
-                    umma_commit(&sh->empty[stage]);
-                    if (++stage == C::STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
                     }
                 }
+                if (!ok) spin_ns(2000000);  // let MMAs already issued retire
             }
-            if (!ok) spin_ns(2000000);  // let MMAs already issued retire
         }
     } else if (warp >= EPI_WARP0) {
         // --------------------------------------------------- epilogue --
@@ -665,7 +627,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 const bool last = c == nchunks - 1;
                 const uint32_t due = due_mask(c, last, C::NACC);
                 if (!due) continue;
-                if constexpr (DUAL) {
+                if constexpr (MULTI) {
                     // issuer by issuer, each issuer's accumulators in the order 4, 0, 1, 2, 3
                     bool good = true;
 #pragma unroll
