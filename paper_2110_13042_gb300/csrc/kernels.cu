@@ -468,8 +468,13 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
 // block walks its tiles in increasing order and keeps a cursor on the
 // problem table (prefix prep_base), so locating a tile's problem costs one
 // binary search per block.
+// Five resident blocks per SM (48 registers) for FP32 inputs with up to 3
+// digits, whose 32-bit arithmetic fits; four otherwise.
+template <typename T, int S>
+constexpr int batched_prep_blocks() { return (sizeof(T) == 4 && S <= 3) ? 5 : 4; }
+
 template <int S, typename T>
-__global__ void __launch_bounds__(256, 4) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
+__global__ void __launch_bounds__(256, batched_prep_blocks<T, S>()) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
                                                               const int *__restrict__ expo, int64_t ntiles,
                                                               uint8_t *planes) {
     __shared__ int64_t sV[PREP_SV];
@@ -538,7 +543,7 @@ __global__ void __launch_bounds__(256) batched_expo_kernel(const BatchProb *__re
 }
 
 // Persistent grid: four 256-thread blocks per SM (64 registers each).
-static unsigned prep_grid(int64_t ntiles) {
+static unsigned prep_grid(int64_t ntiles, int per_sm = 4) {
     static int sms[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
@@ -547,7 +552,7 @@ static unsigned prep_grid(int64_t ntiles) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         sms[dev] = n > 0 ? n : 1;
     }
-    const int64_t cap = 4 * static_cast<int64_t>(sms[dev]);
+    const int64_t cap = per_sm * static_cast<int64_t>(sms[dev]);
     return static_cast<unsigned>(ntiles < cap ? ntiles : cap);
 }
 
@@ -800,13 +805,14 @@ cudaError_t launch_batched_expo(const BatchPlan &B, const BatchProb *probs, bool
 cudaError_t launch_batched_prep(const BatchPlan &B, const BatchProb *probs, bool is_f32, const int *expo,
                                 uint8_t *planes, cudaStream_t s) {
     if (B.prep_tiles == 0) return cudaSuccess;
-    const unsigned g = prep_grid(B.prep_tiles);
 #define ATA_PREP_B(SS)                                                                                        \
     case SS:                                                                                                  \
         if (is_f32)                                                                                           \
-            batched_prep_kernel<SS, float><<<g, 256, 0, s>>>(probs, B.count, expo, B.prep_tiles, planes);    \
+            batched_prep_kernel<SS, float><<<prep_grid(B.prep_tiles, batched_prep_blocks<float, SS>()), 256, 0, \
+                                            s>>>(probs, B.count, expo, B.prep_tiles, planes);                 \
         else                                                                                                  \
-            batched_prep_kernel<SS, double><<<g, 256, 0, s>>>(probs, B.count, expo, B.prep_tiles, planes);   \
+            batched_prep_kernel<SS, double><<<prep_grid(B.prep_tiles, batched_prep_blocks<double, SS>()), 256, \
+                                             0, s>>>(probs, B.count, expo, B.prep_tiles, planes);             \
         break;
     switch (B.slices) {
         ATA_PREP_B(1)
