@@ -226,3 +226,37 @@ def test_prep_and_combine_tile_maps(plan_cli, mode, m, n, depth):
     assert r["prep_groups"] <= r["ops"]
     if r["products"] > 0:
         assert r["prep_groups"] < r["ops"]  # Strassen operand sums were grouped
+
+
+@pytest.fixture(scope="session")
+def plan_cli_sanitized(lib, tmp_path_factory):
+    """The planner inspector built with AddressSanitizer and UBSan (skipped
+    where the compiler has no sanitizer runtime)."""
+    src = os.path.join(ROOT, "paper_2110_13042_gb300", "csrc", "plan_cli.cpp")
+    plan_cpp = os.path.join(ROOT, "paper_2110_13042_gb300", "csrc", "plan.cpp")
+    out = str(tmp_path_factory.mktemp("san") / "plan_cli_san")
+    r = subprocess.run(["g++", "-O1", "-g", "-std=c++17", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+                        "-I", os.path.dirname(src), src, plan_cpp, "-o", out], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("no sanitizer runtime: " + r.stderr[:200])
+    return out
+
+
+SAN_SHAPES = [(1, 1), (1, 77), (129, 1), (2, 2), (37, 129), (300, 257), (531, 600), (97, 513), (600, 96)]
+
+
+@pytest.mark.parametrize("m,n", SAN_SHAPES)
+def test_planner_under_sanitizers(plan_cli_sanitized, m, n):
+    """Every mode, Strassen depth and cutoff style on odd and degenerate
+    shapes: no out-of-bounds access or undefined behaviour in the planner,
+    every lower entry produced once, and consistent prep and combine tile
+    maps."""
+    for mode in (0, 1, 2, 5):  # (the one-digit BF16 mode plans like FP32)
+        for depth in (0, 1, 3):
+            for cutoff, smin in ((0, 4096), (max(1, n // 4), 2), (16, 1)):
+                r = subprocess.run([plan_cli_sanitized, str(m), str(n), str(mode), str(cutoff), str(depth), "0",
+                                    str(smin), "1", "152"], capture_output=True, text=True)
+                assert r.returncode == 0, (mode, depth, cutoff, r.stderr[:500])
+                kv = dict(x.split("=") for x in r.stdout.split())
+                assert kv["overlap"] == "0" and kv["prep_map_ok"] == "1" and kv["comb_map_ok"] == "1"
+                assert int(kv["covered"]) == n * (n + 1) // 2
