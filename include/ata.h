@@ -18,14 +18,16 @@
  *
  * All matrices are ROW-MAJOR.  A is m x n with leading dimension lda >= n
  * (element (i, j) at A[i*lda + j]).  C is n x n with leading dimension
- * ldc >= n.  All pointers passed to ata_lower / ata_batched are DEVICE
- * pointers on the current CUDA device; the caller owns them.  A is read only
+ * ldc >= n.  All pointers passed to ata_lower / ata_syrk / ata_batched are
+ * DEVICE pointers on the current CUDA device; the caller owns them.  A is read only
  * and must not overlap C.  `stream` is a cudaStream_t (NULL = legacy default
  * stream); every call is asynchronous on it.
  *
- * Semantics: low(C) <- low(A^T A) (overwrite; alpha = 1, beta = 0).  Entries
- * (j, k) with k <= j are written; the strict upper triangle of C is never
- * read or written.  m == 0 writes zeros to low(C); n == 0 does nothing.
+ * Semantics: ata_lower overwrites, low(C) <- low(A^T A); ata_syrk takes the
+ * BLAS scalars, low(C) <- alpha low(A^T A) + beta low(C).  Entries (j, k)
+ * with k <= j are written; the strict upper triangle of C is never read or
+ * written.  m == 0 writes zeros to low(C) (ata_syrk: scales it by beta);
+ * n == 0 does nothing.
  *
  * Errors: every entry point returns an ata_status.  No exception crosses the
  * ABI and no call aborts the process.  A device-side wait that exceeds its
