@@ -177,6 +177,23 @@ const char *ata_last_error(ata_handle h);
 #define ATA_PLAN_FIELDS 10
 int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out);
 
+/* Host-only description of the off-diagonal blocks of the plan ata_lower
+ * would run for (m, n, dtype) under the handle's configuration (the AtA
+ * recursion of Section 3.1 / Algorithm 1: block C21 = A12^T A11 + A22^T A21 of
+ * every split).  Writes up to max_blocks records of ATA_BLOCK_FIELDS int64
+ * into `out` (host array):
+ *   [0] r0  first row of the block in C (= first column of A12 / A22)
+ *   [1] p   its rows
+ *   [2] c0  first column of the block in C (= first column of A11 / A21)
+ *   [3] q   its columns
+ *   [4] Strassen levels applied to it (0: classical tiles)
+ * in recursion order, and the total block count to *count (host).  Touches
+ * no GPU; h may be NULL (default configuration).  Errors: ATA_ERR_INVALID
+ * for bad sizes or a NULL count, ATA_ERR_DTYPE for an unknown dtype. */
+#define ATA_BLOCK_FIELDS 5
+int ata_plan_blocks(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out, int64_t max_blocks,
+                    int64_t *count);
+
 /* Phase timing.  When enabled, ata_lower records CUDA events on its stream
  * around each phase; ata_phase_times waits for the most recent call's events
  * and writes 4 durations in milliseconds: [0] column exponents, [1] operand

@@ -28,13 +28,32 @@ Functions:
                            returns D8 = low(|Q|^T|Q|) scaled the same way.
 * ``fp8_error_bound(A)``   componentwise bound on |C_fp8 - C_exact| at
                            Strassen depth 0 (derivation in the docstring).
+* ``fp8_strassen_atb(X, Y, depth)``  the FP8 mode's Strassen product X^T Y of two
+                           equilibrated panels: ``depth`` levels of Strassen's
+                           algorithm (Section 3.1, Section 3.3 splits), every
+                           leaf operand an exact sum of blocks rounded once to
+                           E4M3; returns the product and the matching |Q|^T|Q|
+                           magnitude sum (for the FP32-accumulation tolerance).
+* ``fp8_ata_lower_blocks(A, blocks)``  low C of the FP8 mode for a given AtA
+                           block layout: depth-0 entries everywhere, Strassen
+                           on each listed off-diagonal block.
+* ``fp8_strassen_bound(A, depth)``  scalar normwise bound at Strassen depth > 0.
+
+With Strassen the operands are signed sums of blocks of the equilibrated
+matrix Ahat = A diag(2^-e).  An operand of t' nonempty terms is scaled by
+2^(8 - t), t = ceil(log2 t'), so it stays below 2^8 in magnitude; each term is
+first rounded to FP8_FIX = 47 fraction bits of that scale (half away from
+zero; exact for every FP32 entry at or above 2^-21 of its column scale), the
+terms are summed exactly, and the sum is rounded once to E4M3.  Leaf products
+Q_u^T Q_v are exact in FP64 as above; the Strassen result sums are FP64 sums.
 """
 from __future__ import annotations
 
 import numpy as np
 
 __all__ = ["E4M3_MAX", "U8", "e4m3_round", "e4m3_decode", "column_exponents", "fp8_quantize",
-           "fp8_ata_lower", "fp8_error_bound", "fp8_strassen_bound"]
+           "fp8_ata_lower", "fp8_error_bound", "fp8_strassen_atb", "fp8_ata_lower_blocks",
+           "fp8_strassen_bound"]
 
 E4M3_MAX = 448.0
 U8 = 2.0 ** -4          # unit roundoff of a 4-significant-bit format
@@ -123,27 +142,172 @@ def fp8_error_bound(A, accum_terms=None):
     return np.tril(rnd + accum_terms * 2.0 ** -24 * QQ)
 
 
+def _row_regions(m, depth):
+    """The contraction-row regions after ``depth`` ceil-first halvings
+    (Section 3.3 rounds up; a second half past the end is zero padding)."""
+    regs, N = [(0, m)], m
+    for _ in range(depth):
+        Nc = (N + 1) // 2
+        regs = [x for off, ext in regs for x in ((off, min(Nc, ext)), (off + Nc, max(0, ext - Nc)))]
+        N = Nc
+    return regs, N
+
+
 def fp8_strassen_bound(A, depth):
     """Normwise bound on max |C_fp8 - A^T A| / 2^(e_j + e_k) with Strassen on
-    the off-diagonal blocks to the given depth (any split points).
+    the off-diagonal blocks to the given depth (any column split points; the
+    contraction rows split ceil-first).
 
     In the scaled matrix Ahat = A diag(2^-e) every output entry is a sum of
     products M_r = U_r^T V_r whose operands are exact sums of blocks of Ahat,
-    each rounded once to E4M3 in units 2^-t (t <= depth) of the sum; the pairs
-    (block of U_r, block of V_r) over all products that reach one output
-    block number 12 per level (M1 + M4 - M5 + M7 and M1 - M2 + M3 + M6: 4 + 2
-    + 2 + 4 pairs), so at most 12^depth.  Each pair contributes at most
-    (2u + u^2) max_p Dhat_pp (Cauchy-Schwarz on |X|^T|Y|) plus the subnormal
-    terms 2 (1 + u) 2^(t - 18) max_p Shat_p + m 2^(2t - 36), and the FP32
-    accumulation as in fp8_error_bound.  Returns that scalar bound."""
+    each rounded once to E4M3 in units 2^-t (t <= depth) of the sum, so
+    |Qhat_r - U_r| <= u |U_r| + 2^(t - 18) elementwise and
+      |Qu^T Qv - U^T V| <= (2u + u^2) |U|^T |V| + (1 + u) 2^(t - 18) (|U|^T 1 + 1^T |V|)
+                           + R 2^(2t - 36)
+    over the R = ceil^depth(m) rows of one leaf.  |U|^T|V| is at most the sum
+    over the (block of U_r, block of V_r) pairs, and the pairs over all
+    products that reach one output block number 12 per level (M1 + M4 - M5 + M7
+    and M1 - M2 + M3 + M6: 4 + 2 + 2 + 4), so at most 12^depth.  Every block
+    of a pair lies in one contraction-row region of the depth's row split, so
+    by Cauchy-Schwarz a pair is at most dmax = the largest sum over one region
+    of Ahat_ij^2 for one column (and a row sum of |U| at most smax, the
+    largest such sum of |Ahat_ij|).  The FP32 accumulation adds
+    (512 + R / 512 + 2 + 8 (depth + 1)) 2^-24 of the rounded magnitudes.
+    Returns that scalar bound."""
     A = np.asarray(A, np.float64)
     m = A.shape[0]
+    if A.size == 0:
+        return 0.0
     e = column_exponents(A)
     Ah = np.abs(A) * np.ldexp(1.0, -e)[None, :]
-    dmax = float(np.max(np.sum(Ah * Ah, axis=0))) if A.size else 0.0
-    smax = float(np.max(np.sum(Ah, axis=0))) if A.size else 0.0
+    regs, R = _row_regions(m, depth)
+    dmax = max(float(np.max(np.sum(Ah[o:o + x] ** 2, axis=0))) for o, x in regs if x > 0)
+    smax = max(float(np.max(np.sum(Ah[o:o + x], axis=0))) for o, x in regs if x > 0)
     u, t = U8, depth
     pairs = 12.0 ** depth
-    per_pair = (2 * u + u * u) * dmax + 2 * (1 + u) * 2.0 ** (t - 18) * smax + m * 2.0 ** (2 * t - 36)
-    accum = (512 + m / 512.0 + 2 + 8 * (depth + 1)) * 2.0 ** -24 * ((1 + u) ** 2 * dmax + per_pair)
+    per_pair = (2 * u + u * u) * dmax + 2 * (1 + u) * 2.0 ** (t - 18) * smax + R * 2.0 ** (2 * t - 36)
+    accum = (512 + R / 512.0 + 2 + 8 * (depth + 1)) * 2.0 ** -24 * ((1 + u) ** 2 * dmax + per_pair)
     return pairs * (per_pair + accum)
+
+
+# ------------------------------------------------------------ Strassen --
+FP8_FIX = 47      # fraction bits of an operand sum before its E4M3 rounding
+
+# Strassen's algorithm (Strassen 1969, the form the paper uses in Section 3.1)
+# written for C = X^T Y.  X_ab is the block of contraction half a and column
+# half b (0 = first); products M1..M7 and result sums
+#   M1 = (X11 + X22)^T (Y11 + Y22)     M5 = (X11 + X21)^T Y22
+#   M2 = (X12 + X22)^T Y11             M6 = (X12 - X11)^T (Y11 + Y12)
+#   M3 = X11^T (Y12 - Y22)             M7 = (X21 - X22)^T (Y21 + Y22)
+#   M4 = X22^T (Y21 - Y11)
+#   C11 = M1 + M4 - M5 + M7   C12 = M3 + M5   C21 = M2 + M4   C22 = M1 - M2 + M3 + M6
+# Each operand is a tuple of (coef, a, b); each result a tuple of (coef, product).
+_M = (
+    (((1, 0, 0), (1, 1, 1)), ((1, 0, 0), (1, 1, 1))),
+    (((1, 0, 1), (1, 1, 1)), ((1, 0, 0),)),
+    (((1, 0, 0),), ((1, 0, 1), (-1, 1, 1))),
+    (((1, 1, 1),), ((1, 1, 0), (-1, 0, 0))),
+    (((1, 0, 0), (1, 1, 0)), ((1, 1, 1),)),
+    (((1, 0, 1), (-1, 0, 0)), ((1, 0, 0), (1, 0, 1))),
+    (((1, 1, 0), (-1, 1, 1)), ((1, 1, 0), (1, 1, 1))),
+)
+_C = {(0, 0): ((1, 0), (1, 3), (-1, 4), (1, 6)),
+      (0, 1): ((1, 2), (1, 4)),
+      (1, 0): ((1, 1), (1, 3)),
+      (1, 1): ((1, 0), (-1, 1), (1, 2), (1, 5))}
+
+
+def _block(terms, R, P, a, b):
+    """Terms of block (a, b) of an operand of nominal size R x P given as terms
+    (coef, row0, col0, rows, cols) of a panel.  Halving is ceil-first; a second
+    half that runs past a term's extent is zero padding (clipped, possibly to
+    nothing), as Section 3.1 handles odd sizes."""
+    R1, P1 = (R + 1) // 2, (P + 1) // 2
+    out = []
+    for coef, r0, c0, rows, cols in terms:
+        rr0, rr = (r0, min(R1, rows)) if a == 0 else (r0 + R1, max(0, rows - R1))
+        cc0, cc = (c0, min(P1, cols)) if b == 0 else (c0 + P1, max(0, cols - P1))
+        if rr > 0 and cc > 0:
+            out.append((coef, rr0, cc0, rr, cc))
+    return out
+
+
+def _operand(terms, R, P, combo):
+    """Terms of a signed sum of blocks, e.g. X11 + X22."""
+    out = []
+    for coef, a, b in combo:
+        out += [(coef * c, r0, c0, rr, cc) for c, r0, c0, rr, cc in _block(terms, R, P, a, b)]
+    return out
+
+
+def _round_half_away(x):
+    return np.copysign(np.floor(np.abs(x) + 0.5), x)
+
+
+def _e4m3_operand(panel, terms, R, P):
+    """(Q, t): the operand sum of `terms` scaled by 2^(8 - t) and rounded to
+    E4M3 (see the module docstring)."""
+    t = int(np.ceil(np.log2(len(terms)))) if len(terms) > 1 else 0
+    V = np.zeros((R, P), np.float64)          # integer values, |V| < 2^47: exact
+    for coef, r0, c0, rr, cc in terms:
+        V[:rr, :cc] += coef * _round_half_away(panel[r0:r0 + rr, c0:c0 + cc] * 2.0 ** (FP8_FIX - t))
+    return e4m3_round(V * 2.0 ** (8 - FP8_FIX)), t
+
+
+def _strassen(X, Y, xt, yt, R, P, Q, depth):
+    if depth == 0:
+        Qu, tu = _e4m3_operand(X, xt, R, P)
+        Qv, tv = _e4m3_operand(Y, yt, R, Q)
+        sc = 2.0 ** (tu + tv - 16)
+        return (Qu.T @ Qv) * sc, (np.abs(Qu).T @ np.abs(Qv)) * sc
+    R1, P1, Q1 = (R + 1) // 2, (P + 1) // 2, (Q + 1) // 2
+    prods = [_strassen(X, Y, _operand(xt, R, P, ux), _operand(yt, R, Q, vy), R1, P1, Q1, depth - 1)
+             for ux, vy in _M]
+    M = np.zeros((P, Q))
+    D = np.zeros((P, Q))
+    for (a, b), combo in _C.items():
+        rows = slice(0, P1) if a == 0 else slice(P1, P)
+        cols = slice(0, Q1) if b == 0 else slice(Q1, Q)
+        pr, pc = rows.stop - rows.start, cols.stop - cols.start
+        acc = np.zeros((P1, Q1))
+        dacc = np.zeros((P1, Q1))
+        for coef, r in combo:
+            acc += coef * prods[r][0]
+            dacc += prods[r][1]
+        M[rows, cols] = acc[:pr, :pc]
+        D[rows, cols] = dacc[:pr, :pc]
+    return M, D
+
+
+def fp8_strassen_atb(Xh, Yh, depth):
+    """FP8-mode Strassen product of two equilibrated panels (Xh r x p, Yh r x q,
+    columns already scaled by 2^-e): (M, D) with M ~ Xh^T Yh computed by
+    ``depth`` levels of Strassen with E4M3 leaf operands, and
+    D = sum over the products reaching each entry of |Q_u|^T |Q_v| (scaled
+    like M), the magnitude the FP32 accumulation error is relative to."""
+    Xh = np.asarray(Xh, np.float64)
+    Yh = np.asarray(Yh, np.float64)
+    r, p = Xh.shape
+    r2, q = Yh.shape
+    assert r == r2 and r < 2 ** 19
+    return _strassen(Xh, Yh, [(1, 0, 0, r, p)] if r and p else [],
+                     [(1, 0, 0, r, q)] if r and q else [], r, p, q, depth)
+
+
+def fp8_ata_lower_blocks(A, blocks):
+    """(C8, D8) of the FP8 mode for an AtA block layout.  ``blocks`` lists the
+    off-diagonal blocks (r0, p, c0, q, depth): C[r0:r0+p, c0:c0+q] =
+    A[:, r0:r0+p]^T A[:, c0:c0+q] by ``depth`` Strassen levels; every other
+    entry (diagonal panels, depth-0 blocks) is the plain FP8 product."""
+    A = np.asarray(A, np.float64)
+    C, D = fp8_ata_lower(A)
+    e = column_exponents(A)
+    Ah = A * np.ldexp(1.0, -e)[None, :]
+    for r0, p, c0, q, d in blocks:
+        if d == 0:
+            continue
+        M, Dm = fp8_strassen_atb(Ah[:, r0:r0 + p], Ah[:, c0:c0 + q], d)
+        sc = np.ldexp(1.0, e[r0:r0 + p])[:, None] * np.ldexp(1.0, e[c0:c0 + q])[None, :]
+        C[r0:r0 + p, c0:c0 + q] = M * sc
+        D[r0:r0 + p, c0:c0 + q] = Dm * sc
+    return C, D

@@ -9,5 +9,5 @@ fallback.
 """
 from ._binding import (  # noqa: F401
     ATA_F32, ATA_F32_BF16, ATA_F32_FP8, ATA_F64, ATA_F64_EMU, AtaError, Handle, STATUS, library_path, load,
-    plan_info, status_string, version,
+    plan_blocks, plan_info, status_string, version,
 )

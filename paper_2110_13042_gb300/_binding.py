@@ -50,6 +50,7 @@ def load():
     L.ata_status_string.argtypes = [ip]
     L.ata_status_string.restype = ctypes.c_char_p
     L.ata_plan_info.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64)]
+    L.ata_plan_blocks.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64), i64, ctypes.POINTER(i64)]
     L.ata_syrk.argtypes = [vp, i64, i64, ctypes.c_double, vp, i64, ctypes.c_double, vp, i64, ip, vp]
     L.ata_lower_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, ip, vp]
     L.ata_lower_noalloc.restype = ip
@@ -60,7 +61,7 @@ def load():
     L.ata_tune.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp, ctypes.c_double, ctypes.POINTER(i64)]
     L.ata_tune_clear.argtypes = [vp]
     for f in ("ata_create", "ata_set_config", "ata_lower", "ata_syrk", "ata_batched", "ata_sync",
-              "ata_destroy", "ata_plan_info", "ata_version", "ata_set_timing",
+              "ata_destroy", "ata_plan_info", "ata_plan_blocks", "ata_version", "ata_set_timing",
               "ata_phase_times", "ata_tune", "ata_tune_clear"):
         getattr(L, f).restype = ip
     _lib = L
@@ -95,6 +96,19 @@ def plan_info(m: int, n: int, dtype: int, handle: "Handle | None" = None) -> dic
     _check(load().ata_plan_info(handle._h if handle else None, int(m), int(n), int(dtype), out),
            "ata_plan_info")
     return dict(zip(PLAN_FIELDS, (int(v) for v in out)))
+
+
+def plan_blocks(m: int, n: int, dtype: int, handle: "Handle | None" = None) -> list:
+    """Off-diagonal blocks (r0, p, c0, q, strassen_depth) of the plan, in
+    recursion order (host-only planner call, ata_plan_blocks)."""
+    L = load()
+    count = ctypes.c_int64()
+    hh = handle._h if handle else None
+    _check(L.ata_plan_blocks(hh, int(m), int(n), int(dtype), None, 0, ctypes.byref(count)), "ata_plan_blocks")
+    out = (ctypes.c_int64 * (5 * max(count.value, 1)))()
+    _check(L.ata_plan_blocks(hh, int(m), int(n), int(dtype), out, count.value, ctypes.byref(count)),
+           "ata_plan_blocks")
+    return [tuple(int(v) for v in out[5 * i:5 * i + 5]) for i in range(count.value)]
 
 
 def lower_noalloc_ptr(m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:

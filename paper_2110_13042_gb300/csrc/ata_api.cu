@@ -315,6 +315,30 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     return ATA_OK;
 }
 
+int ata_plan_blocks(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out, int64_t max_blocks,
+                    int64_t *count) {
+    if (!count || max_blocks < 0 || (max_blocks > 0 && !out)) return ATA_ERR_INVALID;
+    if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
+    ata_config cfg{};
+    cfg.strassen_depth = -1;
+    if (h) cfg = effective_cfg(h, m, n, dtype);
+    Plan P;
+    std::string err;
+    if (!make_plan(params_for(cfg, m, n, n > 0 ? n : 1, n > 0 ? n : 1, dtype), &P, &err))
+        return ATA_ERR_INVALID;
+    *count = static_cast<int64_t>(P.blocks.size());
+    for (int64_t i = 0; i < max_blocks && i < *count; ++i) {
+        const BlockInfo &b = P.blocks[static_cast<size_t>(i)];
+        int64_t *o = out + i * ATA_BLOCK_FIELDS;
+        o[0] = b.r0;
+        o[1] = b.p;
+        o[2] = b.c0;
+        o[3] = b.q;
+        o[4] = b.depth;
+    }
+    return ATA_OK;
+}
+
 namespace {
 
 // low(C) <- alpha low(A^T A) + beta low(C) (ata_lower: alpha = 1, beta = 0).

@@ -398,6 +398,7 @@ struct Builder {
         recurse(c0 + n1, n2);
         P.n_blocks++;
         int d = digits && P.p.split_search ? d0 : block_depth(n2, n1);
+        P.blocks.push_back({c0 + n1, n2, c0, n1, d, 0});
         if (d == 0)
             classical_block(c0 + n1, n2, c0, n1);
         else

@@ -189,6 +189,14 @@ struct CombDesc {
 constexpr int COMB_ROWS = 64;  // combine tile: 64 rows x 32 columns, 8 rows per thread
 constexpr int COMB_COLS = 32;
 
+// One off-diagonal block of the AtA recursion: C[r0:r0+p, c0:c0+q] =
+// A[:, r0:r0+p]^T A[:, c0:c0+q] by `depth` Strassen levels (0: classical tiles).
+struct BlockInfo {
+    int64_t r0, p, c0, q;
+    int32_t depth;
+    int32_t pad;
+};
+
 struct PlanParams {
     int64_t m = 0, n = 0, lda = 0, ldc = 0;
     int mode = MODE_F64_EMU;
@@ -215,6 +223,7 @@ struct Plan {
     std::vector<LeafTask> tasks;
     std::vector<CombDesc> combs;
     std::vector<CombTerm> cterms;
+    std::vector<BlockInfo> blocks;      // off-diagonal blocks, in recursion order
     int64_t prep_tiles = 0, comb_tiles = 0;
     // workspace layout (byte offsets)
     int64_t off_colmax = 0, off_expo = 0, off_products = 0, product_bytes = 0;

@@ -260,3 +260,20 @@ def test_planner_under_sanitizers(plan_cli_sanitized, m, n):
                 kv = dict(x.split("=") for x in r.stdout.split())
                 assert kv["overlap"] == "0" and kv["prep_map_ok"] == "1" and kv["comb_map_ok"] == "1"
                 assert int(kv["covered"]) == n * (n + 1) // 2
+
+
+@pytest.mark.parametrize("m,n,mode", [(8192, 8192, 1), (300, 5000, 2), (1000, 4096, 5), (64, 129, 1)])
+def test_plan_blocks_describe_the_recursion(lib, m, n, mode):
+    """ata_plan_blocks: one record per off-diagonal block of the plan
+    (ata_plan_info's block count), each strictly below the diagonal, and
+    together with the diagonal panels they cover the lower triangle once."""
+    info = lib.plan_info(m, n, mode)
+    blocks = lib.plan_blocks(m, n, mode)
+    assert len(blocks) == info["blocks"]
+    covered = 0
+    for r0, p, c0, q, d in blocks:
+        assert p > 0 and q > 0 and r0 >= c0 + q and r0 + p <= n and 0 <= d <= info["depth"]
+        covered += p * q
+    # the rest of the lower triangle is diagonal panels (w (w + 1) / 2 each)
+    assert covered < n * (n + 1) // 2
+    assert any(d > 0 for *_, d in blocks) == (info["products"] > 0)

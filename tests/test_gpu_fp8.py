@@ -9,6 +9,8 @@ Two references:
   far more than that.
 * the FP64 definition: within the mode's stated componentwise bound at
   Strassen depth 0, and within the normwise bound with Strassen levels.
+* with Strassen levels, the exact Strassen of the same E4M3 operand sums on
+  the plan's block layout (ata_plan_blocks): again only FP32 accumulation.
 Plus exact results where E4M3 holds the data exactly, bit-identical repeated
 runs, an untouched strict upper triangle, and the entry points that reject
 the mode."""
@@ -94,6 +96,25 @@ def test_strassen_within_normwise_bound(h, depth):
     low = np.tril_indices(520)
     scaled = np.abs(C - ref)[low] / sc[low]
     assert np.max(scaled) <= fp8.fp8_strassen_bound(A, depth)
+    assert upper_untouched(C)
+
+
+@pytest.mark.parametrize("m,n,cutoff,depth", [(1200, 520, 130, 1), (1200, 520, 130, 2), (701, 397, 100, 2),
+                                               (513, 300, 0, 3), (2000, 1100, 0, 1)])
+def test_strassen_matches_fp8_reference(h, ata, m, n, cutoff, depth):
+    """With Strassen levels the reference is the same arithmetic done exactly
+    (oracle.fp8.fp8_ata_lower_blocks on the plan's block layout): every
+    operand an exact sum of blocks rounded once to E4M3, exact leaf products,
+    FP64 result sums.  The GPU differs only by the FP32 accumulation of each
+    leaf product, at most (512 + m/512 + 2) 2^-24 of the summed |Q_u|^T|Q_v|."""
+    A = inputs.uniform(m, n, seed=m + 3 * n + depth).astype(np.float32).astype(np.float64)
+    C = run(h, A, cutoff=cutoff, depth=depth)
+    blocks = ata.plan_blocks(m, n, FP8, h)
+    assert any(b[4] == depth for b in blocks), blocks
+    C8, D8 = fp8.fp8_ata_lower_blocks(A, blocks)
+    low = np.tril_indices(n)
+    err = np.abs(C[low] - C8[low])
+    assert np.all(err <= accum_tol(m) * D8[low] + 1e-30), float(np.max(err / np.maximum(D8[low], 1e-300)))
     assert upper_untouched(C)
 
 
