@@ -22,7 +22,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -160,24 +159,33 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def leaf_traffic(mode, m, n, depth, slices):
-    """DRAM bytes per leaf launch from the committed ncu summary, when it was
-    taken on this configuration and on the current leaf sources; else None."""
-    if (mode, m, n, depth, slices) != (1, 8192, 8192, 1, 6):
-        return None
-    try:
-        with open(os.path.join(ROOT, "profiles", "leaf_tc_s6_n8192_depth1_dram.md")) as f:
-            text = f.read()
-    except OSError:
-        return None
-    mt = re.search(r"traffic_bytes_per_launch: (\d+) sources: ([0-9a-f]+)", text)
-    if not mt:
-        return None
+LEAF_SOURCES = ("leaf_tc.cu", "ptx.cuh", "plan.cpp")
+
+
+def leaf_sources_sha16(root=None):
+    """Prefix of the sha256 of the sources that decide the leaf's traffic."""
     h = hashlib.sha256()
-    for name in ("leaf_tc.cu", "ptx.cuh", "plan.cpp"):
-        with open(os.path.join(ROOT, "paper_2110_13042_gb300", "csrc", name), "rb") as f:
+    for name in LEAF_SOURCES:
+        with open(os.path.join(root or ROOT, "paper_2110_13042_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
-    return int(mt.group(1)) if h.hexdigest()[:16] == mt.group(2) else None
+    return h.hexdigest()[:16]
+
+
+def leaf_traffic(mode, m, n, depth, slices):
+    """DRAM bytes per leaf launch, from the ncu captures listed in
+    profiles/leaf_traffic.json (each with its profile summary), when one was
+    taken on this configuration and on the current leaf sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "leaf_traffic.json")) as f:
+            captures = json.load(f)["captures"]
+    except (OSError, ValueError, KeyError):
+        return None
+    sha = leaf_sources_sha16()
+    for c in captures:
+        if (c["mode"], c["m"], c["n"], c["depth"], c["slices"]) == (mode, m, n, depth, slices) and \
+                c["sources_sha16"] == sha:
+            return int(c["traffic_bytes_per_launch"])
+    return None
 
 
 def batched_bench(ata, torch, dev, stream, args, timed):

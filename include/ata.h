@@ -131,6 +131,36 @@ int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda,
 int ata_syrk(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, int64_t lda,
              double beta, void *C, int64_t ldc, int dtype, void *stream);
 
+/* Flags of ata_syrk_ex (bitwise or). */
+#define ATA_TRANS 1   /* the product A A^T instead of A^T A                    */
+#define ATA_PACKED 2  /* C is a packed lower triangle instead of a full array  */
+
+/* ata_syrk with layout flags; flags == 0 is ata_syrk (bit-identical).
+ *
+ * ATA_TRANS: low(C) <- alpha low(A A^T) + beta low(C).  The paper's method
+ *   covers this product too (Section 3 introduction: A A^T is the A^T A of
+ *   the transposed matrix, and the same recursion of Section 3.1 /
+ *   Algorithm 1 applies).  A is still m x n row-major with lda >= n (the
+ *   caller's array, not transposed); C is m x m (ldc >= m).  The contraction
+ *   runs over the n columns of A: the column exponents are taken over A's
+ *   rows and the operand preparation reads A row by row.  Same modes,
+ *   planning (cutoff, Strassen depth on the m x m recursion) and arithmetic
+ *   as ata_syrk on an explicit copy of A^T: results are bit-identical to it.
+ * ATA_PACKED: C holds only the lower triangle, packed by rows: entry (j, k),
+ *   k <= j, at C[j (j + 1) / 2 + k]; ldc is ignored.  The row-major layout
+ *   of ata_lower stores the same values.  Packed triangles are what the
+ *   paper's distributed AtA sends up its task tree (Section 4.3).
+ * Arguments and errors otherwise as ata_syrk; unknown flag bits:
+ * ATA_ERR_INVALID.  A must not overlap C (C spans m (m + 1) / 2 or
+ * n (n + 1) / 2 elements when packed). */
+int ata_syrk_ex(ata_handle h, int flags, int64_t m, int64_t n, double alpha, const void *A, int64_t lda,
+                double beta, void *C, int64_t ldc, int dtype, void *stream);
+
+/* low(C) <- low(A A^T) for a row-major m x n A (C is m x m): ata_syrk_ex with
+ * ATA_TRANS, alpha = 1, beta = 0. */
+int ata_lower_aat(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
+                  int dtype, void *stream);
+
 /* low(C_i) <- low(A_i^T A_i) for `count` independent problems in one
  * persistent launch.  m, n, lda, ldc: HOST arrays of length count.  A, C:
  * HOST arrays of `count` DEVICE pointers.  Only ATA_F32, ATA_F32_BF16 and
@@ -141,17 +171,45 @@ int ata_syrk(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, in
  * persistent leaf launch over all problems' tiles (longest first).  Problems
  * with n == 0 are skipped and m == 0 zero-fills low(C_i).  The plan and its
  * task table live in pinned host memory owned by the handle and are reused
- * while the same problem set (shapes and pointers) comes back, so the call is
- * graph-capturable after a first uncaptured call with that set.  Errors: as
- * ata_lower, checked per problem before anything is launched. */
+ * while the same shapes (m, n, lda, ldc, dtype) come back; new pointers are
+ * written into the pinned table (after its previous upload has completed).
+ * The call can be captured in a CUDA graph after a first uncaptured call
+ * with those shapes; a replay uses the pointers of the captured call, as
+ * long as no later call rewrote them (use ata_batched_dev to replay on new
+ * buffers).  Errors: as ata_lower, checked per problem before anything is
+ * launched.  The recursion analogue is the paper's static task list
+ * (Section 4.1, Algorithm 3): every tile of every problem is one task. */
 int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n,
                 const void *const *A, const int64_t *lda, void *const *C,
                 const int64_t *ldc, int dtype, void *stream);
+
+/* ata_batched with DEVICE-resident pointer arrays: A_dev and C_dev are device
+ * arrays of `count` device pointers (A_i, C_i); m, n, lda, ldc stay host
+ * arrays (the plan is made on the host from the shapes alone).  The arrays
+ * are read on the device every time the call runs, so a CUDA graph captured
+ * from one call can be replayed after the caller rewrites the arrays with
+ * other buffers of the same shapes.  Pointers are not checked on the host:
+ * each A_i and C_i must be a valid device buffer of its shape, and A_i must
+ * not overlap C_i.  Everything else as ata_batched (bit-identical results). */
+int ata_batched_dev(ata_handle h, int count, const int64_t *m, const int64_t *n,
+                    const void *const *A_dev, const int64_t *lda, void *const *C_dev,
+                    const int64_t *ldc, int dtype, void *stream);
 
 /* Wait for `stream`, then return (and clear) the device status word:
  * ATA_OK, or ATA_ERR_TIMEOUT if a device-side wait ran out since the last
  * ata_sync, or ATA_ERR_CUDA if the stream reported an error. */
 int ata_sync(ata_handle h, void *stream);
+
+/* Self-test of the bounded device-side waits (the failure detection of the
+ * persistent kernels; no counterpart in the paper).  Launches one block on
+ * `stream` whose thread waits, through the same bounded-wait routine the leaf
+ * kernels use, on a barrier that nothing completes.  After budget_ns of GPU
+ * time (1000 <= budget_ns <= 10^10) the wait gives up, records
+ * ATA_ERR_TIMEOUT in the handle's status word and the kernel returns; the
+ * next ata_sync reports it and clears it, and the handle and the CUDA context
+ * stay usable.  For tests and health checks.  ATA_ERR_INVALID for a budget
+ * outside the range. */
+int ata_check_wait_timeout(ata_handle h, int64_t budget_ns, void *stream);
 
 /* Release the handle and its workspace (synchronises the device first). */
 int ata_destroy(ata_handle h);
@@ -241,8 +299,10 @@ int ata_tune_clear(ata_handle h);
  * that device current; make that first call before any stream capture.
  * Every call on a device shares the one array and leaves its contents behind
  * (the call clears what must start at zero): calls that overlap on the GPU
- * race, so serialise them (one stream, or events).  Device-side wait
- * timeouts end the kernels but are not reported (there is no handle). */
+ * race, so serialise them (one stream, or events).  There is no handle and
+ * no status word to read: a non-finite entry of A (ata_lower reports
+ * ATA_ERR_INVALID at ata_sync) or a device-side wait that ran out leaves
+ * every entry of low(C) NaN instead. */
 int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t lda,
                       void *C, int64_t ldc, int dtype, void *stream);
 

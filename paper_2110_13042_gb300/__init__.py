@@ -8,6 +8,6 @@ library; the first call does, and raises if it has not been built
 fallback.
 """
 from ._binding import (  # noqa: F401
-    ATA_F32, ATA_F32_BF16, ATA_F32_FP8, ATA_F64, ATA_F64_EMU, AtaError, Handle, STATUS, library_path, load,
+    ATA_F32, ATA_F32_BF16, ATA_F32_FP8, ATA_F64, ATA_F64_EMU, ATA_PACKED, ATA_TRANS, AtaError, Handle, STATUS, library_path, load,
     plan_blocks, plan_info, status_string, version,
 )

@@ -12,6 +12,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 ATA_F64, ATA_F64_EMU, ATA_F32, ATA_F32_BF16, ATA_F32_FP8 = 0, 1, 2, 4, 5
+ATA_TRANS, ATA_PACKED = 1, 2
 STATUS = {0: "ATA_OK", 1: "ATA_ERR_INVALID", 2: "ATA_ERR_DTYPE", 3: "ATA_ERR_ALLOC",
           4: "ATA_ERR_CUDA", 5: "ATA_ERR_TIMEOUT", 6: "ATA_ERR_UNSUPPORTED"}
 PLAN_FIELDS = ("cutoff", "depth", "slices", "panels", "blocks", "products", "tiles",
@@ -45,11 +46,14 @@ def load():
     L.ata_set_config.argtypes = [vp, vp]
     L.ata_lower.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp]
     L.ata_batched.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, ip, vp]
+    L.ata_batched_dev.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, ip, vp]
     L.ata_sync.argtypes = [vp, vp]
     L.ata_destroy.argtypes = [vp]
     L.ata_status_string.argtypes = [ip]
     L.ata_status_string.restype = ctypes.c_char_p
     L.ata_plan_info.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64)]
+    L.ata_syrk_ex.argtypes = [vp, ip, i64, i64, ctypes.c_double, vp, i64, ctypes.c_double, vp, i64, ip, vp]
+    L.ata_lower_aat.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp]
     L.ata_plan_blocks.argtypes = [vp, i64, i64, ip, ctypes.POINTER(i64), i64, ctypes.POINTER(i64)]
     L.ata_syrk.argtypes = [vp, i64, i64, ctypes.c_double, vp, i64, ctypes.c_double, vp, i64, ip, vp]
     L.ata_lower_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, ip, vp]
@@ -60,9 +64,11 @@ def load():
     L.ata_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.ata_tune.argtypes = [vp, i64, i64, vp, i64, vp, i64, ip, vp, ctypes.c_double, ctypes.POINTER(i64)]
     L.ata_tune_clear.argtypes = [vp]
-    for f in ("ata_create", "ata_set_config", "ata_lower", "ata_syrk", "ata_batched", "ata_sync",
+    L.ata_check_wait_timeout.argtypes = [vp, i64, vp]
+    for f in ("ata_create", "ata_set_config", "ata_lower", "ata_syrk", "ata_syrk_ex", "ata_lower_aat",
+              "ata_batched", "ata_batched_dev", "ata_sync",
               "ata_destroy", "ata_plan_info", "ata_plan_blocks", "ata_version", "ata_set_timing",
-              "ata_phase_times", "ata_tune", "ata_tune_clear"):
+              "ata_phase_times", "ata_tune", "ata_tune_clear", "ata_check_wait_timeout"):
         getattr(L, f).restype = ip
     _lib = L
     return L
@@ -169,12 +175,48 @@ class Handle:
         if rc != 0:
             raise AtaError(rc, f"ata_syrk [{self.last_error()}]")
 
+    def syrk_ex_ptr(self, flags, m, n, alpha, A_ptr, lda, beta, C_ptr, ldc, dtype, stream=None) -> int:
+        """Raw ata_syrk_ex call; returns the status code (no exception)."""
+        return int(load().ata_syrk_ex(self._h, int(flags), int(m), int(n), float(alpha), A_ptr, int(lda),
+                                      float(beta), C_ptr, int(ldc), int(dtype), _stream_ptr(stream)))
+
+    def syrk_ex(self, A, C, dtype, flags=0, alpha=1.0, beta=0.0, stream=None):
+        """ata_syrk_ex on a row-major CUDA tensor A (m x n).  C: n x n (m x m
+        with ATA_TRANS) row-major, or a 1-D tensor of the packed lower
+        triangle with ATA_PACKED."""
+        m, n = A.shape
+        if A.stride(1) != 1 or (C.dim() == 2 and C.stride(1) != 1):
+            raise ValueError("A and C must be row-major with unit column stride")
+        ldc = int(C.stride(0)) if C.dim() == 2 else 0
+        rc = self.syrk_ex_ptr(flags, m, n, alpha, A.data_ptr(), A.stride(0), beta, C.data_ptr(), ldc, dtype,
+                              stream)
+        if rc != 0:
+            raise AtaError(rc, f"ata_syrk_ex [{self.last_error()}]")
+
+    def lower_aat(self, A, C, dtype, stream=None):
+        """low(C) <- low(A A^T) for a row-major CUDA tensor A (m x n), C m x m (ata_lower_aat)."""
+        m, n = A.shape
+        if A.stride(1) != 1 or C.stride(1) != 1:
+            raise ValueError("A and C must be row-major with unit column stride")
+        rc = int(load().ata_lower_aat(self._h, int(m), int(n), A.data_ptr(), int(A.stride(0)), C.data_ptr(),
+                                      int(C.stride(0)), int(dtype), _stream_ptr(stream)))
+        if rc != 0:
+            raise AtaError(rc, f"ata_lower_aat [{self.last_error()}]")
+
     def batched_ptr(self, ms, ns, A_ptrs, ldas, C_ptrs, ldcs, dtype, stream=None) -> int:
         count = len(ms)
         I64 = ctypes.c_int64 * count
         VP = ctypes.c_void_p * count
         return int(load().ata_batched(self._h, count, I64(*ms), I64(*ns), VP(*A_ptrs), I64(*ldas),
                                       VP(*C_ptrs), I64(*ldcs), int(dtype), _stream_ptr(stream)))
+
+    def batched_dev_ptr(self, ms, ns, A_table_ptr, ldas, C_table_ptr, ldcs, dtype, stream=None) -> int:
+        """ata_batched_dev: A_table_ptr / C_table_ptr are device addresses of
+        arrays of len(ms) device pointers (e.g. int64 CUDA tensors)."""
+        count = len(ms)
+        I64 = ctypes.c_int64 * count
+        return int(load().ata_batched_dev(self._h, count, I64(*ms), I64(*ns), A_table_ptr, I64(*ldas), C_table_ptr,
+                                          I64(*ldcs), int(dtype), _stream_ptr(stream)))
 
     def batched(self, As, Cs, dtype, stream=None):
         """low(C_i) <- low(A_i^T A_i) for lists of row-major CUDA tensors in one
@@ -215,6 +257,12 @@ class Handle:
         out = (ctypes.c_double * 4)()
         _check(load().ata_phase_times(self._h, out), "ata_phase_times")
         return [float(v) for v in out]
+
+    def check_wait_timeout(self, budget_ns: int, stream=None) -> int:
+        """ata_check_wait_timeout: a bounded device wait on a barrier nothing
+        completes; returns the launch status (the timeout itself is reported
+        by the next sync())."""
+        return int(load().ata_check_wait_timeout(self._h, int(budget_ns), _stream_ptr(stream)))
 
     def sync(self, stream=None) -> int:
         return int(load().ata_sync(self._h, _stream_ptr(stream)))

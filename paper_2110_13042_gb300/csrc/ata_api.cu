@@ -22,7 +22,7 @@ using namespace ata;
 
 namespace {
 
-using Key = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int, int, int>;
+using Key = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int, int, int, int>;
 
 struct CachedPlan {
     Plan plan;
@@ -35,15 +35,24 @@ struct CachedPlan {
     }
 };
 
-// The plan and pinned task tables of the last batched call (re-used while
-// the same problems, pointers and configuration come back).
+// The plan and pinned task tables of the last batched call, re-used while
+// the same shapes and configuration come back.  The host-array form patches
+// the problem pointers into the pinned table when they change (after the
+// previous upload from it has completed).
 struct CachedBatch {
     std::vector<int64_t> key;
+    std::vector<const void *> ptrs;   // host form: the A_i, C_i in the pinned table
     BatchPlan plan;
     uint8_t *pinned = nullptr;
     size_t table_bytes = 0;
     int64_t off_expo = 0, off_probs = 0, off_tasks = 0, off_planes = 0, total = 0;
+    bool any_empty_m = false;         // some problem has m == 0 and n > 0 (zero fill)
+    cudaEvent_t uploaded = nullptr;   // recorded after each upload from `pinned`
     ~CachedBatch() {
+        if (uploaded) {
+            cudaEventSynchronize(uploaded);
+            cudaEventDestroy(uploaded);
+        }
         if (pinned) cudaFreeHost(pinned);
     }
 };
@@ -177,7 +186,8 @@ ata_config effective_cfg(ata_handle h, int64_t m, int64_t n, int dtype) {
 }
 
 CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
-    Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices, pp.strassen_min};
+    Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices, pp.strassen_min,
+            pp.trans | (pp.packed << 1)};
     auto it = h->plans.find(key);
     if (it != h->plans.end()) return it->second.get();
     std::unique_ptr<CachedPlan> cp(new CachedPlan());
@@ -341,29 +351,38 @@ int ata_plan_blocks(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out,
 
 namespace {
 
-// low(C) <- alpha low(A^T A) + beta low(C) (ata_lower: alpha = 1, beta = 0).
-int lower_impl(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, int64_t lda, double beta, void *C,
-               int64_t ldc, int dtype, void *stream) {
+// low(C) <- alpha low(X^T X) + beta low(C) with X = A (flags without
+// ATA_TRANS) or X = A^T (ATA_TRANS: the product A A^T); A is m x n row-major.
+// ata_lower: flags 0, alpha = 1, beta = 0.
+int lower_impl(ata_handle h, int flags, int64_t m, int64_t n, double alpha, const void *A, int64_t lda,
+               double beta, void *C, int64_t ldc, int dtype, void *stream) {
     if (!h) return ATA_ERR_INVALID;
     h->last_error.clear();
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
+    if (flags & ~(ATA_TRANS | ATA_PACKED)) return ATA_ERR_INVALID;
     if (m < 0 || n < 0) return ATA_ERR_INVALID;
     if (!std::isfinite(alpha) || !std::isfinite(beta)) return ATA_ERR_INVALID;
-    if (n == 0) return ATA_OK;
-    if (ldc < n || !C) return ATA_ERR_INVALID;
+    const bool trans = (flags & ATA_TRANS) != 0, packed = (flags & ATA_PACKED) != 0;
+    // the product X^T X: contraction length mm, output nn x nn
+    const int64_t mm = trans ? n : m, nn = trans ? m : n;
+    if (nn == 0) return ATA_OK;
+    if ((!packed && ldc < nn) || !C) return ATA_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool f32 = is_f32_mode(dtype);
     const size_t es = f32 ? 4 : 8;
-    if (m == 0 || alpha == 0.0) {  // no product term: low(C) <- beta low(C)
+    const size_t c_bytes = (packed ? nn * (nn + 1) / 2 : (nn - 1) * ldc + nn) * es;
+    if (mm == 0 || alpha == 0.0) {  // no product term: low(C) <- beta low(C)
         if (beta == 1.0) return ATA_OK;
-        return launch_scale_lower(C, n, ldc, f32, beta, s) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
+        return launch_scale_lower(C, nn, ldc, f32, beta, s, packed) == cudaSuccess ? ATA_OK : ATA_ERR_CUDA;
     }
     if (lda < n || !A) return ATA_ERR_INVALID;
-    if (ranges_overlap(A, ((m - 1) * lda + n) * es, C, ((n - 1) * ldc + n) * es)) return ATA_ERR_INVALID;
+    if (ranges_overlap(A, ((m - 1) * lda + n) * es, C, c_bytes)) return ATA_ERR_INVALID;
 
     int status = ATA_OK;
-    PlanParams pp = params_for(effective_cfg(h, m, n, dtype), m, n, lda, ldc, dtype);
+    PlanParams pp = params_for(effective_cfg(h, mm, nn, dtype), mm, nn, lda, packed ? nn : ldc, dtype);
     pp.num_ctas = h->num_sms;
+    pp.trans = trans ? 1 : 0;
+    pp.packed = packed ? 1 : 0;
     CachedPlan *cp = get_plan(h, pp, &status);
     if (!cp) return status;
     const Plan &P = cp->plan;
@@ -388,7 +407,7 @@ int lower_impl(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, 
     };
     mark(0);
     cudaError_t e;
-    if (need_expo && (e = launch_colmax(A, m, n, lda, f32, colmax, expo, h->d_status, s)) != cudaSuccess)
+    if (need_expo && (e = launch_colmax(A, mm, nn, lda, f32, trans, colmax, expo, h->d_status, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "column-exponent launch", e);
     mark(1);
     if ((e = launch_prep(P, A, f32, expo, tables, ws, s)) != cudaSuccess)
@@ -406,6 +425,8 @@ int lower_impl(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, 
     lp.lda = lda;
     lp.alpha = alpha;
     lp.beta = beta;
+    lp.a_trans = trans ? 1 : 0;
+    lp.packed = packed ? 1 : 0;
     e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
     if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "leaf launch", e);
     mark(3);
@@ -420,12 +441,22 @@ int lower_impl(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, 
 
 int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
               int dtype, void *stream) {
-    return lower_impl(h, m, n, 1.0, A, lda, 0.0, C, ldc, dtype, stream);
+    return lower_impl(h, 0, m, n, 1.0, A, lda, 0.0, C, ldc, dtype, stream);
 }
 
 int ata_syrk(ata_handle h, int64_t m, int64_t n, double alpha, const void *A, int64_t lda, double beta, void *C,
              int64_t ldc, int dtype, void *stream) {
-    return lower_impl(h, m, n, alpha, A, lda, beta, C, ldc, dtype, stream);
+    return lower_impl(h, 0, m, n, alpha, A, lda, beta, C, ldc, dtype, stream);
+}
+
+int ata_syrk_ex(ata_handle h, int flags, int64_t m, int64_t n, double alpha, const void *A, int64_t lda,
+                double beta, void *C, int64_t ldc, int dtype, void *stream) {
+    return lower_impl(h, flags, m, n, alpha, A, lda, beta, C, ldc, dtype, stream);
+}
+
+int ata_lower_aat(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc,
+                  int dtype, void *stream) {
+    return lower_impl(h, ATA_TRANS, m, n, 1.0, A, lda, 0.0, C, ldc, dtype, stream);
 }
 
 int ata_tune(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda, void *C, int64_t ldc, int dtype,
@@ -542,12 +573,23 @@ int ata_phase_times(ata_handle h, double *out) {
     return ATA_OK;
 }
 
-int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, const void *const *A,
-                const int64_t *lda, void *const *C, const int64_t *ldc, int dtype, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// Batched calls.  Host form: A_host / C_host are host arrays of device
+// pointers (written into the problem table on the host).  Device form:
+// A_dev / C_dev are device arrays of device pointers, copied into the problem
+// table by a kernel when the call runs, so a captured graph picks up
+// whatever the arrays hold at replay time.
+int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, const void *const *A_host,
+                 const int64_t *lda, void *const *C_host, const int64_t *ldc, const void *const *A_dev,
+                 void *const *C_dev, int dtype, void *stream) {
     if (!h || count < 0) return ATA_ERR_INVALID;
     h->last_error.clear();
     if (count == 0) return ATA_OK;
-    if (!m || !n || !A || !lda || !C || !ldc) return ATA_ERR_INVALID;
+    const bool dev = A_dev != nullptr || C_dev != nullptr;
+    if (!m || !n || !lda || !ldc || (dev ? (!A_dev || !C_dev) : (!A_host || !C_host))) return ATA_ERR_INVALID;
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
     if (dtype == ATA_F64 || dtype == ATA_F32_FP8)
         return fail(h, ATA_ERR_UNSUPPORTED, "batched calls take F64_EMU, F32 or F32_BF16");
@@ -557,17 +599,20 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
     for (int i = 0; i < count; ++i) {
         if (m[i] < 0 || n[i] < 0) return ATA_ERR_INVALID;
         if (n[i] == 0) continue;
-        if (ldc[i] < n[i] || !C[i]) return ATA_ERR_INVALID;
-        if (m[i] == 0) continue;
-        if (lda[i] < n[i] || !A[i]) return ATA_ERR_INVALID;
-        if (ranges_overlap(A[i], ((m[i] - 1) * lda[i] + n[i]) * es, C[i], ((n[i] - 1) * ldc[i] + n[i]) * es))
-            return ATA_ERR_INVALID;
+        if (ldc[i] < n[i]) return ATA_ERR_INVALID;
+        if (m[i] > 0 && lda[i] < n[i]) return ATA_ERR_INVALID;
         if (m[i] > MAX_DIGIT_K) return fail(h, ATA_ERR_UNSUPPORTED, "contraction beyond the exact-accumulation limit");
+        if (dev) continue;  // device pointers are not visible here
+        if (!C_host[i]) return ATA_ERR_INVALID;
+        if (m[i] == 0) continue;
+        if (!A_host[i]) return ATA_ERR_INVALID;
+        if (ranges_overlap(A_host[i], ((m[i] - 1) * lda[i] + n[i]) * es, C_host[i], ((n[i] - 1) * ldc[i] + n[i]) * es))
+            return ATA_ERR_INVALID;
     }
 
-    // Plan (and its pinned tables) for this exact problem set.
+    // Plan (and its pinned tables) for this problem set: shapes only.
     std::vector<int64_t> key;
-    key.reserve(4 + 6 * static_cast<size_t>(count));
+    key.reserve(4 + 4 * static_cast<size_t>(count));
     key.push_back(dtype);
     key.push_back(h->cfg.slices);
     key.push_back(h->num_sms);
@@ -577,14 +622,14 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
         key.push_back(n[i]);
         key.push_back(lda[i]);
         key.push_back(ldc[i]);
-        key.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(A[i])));
-        key.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(C[i])));
     }
     if (!h->batch || h->batch->key != key) {
+        h->batch.reset();
         std::unique_ptr<CachedBatch> cb(new (std::nothrow) CachedBatch());
         if (!cb) return ATA_ERR_ALLOC;
         std::string err;
-        if (!make_batch_plan(dtype, h->cfg.slices, h->num_sms, count, m, n, lda, ldc, A, C, &cb->plan, &err))
+        if (!make_batch_plan(dtype, h->cfg.slices, h->num_sms, count, m, n, lda, ldc, nullptr, nullptr, &cb->plan,
+                             &err))
             return fail(h, ATA_ERR_INVALID, err.c_str());
         const BatchPlan &B = cb->plan;
         auto align = [](int64_t x) { return (x + 1023) & ~int64_t(1023); };
@@ -596,9 +641,14 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
         cb->off_planes = cb->off_tasks + align(tasks_bytes);
         cb->total = cb->off_planes + align(B.plane_bytes);
         cb->table_bytes = static_cast<size_t>(cb->off_planes - cb->off_probs);
+        for (int i = 0; i < count; ++i) cb->any_empty_m = cb->any_empty_m || (m[i] == 0 && n[i] > 0);
         if (cudaMallocHost(reinterpret_cast<void **>(&cb->pinned), cb->table_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(h, ATA_ERR_ALLOC, "pinned batch tables");
+        }
+        if (cudaEventCreateWithFlags(&cb->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, ATA_ERR_CUDA, "batch upload event");
         }
         std::memset(cb->pinned, 0, cb->table_bytes);
         std::memcpy(cb->pinned, B.probs.data(), static_cast<size_t>(probs_bytes));
@@ -608,6 +658,21 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
     }
     CachedBatch &cb = *h->batch;
     const BatchPlan &B = cb.plan;
+    if (!dev) {  // patch the problem pointers into the pinned table when they changed
+        bool same = cb.ptrs.size() == 2 * static_cast<size_t>(count);
+        for (int i = 0; same && i < count; ++i) same = cb.ptrs[2 * i] == A_host[i] && cb.ptrs[2 * i + 1] == C_host[i];
+        if (!same) {
+            if (cudaEventSynchronize(cb.uploaded) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "batch table reuse");
+            BatchProb *pp = reinterpret_cast<BatchProb *>(cb.pinned);
+            cb.ptrs.resize(2 * static_cast<size_t>(count));
+            for (int i = 0; i < count; ++i) {
+                pp[i].A = A_host[i];
+                pp[i].C = C_host[i];
+                cb.ptrs[2 * i] = A_host[i];
+                cb.ptrs[2 * i + 1] = C_host[i];
+            }
+        }
+    }
     int rc = ensure_workspace(h, static_cast<size_t>(cb.total));
     if (rc != ATA_OK) return fail(h, rc, "workspace");
     h->resident = nullptr;  // the batch overwrites the single-call tables
@@ -616,9 +681,11 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
     int *expo = reinterpret_cast<int *>(ws + cb.off_expo);
     cudaError_t e = cudaMemcpyAsync(ws + cb.off_probs, cb.pinned, cb.table_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload", e);
-    for (int i = 0; i < count; ++i)
-        if (n[i] > 0 && m[i] == 0 && (e = launch_scale_lower(C[i], n[i], ldc[i], f32, 0.0, s)) != cudaSuccess)
-            return fail(h, ATA_ERR_CUDA, "zero fill", e);
+    if ((e = cudaEventRecord(cb.uploaded, s)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload event", e);
+    if (dev && (e = launch_batched_ptrs(probs, count, A_dev, C_dev, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "batched pointer gather", e);
+    if (cb.any_empty_m && (e = launch_batched_zero(probs, count, f32, s)) != cudaSuccess)
+        return fail(h, ATA_ERR_CUDA, "zero fill", e);
     if ((e = launch_batched_expo(B, probs, f32, expo, h->d_status, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched exponents", e);
     if ((e = launch_batched_prep(B, probs, f32, expo, ws + cb.off_planes, s)) != cudaSuccess)
@@ -634,6 +701,27 @@ int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, con
     if ((e = launch_leaf_tc_raw(B.slices, lp, lp.ntasks, h->num_sms, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched leaf", e);
     return ATA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ata_batched(ata_handle h, int count, const int64_t *m, const int64_t *n, const void *const *A,
+                const int64_t *lda, void *const *C, const int64_t *ldc, int dtype, void *stream) {
+    return batched_impl(h, count, m, n, A, lda, C, ldc, nullptr, nullptr, dtype, stream);
+}
+
+int ata_batched_dev(ata_handle h, int count, const int64_t *m, const int64_t *n, const void *const *A_dev,
+                    const int64_t *lda, void *const *C_dev, const int64_t *ldc, int dtype, void *stream) {
+    if (!A_dev || !C_dev) return count == 0 && h ? ATA_OK : ATA_ERR_INVALID;
+    return batched_impl(h, count, m, n, nullptr, lda, nullptr, ldc, A_dev, C_dev, dtype, stream);
+}
+int ata_check_wait_timeout(ata_handle h, int64_t budget_ns, void *stream) {
+    if (!h || budget_ns < 1000 || budget_ns > 10000000000LL) return ATA_ERR_INVALID;
+    cudaError_t e = launch_wait_check(h->d_status, static_cast<unsigned long long>(budget_ns),
+                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ATA_OK : fail(h, ATA_ERR_CUDA, "wait self-test launch", e);
 }
 
 int ata_sync(ata_handle h, void *stream) {

@@ -125,6 +125,31 @@ __global__ void expo_kernel(const unsigned long long *colmax, int64_t n, int *ex
     expo[j] = column_exponent<T>(colmax[j], status);
 }
 
+// Transposed operand (the A A^T product): the exponent of operand column j
+// is taken over row j of A, which is contiguous.  One warp per row (coalesced
+// loads, four in flight per lane), a warp maximum, no atomics.
+template <typename T>
+__global__ void __launch_bounds__(256) rowmax_expo_kernel(const T *__restrict__ A, int64_t rows, int64_t len,
+                                                          int64_t lda, int *expo, int *status) {
+    const int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= rows) return;  // whole warps
+    const T *r = A + j * lda;
+    unsigned long long mx = 0;
+    int64_t i = lane;
+    for (; i + 96 < len; i += 128) {
+        const unsigned long long b0 = abs_bits(r[i]), b1 = abs_bits(r[i + 32]);
+        const unsigned long long b2 = abs_bits(r[i + 64]), b3 = abs_bits(r[i + 96]);
+        mx = max(mx, max(max(b0, b1), max(b2, b3)));
+    }
+    for (; i < len; i += 32) mx = max(mx, abs_bits(r[i]));
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) expo[j] = column_exponent<T>(mx, status);
+}
+
+// Element offset of entry (j, k), k <= j, of a packed lower triangle.
+__device__ __forceinline__ int64_t packed_at(int64_t j, int64_t k) { return j * (j + 1) / 2 + k; }
+
 // -------------------------------------------------------- operand prep --
 struct Families {
     Family f[MAX_FAMILIES];
@@ -281,10 +306,13 @@ constexpr int PREP_SMEM_TERMS = 128;
 // group are issued before any is used (16 loads in flight per thread whatever
 // the term count), and a group's sums go to shared memory as soon as they are
 // complete.  NT = 0: any count, groups of four rows, one term at a time.
+// trans: the operand is the transpose of A (element (r, c) at A[c * lda + r]);
+// each thread then reads 16 consecutive elements of one row of A.
 template <int S, int NT, typename T, bool F8>
-__device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
-                                           const OpDesc &od, const OpTerm *terms, int k0, int c0, int cc,
-                                           int64_t *sv, int ld) {
+__device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda, bool trans,
+                                           const int *__restrict__ expo, const OpDesc &od, const OpTerm *terms,
+                                           int k0, int c0, int cc, int64_t *sv, int ld) {
+    const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;  // strides of an operand row / column
     constexpr int F = F8 ? FP8_FIX : DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
     // FP32 input with up to 3 digits: every value and sum fits 32 bits.
     constexpr bool NARROW = sizeof(T) == 4 && !F8 && F <= 29;
@@ -307,7 +335,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
             const bool present = t < od.nterms;
             const OpTerm tm = present ? terms[od.first_term + t] : OpTerm{};
             const bool cv = present && c < tm.cols;
-            base[t] = A + (tm.row0 + k0) * lda + tm.col0 + c;
+            base[t] = A + (tm.row0 + k0) * rs + (tm.col0 + c) * cs;
             lim[t] = cv ? tm.rows - k0 : 0;  // rows it < lim are inside the term
             sh[t] = cv ? F - od.t_shift - expo[tm.col0 + c] : 0;
             neg[t] = tm.coef < 0;
@@ -318,7 +346,7 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
 #pragma unroll
             for (int t = 0; t < NT; ++t)
 #pragma unroll
-                for (int j = 0; j < G; ++j) raw[t][j] = (g + j) < lim[t] ? base[t][(g + j) * lda] : T(0);
+                for (int j = 0; j < G; ++j) raw[t][j] = (g + j) < lim[t] ? base[t][(g + j) * rs] : T(0);
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 V v = 0;
@@ -337,12 +365,12 @@ __device__ __forceinline__ void read_terms(const T *__restrict__ A, int64_t lda,
             for (int t = 0; t < od.nterms; ++t) {
                 const OpTerm tm = terms[od.first_term + t];
                 const bool cvalid = c < tm.cols;
-                const T *col = A + tm.col0 + c;
+                const T *col = A + (tm.col0 + c) * cs;
                 T raw[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int k = k0 + g + j;
-                    raw[j] = (cvalid && k < tm.rows) ? col[(tm.row0 + k) * lda] : T(0);
+                    raw[j] = (cvalid && k < tm.rows) ? col[(tm.row0 + k) * rs] : T(0);
                 }
                 const int sh = cvalid ? F - od.t_shift - expo[tm.col0 + c] : 0;
 #pragma unroll
@@ -379,9 +407,9 @@ __device__ __forceinline__ uint32_t e4m3_of_fixed(int64_t V) {
 }
 
 template <int S, typename T, bool F8 = false>
-__device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, const int *__restrict__ expo,
-                                          const OpDesc &od, const OpTerm *terms, int64_t tile,
-                                          const Family &fam, uint8_t *ws, int64_t *sV, int lgtc) {
+__device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, bool trans,
+                                          const int *__restrict__ expo, const OpDesc &od, const OpTerm *terms,
+                                          int64_t tile, const Family &fam, uint8_t *ws, int64_t *sV, int lgtc) {
     const int tc = 1 << lgtc, tk = 4096 >> lgtc, ld = tc + 1;
     const int64_t local = tile - od.tile_base;
     const int tiles_k = od.K_pitch / tk;
@@ -391,11 +419,11 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     const int rg = threadIdx.x >> lgtc;     // 16-row group (K step) within the tile
     int64_t *sv = sV + rg * KSTEP * ld + cc;
     switch (od.nterms) {
-        case 1: read_terms<S, 1, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
-        case 2: read_terms<S, 2, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 1: read_terms<S, 1, T, F8>(A, lda, trans, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 2: read_terms<S, 2, T, F8>(A, lda, trans, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
         case 3:
-        case 4: read_terms<S, 4, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
-        default: read_terms<S, 0, T, F8>(A, lda, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        case 4: read_terms<S, 4, T, F8>(A, lda, trans, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
+        default: read_terms<S, 0, T, F8>(A, lda, trans, expo, od, terms, k0 + rg * KSTEP, c0, cc, sv, ld); break;
     }
     __syncthreads();
 
@@ -440,7 +468,7 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
 }
 
 template <int S, typename T, bool F8 = false>
-__global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict__ A, int64_t lda, bool trans,
                                                              const int *__restrict__ expo,
                                                              const OpDesc *__restrict__ ops, int nops,
                                                              const OpTerm *__restrict__ terms, int nterms,
@@ -460,7 +488,8 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
         int64_t local;
         const OpDesc &od = o[op_of_tile(o, nops, tile, &local)];  // read where used (register budget)
         // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
-        prep_tile<S, T, F8>(A, lda, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV, F8 ? 7 : 8);
+        prep_tile<S, T, F8>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV,
+                            F8 ? 7 : 8);
     }
 }
 
@@ -503,8 +532,8 @@ __global__ void __launch_bounds__(256, batched_prep_blocks<T, S>()) batched_prep
         fam.cols = bp.ncb * BLOCK_COLS;
         fam.offset = bp.plane_off;
         const int lgtc = bp.tc == 64 ? 6 : (bp.tc == 128 ? 7 : 8);
-        prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, expo + bp.col_off, od, &term, tile, fam, planes, sV,
-                        lgtc);
+        prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, false, expo + bp.col_off, od, &term, tile, fam,
+                        planes, sV, lgtc);
     }
 }
 
@@ -542,6 +571,36 @@ __global__ void __launch_bounds__(256) batched_expo_kernel(const BatchProb *__re
     }
 }
 
+// Batched calls with device-resident pointer arrays: copy the problems' A_i
+// and C_i into the problem table (every call, so a replayed graph reads the
+// arrays as they are at replay time).
+__global__ void batched_ptrs_kernel(BatchProb *probs, int64_t count, const void *const *A, void *const *C) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        probs[i].A = A[i];
+        probs[i].C = C[i];
+    }
+}
+
+// Batched calls: low(C_i) <- 0 for the problems with m_i == 0 (one block per
+// problem, grid-stride over problems).
+template <typename T>
+__global__ void __launch_bounds__(256) batched_zero_kernel(const BatchProb *probs, int64_t count) {
+    for (int64_t pi = blockIdx.x; pi < count; pi += gridDim.x) {
+        const BatchProb &bp = probs[pi];
+        if (bp.m != 0 || bp.n == 0) continue;
+        T *C = static_cast<T *>(bp.C);
+        const int64_t total = bp.n * (bp.n + 1) / 2;
+        for (int64_t x = threadIdx.x; x < total; x += blockDim.x) {
+            // x = j (j + 1) / 2 + k, k <= j
+            int64_t j = static_cast<int64_t>((sqrt(8.0 * static_cast<double>(x) + 1.0) - 1.0) * 0.5);
+            while (j * (j + 1) / 2 > x) --j;
+            while ((j + 1) * (j + 2) / 2 <= x) ++j;
+            C[j * bp.ldc + (x - j * (j + 1) / 2)] = T(0);
+        }
+    }
+}
+
 // Persistent grid: four 256-thread blocks per SM (64 registers each).
 static unsigned prep_grid(int64_t ntiles, int per_sm = 4) {
     static int sms[64] = {};
@@ -559,7 +618,7 @@ static unsigned prep_grid(int64_t ntiles, int per_sm = 4) {
 // Native FP64 operands: U[k][c] = sum_t coef_t * a * 2^-e  (FP64, row-major
 // [k][col] with leading dimension fam.cols).
 template <typename T>
-__global__ void __launch_bounds__(256) prep_f64_kernel(const T *__restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(256) prep_f64_kernel(const T *__restrict__ A, int64_t lda, bool trans,
                                                        const int *__restrict__ expo,
                                                        const OpDesc *__restrict__ ops, int nops,
                                                        const OpTerm *__restrict__ terms,
@@ -580,12 +639,13 @@ __global__ void __launch_bounds__(256) prep_f64_kernel(const T *__restrict__ A, 
         const int c = c0 + cc;
         if (c < tm.cols) {
             const double sc = exp2i(-expo[tm.col0 + c]);
-            const T *col = A + tm.col0 + c;
+            const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
+            const T *col = A + (tm.col0 + c) * cs;
 #pragma unroll
             for (int it = 0; it < 16; ++it) {
                 const int k = k0 + kr0 + 4 * it;
                 if (k < tm.rows) {
-                    const double v = static_cast<double>(col[(tm.row0 + k) * lda]) * sc;
+                    const double v = static_cast<double>(col[(tm.row0 + k) * rs]) * sc;
                     V[it] = tm.coef > 0 ? V[it] + v : V[it] - v;
                 }
             }
@@ -625,8 +685,8 @@ template <typename TOut>
 __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
                                                           const int64_t *__restrict__ M, TOut *C,
-                                                          int64_t ldc, const int *__restrict__ expo, double alpha,
-                                                          double beta) {
+                                                          int64_t ldc, bool packed, const int *__restrict__ expo,
+                                                          double alpha, double beta) {
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
     const int64_t local = blockIdx.x - d.tile_base;
     const int tcols = (d.cols + COMB_COLS - 1) / COMB_COLS;
@@ -662,7 +722,8 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
         const int row = r0 + 8 * i;
         if (row >= d.rows) break;
         const int x = xc + expo[d.e_row0 + row];
-        TOut *c = C + d.c_off + static_cast<int64_t>(row) * ldc + col;
+        TOut *c = packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
+                         : C + d.c_off + static_cast<int64_t>(row) * ldc + col;
         if constexpr (sizeof(TOut) == 8)
             store_scaled(c, static_cast<double>(sum[i]) * exp2i(x), alpha, beta);
         else
@@ -676,8 +737,8 @@ template <typename TOut>
 __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
                                                           const double *__restrict__ M, TOut *C,
-                                                          int64_t ldc, const int *__restrict__ expo, double alpha,
-                                                          double beta) {
+                                                          int64_t ldc, bool packed, const int *__restrict__ expo,
+                                                          double alpha, double beta) {
     const CombDesc d = descs[find_comb(descs, nd, blockIdx.x)];
     const int64_t local = blockIdx.x - d.tile_base;
     const int tcols = (d.cols + COMB_COLS - 1) / COMB_COLS;
@@ -704,7 +765,8 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__rest
     for (int i = 0; i < COMB_RPT; ++i) {
         const int row = r0 + 8 * i;
         if (row >= d.rows) break;
-        store_scaled(C + d.c_off + static_cast<int64_t>(row) * ldc + col,
+        store_scaled(packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
+                            : C + d.c_off + static_cast<int64_t>(row) * ldc + col,
                      static_cast<TOut>(sum[i] * exp2i(expo[d.e_row0 + row] + ec)), alpha, beta);
     }
 }
@@ -725,8 +787,12 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
     const LeafTask t = p.tasks[blockIdx.x];
     const double *U = t.fam_u < 0 ? p.A64 : p.fam64[t.fam_u];
     const double *V = t.fam_v < 0 ? p.A64 : p.fam64[t.fam_v];
+    // operand (row k, column c) at base[k * rstride + c * cstride]: families are
+    // [k][col] arrays; A itself may be the transpose of the operand
+    const bool tu = t.fam_u < 0 && p.a_trans, tv = t.fam_v < 0 && p.a_trans;
     const int64_t ldu = t.fam_u < 0 ? p.lda : p.fam_ld[t.fam_u];
     const int64_t ldv = t.fam_v < 0 ? p.lda : p.fam_ld[t.fam_v];
+    const int64_t urs = tu ? 1 : ldu, ucs = tu ? ldu : 1, vrs = tv ? 1 : ldv, vcs = tv ? ldv : 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 48;
     double acc[4][6][2];
@@ -742,8 +808,8 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
             const int kk = lk + 2 * i;
             const int64_t ku = static_cast<int64_t>(t.k0) + k0 + kk, kv = static_cast<int64_t>(t.k0v) + k0 + kk;
             const bool kin = (k0 + kk) < t.klen;
-            Us[kk][lc] = (kin && lc < t.rows) ? U[ku * ldu + t.col_u + lc] : 0.0;
-            if (lc < TILE_N) Vs[kk][lc] = (kin && lc < t.cols) ? V[kv * ldv + t.col_v + lc] : 0.0;
+            Us[kk][lc] = (kin && lc < t.rows) ? U[ku * urs + (t.col_u + lc) * ucs] : 0.0;
+            if (lc < TILE_N) Vs[kk][lc] = (kin && lc < t.cols) ? V[kv * vrs + (t.col_v + lc) * vcs] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -760,7 +826,8 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
         }
         __syncthreads();
     }
-    double *out = reinterpret_cast<double *>(t.kind == OUT_M_F64 ? p.M : p.C) + t.out_off;
+    const bool to_m = t.kind == OUT_M_F64;
+    double *out = reinterpret_cast<double *>(to_m ? p.M : p.C) + (p.packed && !to_m ? 0 : t.out_off);
 #pragma unroll
     for (int fm = 0; fm < 4; ++fm) {
         const int row = wm + 8 * fm + (lane >> 2);
@@ -770,7 +837,8 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
             for (int h = 0; h < 2; ++h) {
                 const int col = wn + 8 * fn + 2 * (lane & 3) + h;
                 if (row < t.rows && col < t.cols && (!t.diag || col <= row + t.diag_off)) {
-                    double *o = out + static_cast<int64_t>(row) * t.out_ld + col;
+                    double *o = p.packed && !to_m ? out + packed_at(t.out_off + row, t.out_ld + col)
+                                                  : out + static_cast<int64_t>(row) * t.out_ld + col;
                     if (t.kind == OUT_M_F64)
                         *o = acc[fm][fn][h];
                     else
@@ -782,10 +850,13 @@ __global__ void __launch_bounds__(256) leaf_f64_kernel(const __grid_constant__ L
 }
 
 template <typename T>
-__global__ void scale_lower_kernel(T *C, int64_t n, int64_t ldc, double beta) {
+__global__ void scale_lower_kernel(T *C, int64_t n, int64_t ldc, bool packed, double beta) {
     const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t j = blockIdx.y + static_cast<int64_t>(blockIdx.z) * 65535;
-    if (j < n && k <= j) C[j * ldc + k] = beta != 0.0 ? static_cast<T>(beta * C[j * ldc + k]) : T(0);
+    if (j < n && k <= j) {
+        T *c = packed ? C + packed_at(j, k) : C + j * ldc + k;
+        *c = beta != 0.0 ? static_cast<T>(beta * *c) : T(0);
+    }
 }
 
 }  // namespace
@@ -799,6 +870,24 @@ cudaError_t launch_batched_expo(const BatchPlan &B, const BatchProb *probs, bool
         batched_expo_kernel<float><<<grid, 256, 0, s>>>(probs, B.count, expo, status);
     else
         batched_expo_kernel<double><<<grid, 256, 0, s>>>(probs, B.count, expo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_ptrs(BatchProb *probs, int64_t count, const void *const *A, void *const *C,
+                                cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned g = static_cast<unsigned>(count < 256 * 1024 ? (count + 255) / 256 : 1024);
+    batched_ptrs_kernel<<<g, 256, 0, s>>>(probs, count, A, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_zero(const BatchProb *probs, int64_t count, bool is_f32, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned g = static_cast<unsigned>(count < 65535 ? count : 65535);
+    if (is_f32)
+        batched_zero_kernel<float><<<g, 256, 0, s>>>(probs, count);
+    else
+        batched_zero_kernel<double><<<g, 256, 0, s>>>(probs, count);
     return cudaGetLastError();
 }
 
@@ -828,8 +917,16 @@ cudaError_t launch_batched_prep(const BatchPlan &B, const BatchProb *probs, bool
     return cudaGetLastError();
 }
 
-cudaError_t launch_colmax(const void *A, int64_t m, int64_t n, int64_t lda, bool is_f32,
+cudaError_t launch_colmax(const void *A, int64_t m, int64_t n, int64_t lda, bool is_f32, bool trans,
                           unsigned long long *colmax, int *expo, int *status, cudaStream_t s) {
+    if (trans) {  // operand column j is row j of A: one warp per row, exponents written directly
+        const unsigned g = static_cast<unsigned>((n + 7) / 8);
+        if (is_f32)
+            rowmax_expo_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(A), n, m, lda, expo, status);
+        else
+            rowmax_expo_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(A), n, m, lda, expo, status);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * n, s);
     if (e != cudaSuccess) return e;
     const int rows_per_block = 64;
@@ -863,14 +960,15 @@ static void prep_digits_dispatch(const Plan &P, const void *A, bool is_f32, cons
     const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
     const unsigned g = prep_grid(P.prep_tiles);
     const int nops = static_cast<int>(P.ops.size()), nterms = static_cast<int>(P.terms.size());
+    const bool tr = P.p.trans != 0;
     if (S == 1 && P.p.mode == MODE_F32_FP8)  // FP8 mode: float A, one E4M3 plane
-        prep_digits_kernel<1, float, true><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo, ops,
-                                                              nops, terms, nterms, P.prep_tiles, F, ws);
+        prep_digits_kernel<1, float, true><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, tr, expo,
+                                                              ops, nops, terms, nterms, P.prep_tiles, F, ws);
     else if (is_f32)
-        prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, expo, ops, nops,
-                                                        terms, nterms, P.prep_tiles, F, ws);
+        prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, tr, expo, ops,
+                                                        nops, terms, nterms, P.prep_tiles, F, ws);
     else
-        prep_digits_kernel<S, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, expo, ops,
+        prep_digits_kernel<S, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, tr, expo, ops,
                                                          nops, terms, nterms, P.prep_tiles, F, ws);
 }
 
@@ -884,8 +982,8 @@ cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *ex
         const OpDesc *ops = reinterpret_cast<const OpDesc *>(tables + P.t_ops);
         const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
         prep_f64_kernel<double><<<static_cast<unsigned>(P.prep_tiles), 256, 0, s>>>(
-            static_cast<const double *>(A), P.p.lda, expo, ops, static_cast<int>(P.ops.size()), terms,
-            F, ws);
+            static_cast<const double *>(A), P.p.lda, P.p.trans != 0, expo, ops, static_cast<int>(P.ops.size()),
+            terms, F, ws);
         return cudaGetLastError();
     }
     switch (P.slices) {
@@ -914,29 +1012,31 @@ cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, 
     const CombTerm *t = reinterpret_cast<const CombTerm *>(tables + P.t_cterms);
     const unsigned g = static_cast<unsigned>(P.comb_tiles);
     const int nd = static_cast<int>(P.combs.size());
+    const bool pk = P.p.packed != 0;
     if (P.p.mode == MODE_F64)
         combine_f64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
-                                                      static_cast<double *>(C), P.p.ldc, expo, alpha, beta);
+                                                      static_cast<double *>(C), P.p.ldc, pk, expo, alpha, beta);
     else if (P.p.mode == MODE_F32_FP8)  // FP8 products are FP32 sums, stored as double
         combine_f64_kernel<float><<<g, 256, 0, s>>>(d, nd, t, static_cast<const double *>(M),
-                                                     static_cast<float *>(C), P.p.ldc, expo, alpha, beta);
+                                                     static_cast<float *>(C), P.p.ldc, pk, expo, alpha, beta);
     else if (P.p.mode == MODE_F64_EMU)
         combine_i64_kernel<double><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
-                                                      static_cast<double *>(C), P.p.ldc, expo, alpha, beta);
+                                                      static_cast<double *>(C), P.p.ldc, pk, expo, alpha, beta);
     else
         combine_i64_kernel<float><<<g, 256, 0, s>>>(d, nd, t, static_cast<const int64_t *>(M),
-                                                     static_cast<float *>(C), P.p.ldc, expo, alpha, beta);
+                                                     static_cast<float *>(C), P.p.ldc, pk, expo, alpha, beta);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_lower(void *C, int64_t n, int64_t ldc, bool is_f32, double beta, cudaStream_t s) {
+cudaError_t launch_scale_lower(void *C, int64_t n, int64_t ldc, bool is_f32, double beta, cudaStream_t s,
+                               bool packed) {
     if (n <= 0) return cudaSuccess;
     dim3 grid(static_cast<unsigned>((n + 255) / 256), static_cast<unsigned>(n < 65535 ? n : 65535),
               static_cast<unsigned>((n + 65534) / 65535));
     if (is_f32)
-        scale_lower_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(C), n, ldc, beta);
+        scale_lower_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(C), n, ldc, packed, beta);
     else
-        scale_lower_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(C), n, ldc, beta);
+        scale_lower_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(C), n, ldc, packed, beta);
     return cudaGetLastError();
 }
 
@@ -957,10 +1057,10 @@ cudaError_t launch_prep_digits_raw(int slices, const void *A, bool is_f32, int64
 #define ATA_PREP_RAW(SS)                                                                                   \
     case SS:                                                                                               \
         if (is_f32)                                                                                        \
-            prep_digits_kernel<SS, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), lda, expo, ops, \
+            prep_digits_kernel<SS, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), lda, false, expo, ops, \
                                                              nops, terms, 1, prep_tiles, F, ws);           \
         else                                                                                               \
-            prep_digits_kernel<SS, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), lda, expo,    \
+            prep_digits_kernel<SS, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), lda, false, expo, \
                                                               ops, nops, terms, 1, prep_tiles, F, ws);     \
         break;
     switch (slices) {

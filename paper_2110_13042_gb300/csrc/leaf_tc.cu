@@ -121,6 +121,17 @@ __device__ __forceinline__ void spin_ns(unsigned long long ns) {
     }
 }
 
+// Element offset in C of column 0 of tile row `row`: row-major C, or a packed
+// lower triangle (entry (j, k) at j (j + 1) / 2 + k; the task then holds the
+// tile's first row and column in out_off / out_ld).
+__device__ __forceinline__ int64_t c_row_offset(const LeafTask &t, int row, int packed) {
+    if (packed) {
+        const int64_t j = t.out_off + row;
+        return j * (j + 1) / 2 + t.out_ld;
+    }
+    return t.out_off + static_cast<int64_t>(row) * t.out_ld;
+}
+
 __device__ __forceinline__ double exp2d(int x) {
     if (x >= -1022 && x <= 1023) return __longlong_as_double(static_cast<long long>(x + 1023) << 52);
     return scalbn(1.0, x);
@@ -634,7 +645,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     for (int gi = 0; gi < NI; ++gi) {
                         const uint32_t m = issuer_mask<NI>(gi) & due;
                         if (!m) continue;
-                        if (!mbar_wait(&sh->accf[gi], (accf_phase >> gi) & 1u, abort_flag, p.status)) {
+                        // every lane of the warp takes the same decision before
+                        // the warp-collective TMEM loads
+                        if (!__all_sync(0xffffffffu,
+                                        mbar_wait(&sh->accf[gi], (accf_phase >> gi) & 1u, abort_flag, p.status))) {
                             good = false;
                             break;
                         }
@@ -652,7 +666,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     }
                     continue;
                 }
-                if (!mbar_wait(&sh->accf[0], accf_phase, abort_flag, p.status)) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&sh->accf[0], accf_phase, abort_flag, p.status))) {
                     ok = false;
                     break;
                 }
@@ -686,7 +700,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     } else {
                         const int er = -2 * FP8_TOP + t.shift + (t.eu >= 0 ? p.expo[t.eu + row] : 0);
                         const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
-                        float *out = static_cast<float *>(p.C) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                        float *out = static_cast<float *>(p.C) + c_row_offset(t, row, p.packed);
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
@@ -710,7 +724,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                     void *cbase = p.probs ? p.probs[t.prob].C : p.C;
                     if (t.kind == OUT_C_F64) {
-                        double *out = static_cast<double *>(cbase) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                        double *out = static_cast<double *>(cbase) + c_row_offset(t, row, p.packed);
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
@@ -719,7 +733,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                              p.alpha, p.beta);
                         }
                     } else {
-                        float *out = static_cast<float *>(cbase) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                        float *out = static_cast<float *>(cbase) + c_row_offset(t, row, p.packed);
 #pragma unroll
                         for (int i = 0; i < EPI_COLS; ++i) {
                             const int col = colbase + i;
@@ -736,9 +750,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
+        // After an abort, MMAs committed to barriers nobody waited for may
+        // still be writing TMEM: give them time to retire before the release.
+        if (*abort_flag) spin_ns(2000000);
         tc_fence_after();
         tmem_dealloc(tmem, C::TMEM_COLS);
     }
+}
+
+// Self-test of the bounded wait: one thread waits on a barrier that nothing
+// arrives at, with the given budget, so the wait runs out, records the
+// timeout status and the kernel returns.
+__global__ void wait_check_kernel(int *status, unsigned long long budget_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+    mbar_wait_for(&bar, 0u, &abort_flag, status, budget_ns);
 }
 
 // The shared-memory opt-in of leaf_tc_kernel<S>, set once per device (a
@@ -800,6 +830,11 @@ cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cud
 }  // namespace ata
 
 namespace ata {
+
+cudaError_t launch_wait_check(int *status, unsigned long long budget_ns, cudaStream_t s) {
+    wait_check_kernel<<<1, 32, 0, s>>>(status, budget_ns);
+    return cudaGetLastError();
+}
 
 // Leaf launch from an explicit task count (allocation-free and batched entry
 // points).

@@ -41,13 +41,17 @@ struct Layout {
     Family fam;
 };
 
+__host__ __device__ inline int64_t panel_tiles(int64_t J, int64_t n);
+
 int64_t count_tiles(int64_t n) {
     int64_t t = 0;
-    for (int64_t J = 0; J < ceil_div(n, TILE_M); ++J) {
-        const int64_t rows = std::min<int64_t>(TILE_M, n - J * TILE_M);
-        for (int64_t K = 0; K * TILE_N < n && K * TILE_N <= J * TILE_M + rows - 1; ++K) ++t;
-    }
+    for (int64_t J = 0; J < ceil_div(n, TILE_M); ++J) t += panel_tiles(J, n);
     return t;
+}
+
+// Digit-plane bytes alone (the largest part of the scratch), in closed form.
+int64_t plane_bytes(int64_t m, int64_t n, int slices) {
+    return round_up(m, PREP_K) * (round_up(n, TILE) + TILE) * 2 * slices;
 }
 
 Layout layout_for(int64_t m, int64_t n, int slices) {
@@ -76,54 +80,90 @@ Layout layout_for(int64_t m, int64_t n, int slices) {
     return L;
 }
 
-// One thread writes the operand table and the lower-triangle tile list (the
-// same tiles, in the same order, as the planner's single diagonal panel).
-__global__ void noalloc_tables_kernel(int64_t m, int64_t n, int64_t ldc, int kind, int hbits, int64_t K_pitch,
-                                      OpDesc *op, OpTerm *term, LeafTask *tasks) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    OpTerm tm{};
-    tm.row0 = 0;
-    tm.col0 = 0;
-    tm.rows = static_cast<int32_t>(m);
-    tm.cols = static_cast<int32_t>(n);
-    tm.coef = 1;
-    *term = tm;
-    OpDesc od{};
-    od.family = 0;
-    od.t_shift = 0;
-    od.nterms = 1;
-    od.first_term = 0;
-    od.out_col = 0;
-    od.K_pitch = static_cast<int32_t>(K_pitch);
-    od.P_pad = static_cast<int32_t>(((n + TILE - 1) / TILE) * TILE);
-    od.tile_base = 0;
-    *op = od;
-    int64_t t = 0;
-    for (int64_t J = 0; J * TILE_M < n; ++J) {
-        const int64_t rows = n - J * TILE_M < TILE_M ? n - J * TILE_M : TILE_M;
-        for (int64_t K = 0; K * TILE_N < n && K * TILE_N <= J * TILE_M + rows - 1; ++K) {
-            const int64_t r0 = J * TILE_M, c0 = K * TILE_N;
-            const int64_t cols = n - c0 < TILE_N ? n - c0 : TILE_N;
-            LeafTask lt{};
-            lt.fam_u = 0;
-            lt.fam_v = 0;
-            lt.col_u = static_cast<int32_t>(r0);
-            lt.col_v = static_cast<int32_t>(c0);
-            lt.k0 = 0;
-            lt.klen = static_cast<int32_t>(m);
-            lt.rows = static_cast<int32_t>(rows);
-            lt.cols = static_cast<int32_t>(cols);
-            lt.diag = (c0 + cols - 1 > r0) ? 1 : 0;
-            lt.diag_off = static_cast<int32_t>(r0 - c0);
-            lt.kind = kind;
-            lt.shift = 0;
-            lt.eu = static_cast<int32_t>(r0);
-            lt.ev = static_cast<int32_t>(c0);
-            lt.out_off = r0 * ldc + c0;
-            lt.out_ld = ldc;
-            lt.hbits = hbits;
-            tasks[t++] = lt;
-        }
+// Lower-triangle tiles of row panel J (TILE_M rows starting at J * TILE_M) of
+// an n x n product: columns blocks K with K * TILE_N < n that reach the
+// diagonal, i.e. K * TILE_N <= J * TILE_M + rows - 1.
+__host__ __device__ inline int64_t panel_tiles(int64_t J, int64_t n) {
+    const int64_t rows = n - J * TILE_M < TILE_M ? n - J * TILE_M : TILE_M;
+    const int64_t nk = (n + TILE_N - 1) / TILE_N;
+    const int64_t reach = (J * TILE_M + rows - 1) / TILE_N + 1;
+    return reach < nk ? reach : nk;
+}
+
+// The operand table and the lower-triangle tile list (the same tiles, in the
+// same order, as the planner's single diagonal panel).  Block J writes the
+// tiles of row panel J at the offset given by the tile counts of the panels
+// before it (summed by the block's threads), one tile per thread; block 0
+// also writes the operand descriptor.
+__global__ void __launch_bounds__(128) noalloc_tables_kernel(int64_t m, int64_t n, int64_t ldc, int kind, int hbits,
+                                                             int64_t K_pitch, OpDesc *op, OpTerm *term,
+                                                             LeafTask *tasks) {
+    __shared__ int64_t part[4];
+    const int64_t J = blockIdx.x;
+    if (J == 0 && threadIdx.x == 0) {
+        OpTerm tm{};
+        tm.row0 = 0;
+        tm.col0 = 0;
+        tm.rows = static_cast<int32_t>(m);
+        tm.cols = static_cast<int32_t>(n);
+        tm.coef = 1;
+        *term = tm;
+        OpDesc od{};
+        od.family = 0;
+        od.t_shift = 0;
+        od.nterms = 1;
+        od.first_term = 0;
+        od.out_col = 0;
+        od.K_pitch = static_cast<int32_t>(K_pitch);
+        od.P_pad = static_cast<int32_t>(((n + TILE - 1) / TILE) * TILE);
+        od.tile_base = 0;
+        *op = od;
+    }
+    int64_t before = 0;
+    for (int64_t j = threadIdx.x; j < J; j += blockDim.x) before += panel_tiles(j, n);
+    for (int off = 16; off > 0; off >>= 1) before += __shfl_down_sync(0xffffffffu, before, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = before;
+    __syncthreads();
+    const int64_t base = part[0] + part[1] + part[2] + part[3];
+    const int64_t r0 = J * TILE_M;
+    const int64_t rows = n - r0 < TILE_M ? n - r0 : TILE_M;
+    for (int64_t K = threadIdx.x; K < panel_tiles(J, n); K += blockDim.x) {
+        const int64_t c0 = K * TILE_N;
+        const int64_t cols = n - c0 < TILE_N ? n - c0 : TILE_N;
+        LeafTask lt{};
+        lt.fam_u = 0;
+        lt.fam_v = 0;
+        lt.col_u = static_cast<int32_t>(r0);
+        lt.col_v = static_cast<int32_t>(c0);
+        lt.k0 = 0;
+        lt.klen = static_cast<int32_t>(m);
+        lt.rows = static_cast<int32_t>(rows);
+        lt.cols = static_cast<int32_t>(cols);
+        lt.diag = (c0 + cols - 1 > r0) ? 1 : 0;
+        lt.diag_off = static_cast<int32_t>(r0 - c0);
+        lt.kind = kind;
+        lt.shift = 0;
+        lt.eu = static_cast<int32_t>(r0);
+        lt.ev = static_cast<int32_t>(c0);
+        lt.out_off = r0 * ldc + c0;
+        lt.out_ld = ldc;
+        lt.hbits = hbits;
+        tasks[base + K] = lt;
+    }
+}
+
+// Non-finite input (flagged in the status word by the column-exponent pass)
+// or a device wait that ran out (flagged by the leaf): low(C) becomes NaN, so
+// the caller sees the failure without a status read.
+template <typename T>
+__global__ void __launch_bounds__(256) nan_if_flagged_kernel(const int *status, T *C, int64_t n, int64_t ldc) {
+    if (*status == 0) return;
+    const T nan = static_cast<T>(__longlong_as_double(0x7FF8000000000000LL));
+    const int64_t total = n * n;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t j = i / n, k = i - j * n;
+        if (k <= j) C[j * ldc + k] = nan;
     }
 }
 
@@ -183,6 +223,8 @@ extern "C" int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t ld
     }
     if (m > MAX_DIGIT_K || n > (int64_t(1) << 30)) return ATA_ERR_UNSUPPORTED;
     const int slices = default_slices(dtype, m);
+    // closed-form rejection first: the exact layout counts every tile
+    if (plane_bytes(m, n, slices) > static_cast<int64_t>(NOALLOC_SCRATCH_BYTES)) return ATA_ERR_UNSUPPORTED;
     const Layout L = layout_for(m, n, slices);
     if (static_cast<size_t>(L.total) > NOALLOC_SCRATCH_BYTES) return ATA_ERR_UNSUPPORTED;
 
@@ -201,10 +243,10 @@ extern "C" int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t ld
     // The scratch keeps the previous call's contents: the status word starts
     // at zero (colmax is cleared by its own launch).
     if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return ATA_ERR_CUDA;
-    noalloc_tables_kernel<<<1, 1, 0, s>>>(m, n, ldc, f32 ? OUT_C_F32 : OUT_C_F64, hbits_for(m), L.fam.K_pitch, ops,
-                                          terms, tasks);
+    noalloc_tables_kernel<<<static_cast<unsigned>(ceil_div(n, TILE_M)), 128, 0, s>>>(
+        m, n, ldc, f32 ? OUT_C_F32 : OUT_C_F64, hbits_for(m), L.fam.K_pitch, ops, terms, tasks);
     if (cudaGetLastError() != cudaSuccess) return ATA_ERR_CUDA;
-    if (launch_colmax(A, m, n, lda, f32, colmax, expo, status, s) != cudaSuccess) return ATA_ERR_CUDA;
+    if (launch_colmax(A, m, n, lda, f32, false, colmax, expo, status, s) != cudaSuccess) return ATA_ERR_CUDA;
     if (launch_prep_digits_raw(slices, A, f32, lda, expo, ops, 1, terms, L.fam, L.prep_tiles, ws, s) !=
         cudaSuccess)
         return ATA_ERR_CUDA;
@@ -219,5 +261,11 @@ extern "C" int ata_lower_noalloc(int64_t m, int64_t n, const void *A, int64_t ld
     lp.expo = expo;
     lp.status = status;
     if (launch_leaf_tc_raw(slices, lp, static_cast<int>(L.ntasks), sms, s) != cudaSuccess) return ATA_ERR_CUDA;
+    const unsigned nb = static_cast<unsigned>(std::min<int64_t>(ceil_div(n * n, 256), 4 * static_cast<int64_t>(sms)));
+    if (f32)
+        nan_if_flagged_kernel<float><<<nb, 256, 0, s>>>(status, static_cast<float *>(C), n, ldc);
+    else
+        nan_if_flagged_kernel<double><<<nb, 256, 0, s>>>(status, static_cast<double *>(C), n, ldc);
+    if (cudaGetLastError() != cudaSuccess) return ATA_ERR_CUDA;
     return ATA_OK;
 }

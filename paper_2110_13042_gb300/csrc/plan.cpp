@@ -144,8 +144,13 @@ struct Builder {
         }
         t.shift = 0;
         t.hbits = fp8 ? 0 : hbits_for(P.p.m);
-        t.out_off = r0 * P.p.ldc + c0;
-        t.out_ld = P.p.ldc;
+        if (P.p.packed) {  // packed lower triangle: the store computes each row's offset
+            t.out_off = r0;
+            t.out_ld = c0;
+        } else {
+            t.out_off = r0 * P.p.ldc + c0;
+            t.out_ld = P.p.ldc;
+        }
         P.tasks.push_back(t);
         P.plain_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
         P.leaf_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
@@ -462,14 +467,17 @@ bool make_batch_plan(int mode, int slices, int num_ctas, int64_t count, const in
     B.probs.resize(static_cast<size_t>(count));
     int64_t col_off = 0, plane_off = 0, prep = 0;
     for (int64_t i = 0; i < count; ++i) {
+        // A and C may be absent (pointers that only the device holds): then
+        // they are not checked here and the table's pointers stay null.
         if (m[i] < 0 || n[i] < 0 || m[i] > MAX_DIGIT_K || n[i] > (int64_t(1) << 30) ||
-            (n[i] > 0 && (ldc[i] < n[i] || !C[i])) || (n[i] > 0 && m[i] > 0 && (lda[i] < n[i] || !A[i]))) {
+            (n[i] > 0 && (ldc[i] < n[i] || (C && !C[i]))) ||
+            (n[i] > 0 && m[i] > 0 && (lda[i] < n[i] || (A && !A[i])))) {
             if (err) *err = "invalid problem " + std::to_string(i);
             return false;
         }
         BatchProb &q = B.probs[static_cast<size_t>(i)];
-        q.A = A[i];
-        q.C = C[i];
+        q.A = A ? A[i] : nullptr;
+        q.C = C ? C[i] : nullptr;
         q.m = m[i];
         q.n = n[i];
         q.lda = lda[i];
@@ -546,8 +554,10 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     Plan &P = *plan;
     P = Plan();
     P.p = pp;
-    if (pp.m < 0 || pp.n < 0 || pp.lda < std::max<int64_t>(pp.n, 1) ||
-        pp.ldc < std::max<int64_t>(pp.n, 1)) {
+    // A's leading dimension spans the operand's columns, or (transposed
+    // operand) its contraction rows; a packed C has none.
+    const int64_t lda_min = std::max<int64_t>(pp.trans ? pp.m : pp.n, 1);
+    if (pp.m < 0 || pp.n < 0 || pp.lda < lda_min || (!pp.packed && pp.ldc < std::max<int64_t>(pp.n, 1))) {
         if (err) *err = "invalid dimensions";
         return false;
     }

@@ -108,6 +108,8 @@ struct LeafTask {
     int32_t diag_off;       // with diag: write only where col <= row + diag_off
     int64_t out_off;        // element offset of the tile origin in the output
     int64_t out_ld;         // output leading dimension (elements)
+                            // (packed lower-triangular C: out_off = first row,
+                            //  out_ld = first column of the tile in C)
     int32_t hbits;          // extra fraction bits of T for short contractions
     int32_t k0v;            // contraction offset of the column operand (k0: row operand)
     int32_t prob;           // batched calls: problem index (planes and C of that problem)
@@ -209,7 +211,15 @@ struct PlanParams {
                              // model; 0: always split at the aligned middle
     int num_ctas = 0;        // > 1: lay the tile list out for this many
                              // persistent leaf CTAs (longest-first balance)
+    int trans = 0;           // 1: the operand is the transpose of a row-major
+                             // n x m array (A A^T of that array): element (i, j)
+                             // of the m x n operand at A[j * lda + i], lda >= m
+    int packed = 0;          // 1: C is stored as a packed lower triangle, entry
+                             // (j, k) at j (j + 1) / 2 + k (ldc unused)
 };
+
+// Element offset of entry (j, k), k <= j, of a packed lower triangle.
+inline int64_t packed_index(int64_t j, int64_t k) { return j * (j + 1) / 2 + k; }
 
 struct Plan {
     PlanParams p;

@@ -84,21 +84,26 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity to complete.  Returns
 // false (after flagging) if the budget ran out or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int *status) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                              int *status, unsigned long long budget_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*abort_flag) return false;
-            if (globaltimer_ns() - t0 > WAIT_BUDGET_NS) {
+            if (globaltimer_ns() - t0 > budget_ns) {
                 *abort_flag = 1;
                 atomicExch(status, STATUS_TIMEOUT);
                 return false;
             }
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *status) {
+    return mbar_wait_for(bar, parity, abort_flag, status, WAIT_BUDGET_NS);
 }
 
 // --------------------------------------------------------------------- TMA

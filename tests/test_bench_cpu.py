@@ -1,7 +1,7 @@
 """Host logic of bench.py that needs no GPU: the DRAM-traffic key of the
-roofline (reported only for the configuration it was measured on and only
-while the leaf sources are the ones it was measured on), and the command
-line."""
+roofline (read from profiles/leaf_traffic.json; reported only for the
+configuration it was measured on and only while the leaf sources are the ones
+it was measured on), and the command line."""
 import os
 import shutil
 import subprocess
@@ -27,12 +27,20 @@ def test_traffic_only_for_the_measured_configuration(cfg):
     assert bench.leaf_traffic(*cfg) is None
 
 
+def test_traffic_file_names_its_profile_summaries():
+    import json
+    with open(os.path.join(ROOT, "profiles", "leaf_traffic.json")) as f:
+        caps = json.load(f)["captures"]
+    for c in caps:
+        assert os.path.exists(os.path.join(ROOT, "profiles", c["summary"]))
+
+
 def test_traffic_dropped_when_a_leaf_source_changes(tmp_path, monkeypatch):
     """A copy of the tree whose leaf kernel differs by one byte reports no
     traffic: the summary was measured on other sources."""
     root = tmp_path / "tree"
     (root / "profiles").mkdir(parents=True)
-    shutil.copy(os.path.join(ROOT, "profiles", "leaf_tc_s6_n8192_depth1_dram.md"), root / "profiles")
+    shutil.copy(os.path.join(ROOT, "profiles", "leaf_traffic.json"), root / "profiles")
     src = root / "paper_2110_13042_gb300" / "csrc"
     src.mkdir(parents=True)
     for name in ("leaf_tc.cu", "ptx.cuh", "plan.cpp"):

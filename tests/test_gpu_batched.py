@@ -152,3 +152,115 @@ def test_batched_errors(ata, h):
     assert h.batched_ptr([8], [4], [A.data_ptr()], [4], [A.data_ptr()], [4], F64_EMU) == 1
     # unknown dtype
     assert h.batched_ptr([8], [4], [A.data_ptr()], [4], [C.data_ptr()], [4], 9) == 2
+
+
+def ptr_table(tensors):
+    return torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64, device="cuda")
+
+
+@pytest.mark.parametrize("mode", [F64_EMU, F32])
+def test_batched_dev_graph_replay_on_new_buffers(ata, mode):
+    """Device-resident pointer arrays (ata_batched_dev): one call captured in
+    a CUDA graph, the arrays rewritten with a second set of buffers of the same
+    shapes, the graph replayed: the second set gets its products (oracle
+    parity, and the same bits as the host-array form), the first set is not
+    touched.  Problems with m == 0 are zero-filled through the device table."""
+    extra = [(0, 5), (1, 130), (97, 257)]
+    As1 = make_batch(30, 41, mode, m_range=(16, 900), n_range=(8, 300), extra=extra)
+    As2 = make_batch(30, 41, mode, m_range=(16, 900), n_range=(8, 300), extra=extra)
+    As2 = [a * 0.75 - 0.125 for a in As2]   # same shapes, other values
+    A1, C1 = to_dev(As1, mode)
+    A2, C2 = to_dev(As2, mode)
+    ms = [a.shape[0] for a in As1]
+    ns = [a.shape[1] for a in As1]
+    ldas = [max(n, 1) for n in ns]
+    ta, tc = ptr_table(A1), ptr_table(C1)
+    hd = ata.Handle(depth=0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    assert hd.batched_dev_ptr(ms, ns, ta.data_ptr(), ldas, tc.data_ptr(), ldas, mode, s) == 0  # plan + workspace
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert hd.batched_dev_ptr(ms, ns, ta.data_ptr(), ldas, tc.data_ptr(), ldas, mode, s) == 0
+    for c in C1:
+        c.fill_(float("nan"))
+    ta.copy_(ptr_table(A2))
+    tc.copy_(ptr_table(C2))
+    g.replay()
+    torch.cuda.synchronize()
+    assert hd.sync() == 0
+    for c in C1:
+        assert bool(torch.isnan(c).all())
+    for A, Ct in zip(As2, C2):
+        n = A.shape[1]
+        C = Ct.cpu().numpy().astype(np.float64)
+        if A.shape[0] == 0:
+            assert np.all(C[np.tril_indices(n)] == 0)
+            continue
+        check_against_oracle(A, C, mode)
+    # the host-array form on the same buffers gives the same bits
+    C3 = [torch.full_like(c, float("nan")) for c in C2]
+    hd.batched(A2, C3, mode)
+    assert hd.sync() == 0
+    for a, b in zip(C2, C3):
+        assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0))
+    hd.close()
+
+
+def test_batched_host_form_follows_new_pointers(h):
+    """The plan is keyed on shapes only: a second call with other buffers of
+    the same shapes reuses it and writes the new buffers."""
+    mode = F32
+    As1 = make_batch(25, 77, mode, m_range=(16, 600), n_range=(8, 200))
+    As2 = [a[::-1].copy() for a in As1]
+    A1, C1 = to_dev(As1, mode)
+    A2, C2 = to_dev(As2, mode)
+    h.batched(A1, C1, mode)
+    h.batched(A2, C2, mode)
+    assert h.sync() == 0
+    for A, Ct in list(zip(As1, C1)) + list(zip(As2, C2)):
+        check_against_oracle(A, Ct.cpu().numpy().astype(np.float64), mode)
+
+
+def test_batched_full_workload_sampled(ata):
+    """The benchmarked batch: 4096 FP32 problems, m log-uniform in [64, 4096],
+    n log-uniform in [32, 1024], U[-1, 1) drawn on the device.  For every
+    problem: both corners of the diagonal, the last row (first and last
+    column), the first column of the last row block, and three random lower
+    entries, against the oracle at 5e-5 of (|A|^T|A|)_jk."""
+    count, seed = 4096, 2110
+    ms, ns = inputs.batch_shapes(count, seed, (64, 4096), (32, 1024))
+    ms, ns = [int(v) for v in ms], [int(v) for v in ns]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    abuf = torch.rand(sum(a * b for a, b in zip(ms, ns)), generator=g, device="cuda") * 2 - 1
+    cbuf = torch.full((sum(b * b for b in ns),), float("nan"), device="cuda")
+    As, Cs, oa, oc = [], [], 0, 0
+    for a, b in zip(ms, ns):
+        As.append(abuf[oa:oa + a * b].view(a, b))
+        Cs.append(cbuf[oc:oc + b * b].view(b, b))
+        oa += a * b
+        oc += b * b
+    hb = ata.Handle(depth=0)
+    hb.batched(As, Cs, F32)
+    assert hb.sync() == 0
+    hb.close()
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        j = [0, n - 1, n - 1, n - 1, n - 1]
+        k = [0, n - 1, 0, max(0, n - 129), n // 2]
+        for _ in range(3):
+            jj = int(rng.integers(0, n))
+            j.append(jj)
+            k.append(int(rng.integers(0, jj + 1)))
+        j, k = np.array(j), np.array(k)
+        cols = torch.from_numpy(np.concatenate([j, k])).cuda()
+        X = As[i][:, cols].double().cpu().numpy()
+        got = Cs[i][torch.from_numpy(j).cuda(), torch.from_numpy(k).cuda()].double().cpu().numpy()
+        ref, den = oracle.dot_pairs(np.ascontiguousarray(X[:, :len(j)].T), np.ascontiguousarray(X[:, len(j):].T))
+        err = np.abs(got - ref) / den
+        worst = max(worst, float(np.max(err)))
+        assert np.all(err <= 5e-5), (i, m, n, float(np.max(err)))
+    assert worst > 0  # the FP32 mode is not exact on random data
