@@ -36,6 +36,8 @@ sys.path.insert(0, ROOT)
 METRIC = "A^T A effective TFLOP/s (m·n² eq.) vs plain tiled AtA on GB300 at stated error"
 UNIT = "TFLOP/s"
 MODES = {"f64": 0, "f64_emu": 1, "f32": 2, "f32_bf16": 4, "f32_fp8": 5}
+DIST_DESC = {"uniform": "U[-1,1)", "colscaled": "N(0,1) x 10^U(-3,3) per column",
+             "lowrank": "U[-1,1) + 1e4 x rank-16 G1 G2^T / 4"}
 DTYPE_DESC = {0: "f64 (DMMA)", 1: "bf16 digits x fp32 acc -> int64 (fp64-accurate)",
               2: "bf16 digits x fp32 acc -> int64 (fp32-accurate)", 4: "bf16 x fp32",
               5: "e4m3 x fp32"}
@@ -54,6 +56,10 @@ def parse():
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--seed", type=int, default=2110)
+    ap.add_argument("--dist", default="uniform", choices=list(DIST_DESC),
+                    help="entries: U[-1,1); N(0,1) x 10^U(-3,3) per column; U[-1,1) + rank-16 part of size 1e4")
+    ap.add_argument("--device-inputs", action="store_true",
+                    help="draw A on the device (seeded torch generator) instead of on the host")
     ap.add_argument("--no-extras", action="store_true", help="skip plain-tiled, e2e, batched, cpu baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (auto plan instead)")
     ap.add_argument("--tune-budget-ms", type=float, default=3000.0)
@@ -61,6 +67,9 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only ata_batched on the batched workload (one JSON object; for its profiles)")
     ap.add_argument("--ref-seconds", type=float, default=4.0, help="CPU seconds per reference step")
+    ap.add_argument("--dense-peaks", action="store_true",
+                    help="only time cuBLAS FP64 and TF32 GEMMs (torch.matmul, 8192^3, best of 5): the FP64 "
+                         "and TF32 peaks the driver does not measure")
     return ap.parse_args()
 
 
@@ -188,6 +197,20 @@ def leaf_traffic(mode, m, n, depth, slices):
     return None
 
 
+def fp64_peak():
+    """FP64 dense peak: not among the driver's measured peaks, so it is the
+    cuBLAS DGEMM rate measured on this machine's GB300 and committed in
+    profiles/fp64_peak.json (with its command), else the nominal FP64 / BF16
+    ratio (1.25 / 2250) times the measured BF16 sustained peak."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_peak.json")) as f:
+            d = json.load(f)
+        return float(d["dgemm_tflops"]), "measured cuBLAS DGEMM (profiles/fp64_peak.json)"
+    except (OSError, ValueError, KeyError):
+        peaks, src = measured_peaks()
+        return float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1.25 / 2250.0, f"{src} bf16 x nominal fp64/bf16"
+
+
 def batched_bench(ata, torch, dev, stream, args, timed):
     """Many independent Gram products: count FP32 problems with m log-uniform
     in [64, 4096] and n log-uniform in [32, 1024], entries U[-1, 1) drawn on
@@ -226,17 +249,19 @@ def batched_bench(ata, torch, dev, stream, args, timed):
     hb.close()
     if rc:
         raise RuntimeError(f"batched bench: status {rc}")
-    return {"metric": "batched A_i^T A_i effective TFLOP/s (sum m n^2)", "unit": "TFLOP/s",
-            "value": eff / (ms_b * 1e-3) / 1e12, "ms": ms_b, "problems": count,
-            "workload": f"{count} FP32 problems, m logU[64,4096], n logU[32,1024], U[-1,1) on device (seed {args.seed})",
-            "one_launch_per_matrix": ({"value": eff / (ms_p * 1e-3) / 1e12, "ms": ms_p} if ms_p else None),
-            "a_bytes": int(abuf.numel() * 4), "c_bytes": int(cbuf.numel() * 4)}
+    res = {"metric": "batched A_i^T A_i effective TFLOP/s (sum m n^2)", "unit": "TFLOP/s",
+           "value": eff / (ms_b * 1e-3) / 1e12, "ms": ms_b, "problems": count,
+           "workload": f"{count} FP32 problems, m logU[64,4096], n logU[32,1024], U[-1,1) on device (seed {args.seed})",
+           "one_launch_per_matrix": ({"value": eff / (ms_p * 1e-3) / 1e12, "ms": ms_p} if ms_p else None),
+           "a_bytes": int(abuf.numel() * 4), "c_bytes": int(cbuf.numel() * 4)}
+    return res, (As, Cs)
 
 
 def cpu_oracle_sample(A_cols_fn, m, n, target_s, threads=0):
-    """Time the oracle (plain definition, all host cores) on the leading
-    column panel of the workload, sized to take about target_s seconds.
-    Returns (effective TFLOP/s, seconds, cores, description)."""
+    """Time the oracle (plain definition) on the leading column panel of the
+    workload, sized to take about target_s seconds, on `threads` host threads
+    (0 = all cores).  Returns (effective TFLOP/s, seconds, cores, description,
+    (panel width, the oracle's low(C) of the panel))."""
     import oracle
     cores = oracle.set_threads(threads)
     nb = 64
@@ -248,11 +273,44 @@ def cpu_oracle_sample(A_cols_fn, m, n, target_s, threads=0):
     nb = int(min(n, max(64, nb * (target_s / dt) ** 0.5)))
     A = A_cols_fn(nb)
     t0 = time.perf_counter()
-    oracle.ata_lower(A)
+    ref = oracle.ata_lower(A)
     dt = time.perf_counter() - t0
+    oracle.set_threads(0)
     work = float(m) * nb * (nb + 1)  # 2 flops per multiply-add of the lower triangle
     desc = f"low(A[:, :{nb}]^T A[:, :{nb}]) of the {m}x{n} workload ({nb * (nb + 1) // 2} entries)"
-    return work / dt / 1e12, dt, cores, desc
+    return work / dt / 1e12, dt, cores, desc, (nb, ref)
+
+
+def cpu_baseline_leg(A_cols_fn, m, n, C, batch, torch):
+    """The oracle on the host cores: its timing (all cores, then one thread)
+    on bounded column panels of the workload, and, from the same oracle
+    values, the error of the GPU's result on that panel; plus the error of 32
+    sampled problems of the batched leg."""
+    import oracle
+    v, dt, cores, desc, (nb, ref) = cpu_oracle_sample(A_cols_fn, m, n, 12.0)
+    A = A_cols_fn(nb)
+    D = oracle.abs_ata_lower(A)
+    got = C[:nb, :nb].double().cpu().numpy()
+    low = np.tril_indices(nb)
+    err = float(np.max(np.abs(got[low] - ref[low]) / np.where(D[low] > 0, D[low], 1.0)))
+    v1, dt1, _, desc1, _ = cpu_oracle_sample(A_cols_fn, m, n, 6.0, threads=1)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt,
+           "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1, "seconds": dt1}}
+    error = {"max_rel_to_absAtA": err, "entries": int(nb * (nb + 1) // 2),
+             "sample": f"the oracle's panel low(A[:, :{nb}]^T A[:, :{nb}])"}
+    berr = None
+    if batch is not None:
+        As, Cs = batch
+        rng = np.random.default_rng(7)
+        worst = 0.0
+        for i in rng.choice(len(As), size=min(32, len(As)), replace=False):
+            Ai = As[i].double().cpu().numpy()
+            r, Di = oracle.ata_lower(Ai), oracle.abs_ata_lower(Ai)
+            gi = Cs[i].double().cpu().numpy()
+            lw = np.tril_indices(Ai.shape[1])
+            worst = max(worst, float(np.max(np.abs(gi[lw] - r[lw]) / np.where(Di[lw] > 0, Di[lw], 1.0))))
+        berr = {"max_rel_to_absAtA": worst, "problems": min(32, len(As)), "sample": "32 random problems, every lower entry"}
+    return out, error, berr
 
 
 # -------------------------------------------------------------- reference --
@@ -267,7 +325,7 @@ def run_reference(args, rank, world):
     cores = 0
     desc = ""
     for it in range(args.warmup + args.steps):
-        v, dt, cores, desc = cpu_oracle_sample(cols_fn, m, n, args.ref_seconds)
+        v, dt, cores, desc, _ = cpu_oracle_sample(cols_fn, m, n, args.ref_seconds)
         if it >= args.warmup:
             vals.append(v)
             times.append(dt)
@@ -314,6 +372,30 @@ def main():
     import paper_2110_13042_gb300 as ata
     from paper_2110_13042_gb300 import inputs
 
+    if args.dense_peaks:
+        out = {}
+        for name, dt in (("f64", torch.float64), ("tf32", torch.float32)):
+            torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+            nd = 8192
+            a = torch.randn(nd, nd, dtype=dt, device=dev)
+            b = torch.randn(nd, nd, dtype=dt, device=dev)
+            for _ in range(2):
+                a @ b
+            best = None
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                a @ b
+                e1.record()
+                torch.cuda.synchronize(dev)
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            out[name] = {"n": nd, "ms": best, "tflops": 2.0 * nd ** 3 / (best * 1e-3) / 1e12}
+        torch.backends.cuda.matmul.allow_tf32 = False
+        print(json.dumps(out))
+        return
+
     if args.batched_only:
         bstream = torch.cuda.current_stream(dev)
 
@@ -329,16 +411,25 @@ def main():
             e1.record(bstream)
             torch.cuda.synchronize(dev)
             return e0.elapsed_time(e1) / k
-        print(json.dumps(batched_bench(ata, torch, dev, bstream, args, timed_b)))
+        print(json.dumps(batched_bench(ata, torch, dev, bstream, args, timed_b)[0]))
         return
 
     m, n, mode = args.m, args.n, MODES[args.mode]
     f32 = mode in (2, 4, 5)
     tdt = torch.float32 if f32 else torch.float64
-    A_host = inputs.uniform(m, n, args.seed + rank)
-    if f32:
-        A_host = A_host.astype(np.float32)
-    A = torch.from_numpy(A_host).to(dev)
+    seed = args.seed + rank
+    host_gen = {"uniform": inputs.uniform, "colscaled": inputs.column_scaled_normal,
+                "lowrank": inputs.low_rank_stressed}[args.dist]
+    dev_gen = {"uniform": inputs.device_uniform, "colscaled": inputs.device_column_scaled_normal,
+               "lowrank": inputs.device_low_rank_stressed}[args.dist]
+    if args.device_inputs:
+        A = dev_gen(m, n, seed, dev).to(tdt)
+        A_host = None
+    else:
+        A_host = host_gen(m, n, seed)
+        if f32:
+            A_host = A_host.astype(np.float32)
+        A = torch.from_numpy(A_host).to(dev)
     C = torch.zeros((n, n), dtype=tdt, device=dev)
     h = ata.Handle(cutoff=args.cutoff, depth=args.depth, slices=args.slices)
     stream = torch.cuda.current_stream(dev)
@@ -396,11 +487,11 @@ def main():
     slices = info["slices"]
     pairs = slices * (slices + 1) // 2 if mode != 0 else 1
     if mode == 0:
-        roof = {"bound": "tensor", "kernel": "leaf_f64_kernel (DMMA)", "achieved": None,
-                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "note": "FP64 peak not in MEASURED_PEAKS.json"}
         achieved = 2.0 * info["leaf_madds"] / (ph[2] * 1e-3) / 1e12
-        roof["achieved"] = achieved
+        p64, p64_src = fp64_peak()
+        roof = {"bound": "tensor", "kernel": "leaf_f64_kernel (DMMA)", "achieved": achieved,
+                "peak": p64, "unit": "TFLOP/s", "frac": achieved / p64 if p64 else None, "traffic": None,
+                "peak_source": p64_src}
     else:
         leaf_flops = 2.0 * pairs * info["leaf_madds"]
         achieved = leaf_flops / (ph[2] * 1e-3) / 1e12
@@ -420,12 +511,14 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPE_DESC[mode], "data": "synthetic",
-           "config": {"workload": f"A {m}x{n} {'FP32' if f32 else 'FP64'} U[-1,1) (seed {args.seed}), "
+           "config": {"workload": f"A {m}x{n} {'FP32' if f32 else 'FP64'} {DIST_DESC[args.dist]} (seed {args.seed}"
+                                  f"{', drawn on the device' if args.device_inputs else ''}), "
                                   "lower triangle of C = A^T A",
                       "mode": args.mode.upper(), "strassen_depth": info["depth"],
                       "cutoff": info["cutoff"], "slices": slices,
                       "plan": "autotuned (ata_tune)" if tuned else "fixed",
-                      "l2": "inputs larger than L2 (A and C 512 MiB each)"},
+                      "l2": f"inputs larger than L2 (A {A.numel() * A.element_size() / 2**20:.0f} MiB, "
+                            f"C {C.numel() * C.element_size() / 2**20:.0f} MiB)"},
            "roofline": roof,
            "phases_ms": {"colexp": ph[0], "prep": ph[1], "leaf": ph[2], "combine": ph[3]},
            "gpu_launches": args.steps * (4 + (1 if info["products"] else 0)),
@@ -443,7 +536,7 @@ def main():
         # back.  Steps are pipelined over two device buffers and a copy
         # stream (step i+1's upload and step i's download overlap step i's
         # compute), as a serving loop would run them.
-        A_pin = torch.from_numpy(A_host).pin_memory()
+        A_pin = (torch.from_numpy(A_host) if A_host is not None else A.cpu()).pin_memory()
         C_pin = [torch.empty((n, n), dtype=tdt).pin_memory() for _ in range(2)]
         A_dev = [A, torch.empty_like(A)]
         C_dev = [C, torch.empty_like(C)]
@@ -481,27 +574,24 @@ def main():
         torch.cuda.synchronize(dev)
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
         out["e2e"] = {"value": world * eff / (ms_e2e * 1e-3) / 1e12, "unit": UNIT,
-                      "h2d_bytes_per_step": A_host.nbytes, "d2h_bytes_per_step": C.numel() * C.element_size(),
+                      "h2d_bytes_per_step": A_pin.numel() * A_pin.element_size(),
+                      "d2h_bytes_per_step": C.numel() * C.element_size(),
                       "ms_per_step": ms_e2e, "pipelined": "2 buffers, copy stream"}
         del A_dev[1], C_dev[1]
-        # accuracy of the timed configuration on sampled entries
-        import oracle
-        rng = np.random.default_rng(0)
-        j = rng.integers(0, n, 400)
-        k = (rng.random(400) * (j + 1)).astype(np.int64)
-        h.lower(A, C, mode, stream)
-        torch.cuda.synchronize(dev)
-        got = C[torch.from_numpy(j).to(dev), torch.from_numpy(k).to(dev)].double().cpu().numpy()
-        A64 = np.asarray(A_host, np.float64)
-        ref, den = oracle.dot_pairs(np.ascontiguousarray(A64[:, j].T), np.ascontiguousarray(A64[:, k].T))
-        out["error_vs_oracle"] = {"max_rel_to_absAtA": float(np.max(np.abs(got - ref) / den)),
-                                  "samples": 400}
-        out["batched"] = batched_bench(ata, torch, dev, stream, args, timed)
+        res, batch = batched_bench(ata, torch, dev, stream, args, timed)
+        out["batched"] = res
         if rank == 0 and world == 1:
-            v, dt, cores, desc = cpu_oracle_sample(
-                lambda nb: np.ascontiguousarray(A64[:, :nb]), m, n, 12.0)
-            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": desc, "seconds": dt}
+            # the oracle's leg: its CPU time, and the GPU's error on the oracle's own values
+            if A_host is not None:
+                A64 = np.asarray(A_host, np.float64)
+                cols_fn = (lambda nb: np.ascontiguousarray(A64[:, :nb]))
+            else:
+                cols_fn = (lambda nb: A[:, :nb].double().cpu().numpy())
+            cpu, err, berr = cpu_baseline_leg(cols_fn, m, n, C, batch, torch)
+            out["cpu_baseline"] = cpu
+            out["error_vs_oracle"] = err
+            out["batched"]["error_vs_oracle"] = berr
+        del batch
     h.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
