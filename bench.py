@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--depth", type=int, default=-1)
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--strassen-min", type=int, default=0)
+    ap.add_argument("--variant", default="strassen", choices=["strassen", "winograd"])
     ap.add_argument("--seed", type=int, default=2110)
     ap.add_argument("--dist", default="uniform", choices=list(DIST_DESC),
                     help="entries: U[-1,1); N(0,1) x 10^U(-3,3) per column; U[-1,1) + rank-16 part of size 1e4")
@@ -431,10 +433,12 @@ def main():
             A_host = A_host.astype(np.float32)
         A = torch.from_numpy(A_host).to(dev)
     C = torch.zeros((n, n), dtype=tdt, device=dev)
-    h = ata.Handle(cutoff=args.cutoff, depth=args.depth, slices=args.slices)
+    variant = 1 if args.variant == "winograd" else 0
+    h = ata.Handle(cutoff=args.cutoff, depth=args.depth, slices=args.slices, strassen_min=args.strassen_min,
+                   variant=variant)
     stream = torch.cuda.current_stream(dev)
     tuned = None
-    if args.depth < 0 and args.cutoff == 0 and not args.no_tune:
+    if args.depth < 0 and args.cutoff == 0 and args.strassen_min == 0 and not args.no_tune:
         # autotuned plan for this shape (outside every timed region)
         tuned = h.tune(A, C, mode, stream, budget_ms=args.tune_budget_ms)
     info = ata.plan_info(m, n, mode, h)
@@ -515,7 +519,7 @@ def main():
                                   f"{', drawn on the device' if args.device_inputs else ''}), "
                                   "lower triangle of C = A^T A",
                       "mode": args.mode.upper(), "strassen_depth": info["depth"],
-                      "cutoff": info["cutoff"], "slices": slices,
+                      "cutoff": info["cutoff"], "slices": slices, "variant": args.variant,
                       "plan": "autotuned (ata_tune)" if tuned else "fixed",
                       "l2": f"inputs larger than L2 (A {A.numel() * A.element_size() / 2**20:.0f} MiB, "
                             f"C {C.numel() * C.element_size() / 2**20:.0f} MiB)"},

@@ -90,13 +90,26 @@ typedef struct {
                             (Algorithm 1 base case); 0 = auto                     */
     int strassen_depth;  /* Strassen levels on every off-diagonal block
                             (0 = classical tiles, i.e. plain tiled AtA);
-                            -1 = auto                                              */
+                            -1 = auto.  At most ATA_MAX_STRASSEN_DEPTH; a
+                            level splits a block only while both its sides
+                            are >= strassen_min, so ATA_MAX_STRASSEN_DEPTH
+                            recurses Strassen down to that size cutoff, as
+                            the paper's FastStrassen recurses to its base
+                            case (Section 3.1, Algorithm 1)                       */
     int slices;          /* digits per column for ATA_F64_EMU (1..7); 0 = auto    */
     int strassen_min;    /* a Strassen level splits an off-diagonal (sub)block
                             only while both its sides are >= strassen_min
                             columns; 0 = auto                                      */
-    int reserved[4];     /* must be zero                                          */
+    int strassen_variant;/* ATA_STRASSEN (0, Strassen's products, the paper's
+                            choice) or ATA_WINOGRAD (1, Winograd's variant of
+                            the seven products); ATA_F32_FP8 always uses
+                            Strassen's                                             */
+    int reserved[3];     /* must be zero                                          */
 } ata_config;
+
+#define ATA_MAX_STRASSEN_DEPTH 8
+#define ATA_STRASSEN 0
+#define ATA_WINOGRAD 1
 
 typedef struct ata_handle_s *ata_handle;
 

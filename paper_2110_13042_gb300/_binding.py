@@ -85,11 +85,11 @@ def version() -> int:
 class Config(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int), ("strassen_depth", ctypes.c_int),
                 ("slices", ctypes.c_int), ("strassen_min", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("strassen_variant", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
-def _config(cutoff=0, depth=-1, slices=0, strassen_min=0) -> Config:
-    return Config(int(cutoff), int(depth), int(slices), int(strassen_min), (ctypes.c_int * 4)())
+def _config(cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0) -> Config:
+    return Config(int(cutoff), int(depth), int(slices), int(strassen_min), int(variant), (ctypes.c_int * 3)())
 
 
 def _check(rc: int, what: str):
@@ -134,14 +134,14 @@ def _stream_ptr(stream):
 class Handle:
     """Owns an ``ata_handle`` (workspace, plan cache, device status word)."""
 
-    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0):
+    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0):
         L = load()
         self._h = ctypes.c_void_p()
-        cfg = _config(cutoff, depth, slices, strassen_min)
+        cfg = _config(cutoff, depth, slices, strassen_min, variant)
         _check(L.ata_create(ctypes.byref(self._h), ctypes.byref(cfg)), "ata_create")
 
-    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0):
-        cfg = _config(cutoff, depth, slices, strassen_min)
+    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0):
+        cfg = _config(cutoff, depth, slices, strassen_min, variant)
         _check(load().ata_set_config(self._h, ctypes.byref(cfg)), "ata_set_config")
 
     def lower_ptr(self, m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:

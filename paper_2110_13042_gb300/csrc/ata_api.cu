@@ -89,8 +89,9 @@ namespace {
 
 int check_config(const ata_config *c) {
     if (!c) return ATA_OK;
-    if (c->cutoff < 0 || c->strassen_depth < -1 || c->strassen_depth > 4 || c->slices < 0 ||
-        c->slices > MAX_SLICES || c->strassen_min < 0)
+    if (c->cutoff < 0 || c->strassen_depth < -1 || c->strassen_depth > ATA_MAX_STRASSEN_DEPTH || c->slices < 0 ||
+        c->slices > MAX_SLICES || c->strassen_min < 0 ||
+        (c->strassen_variant != ATA_STRASSEN && c->strassen_variant != ATA_WINOGRAD))
         return ATA_ERR_INVALID;
     for (int r : c->reserved)
         if (r != 0) return ATA_ERR_INVALID;
@@ -108,6 +109,7 @@ PlanParams params_for(const ata_config &cfg, int64_t m, int64_t n, int64_t lda, 
     pp.depth = cfg.strassen_depth;
     pp.slices = cfg.slices;
     pp.strassen_min = cfg.strassen_min;
+    pp.variant = cfg.strassen_variant;
     return pp;
 }
 
@@ -187,7 +189,7 @@ ata_config effective_cfg(ata_handle h, int64_t m, int64_t n, int dtype) {
 
 CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
     Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices, pp.strassen_min,
-            pp.trans | (pp.packed << 1)};
+            pp.trans | (pp.packed << 1) | (pp.variant << 2)};
     auto it = h->plans.find(key);
     if (it != h->plans.end()) return it->second.get();
     std::unique_ptr<CachedPlan> cp(new CachedPlan());

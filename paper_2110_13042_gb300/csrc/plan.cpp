@@ -44,6 +44,23 @@ const int kV[7][4] = {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0},
 const int kW[7][4] = {{1, 0, 0, 1}, {0, 0, 1, -1}, {0, 1, 0, 1}, {1, 0, 1, 0},
                       {-1, 1, 0, 0}, {0, 0, 0, 1}, {1, 0, 0, 0}};
 
+// Winograd's variant (7 products, 15 block additions when the sums are
+// chained: Winograd 1971), written out for C = X^T Y in the same indexing.
+// With S1 = X12 + X22, S2 = S1 - X11, S3 = X11 - X12, S4 = X21 - S2 and
+// T1 = Y12 - Y11, T2 = Y22 - T1, T3 = Y22 - Y12, T4 = T2 - Y21:
+//   M1 = X11^T Y11   M2 = X21^T Y21   M3 = S4^T Y22   M4 = X22^T T4
+//   M5 = S1^T T1     M6 = S2^T T2     M7 = S3^T T3
+//   C11 = M1 + M2              C12 = M1 + M6 + M5 + M3
+//   C21 = M1 + M6 + M7 - M4    C22 = M1 + M6 + M7 + M5
+// Here every operand is formed directly from the quadrants (the chained
+// sums flattened), so an operand has up to four terms.
+const int wU[7][4] = {{1, 0, 0, 0}, {0, 0, 1, 0}, {1, -1, 1, -1}, {0, 0, 0, 1},
+                      {0, 1, 0, 1}, {-1, 1, 0, 1}, {1, -1, 0, 0}};
+const int wV[7][4] = {{1, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}, {1, -1, -1, 1},
+                      {-1, 1, 0, 0}, {1, -1, 0, 1}, {0, -1, 0, 1}};
+const int wW[7][4] = {{1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0},
+                      {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1}};
+
 struct Region {
     int64_t off, ext;
 };
@@ -84,6 +101,10 @@ struct Builder {
     bool fp8;    // one E4M3 plane per operand, FP32 accumulation
     int kalign;  // contraction rows of one leaf K step
     bool reuse_quadrants = true;
+    // coefficient tables of the chosen variant (Strassen or Winograd)
+    const int (*tU)[4] = kU;
+    const int (*tV)[4] = kV;
+    const int (*tW)[4] = kW;
     int64_t prod_elems = 0;
 
     explicit Builder(Plan &p)
@@ -244,8 +265,8 @@ struct Builder {
                     int cu = 1, cv = 1;
                     for (int l = 0; l < d; ++l) {
                         int quad = 2 * bit(ia, l, d) + bit(ib, l, d);
-                        cu *= kU[digit[l]][quad];
-                        cv *= kV[digit[l]][quad];
+                        cu *= tU[digit[l]][quad];
+                        cv *= tV[digit[l]][quad];
                     }
                     if (cu != 0)
                         ut.push_back({kreg[ia].off, r0 + preg[ib].off,
@@ -311,7 +332,7 @@ struct Builder {
                     for (int l = d - 1; l >= 0; --l) {
                         int dg = static_cast<int>(rr % 7);
                         rr /= 7;
-                        w *= kW[dg][2 * bit(ir, l, d) + bit(ic, l, d)];
+                        w *= tW[dg][2 * bit(ir, l, d) + bit(ic, l, d)];
                     }
                     if (w != 0)
                         P.cterms.push_back({prod_off[r], static_cast<int32_t>(qn), w, prod_shift[r], 0});
@@ -578,7 +599,13 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         return false;
     }
     P.depth = pp.depth >= 0 ? pp.depth : (pp.n >= 4096 ? 1 : 0);
-    if (P.depth > 4) P.depth = 4;
+    if (P.depth > MAX_STRASSEN_DEPTH) P.depth = MAX_STRASSEN_DEPTH;
+    if (pp.variant != VARIANT_STRASSEN && pp.variant != VARIANT_WINOGRAD) {
+        if (err) *err = "unknown Strassen variant";
+        return false;
+    }
+    // The FP8 mode's stated bounds are Strassen's: it always uses Strassen.
+    P.variant = pp.mode == MODE_F32_FP8 ? VARIANT_STRASSEN : pp.variant;
     if (P.depth == 0)
         P.cutoff = static_cast<int>(std::max<int64_t>(pp.n, 1));
     else
@@ -593,6 +620,11 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     }
 
     Builder B(P);
+    if (P.variant == VARIANT_WINOGRAD) {
+        B.tU = wU;
+        B.tV = wV;
+        B.tW = wW;
+    }
     if (B.digits) {
         // Family 0: digit planes of A itself (diagonal panels, classical tiles).
         Family f0{};

@@ -32,6 +32,11 @@ constexpr int PREP_TK = KSTEP;
 constexpr int PREP_TC = 256;
 constexpr int MAX_FAMILIES = 6;  // operand families (tensor maps) per launch
 constexpr int MAX_SLICES = 7;
+// Strassen levels per off-diagonal block: a budget; a level splits a block
+// only while both its sides are >= strassen_min, so a large budget recurses
+// to that size cutoff (the paper's FastStrassen recursion to its base case).
+constexpr int MAX_STRASSEN_DEPTH = 8;
+enum Variant : int { VARIANT_STRASSEN = 0, VARIANT_WINOGRAD = 1 };
 
 enum Mode : int { MODE_F64 = 0, MODE_F64_EMU = 1, MODE_F32 = 2, MODE_F32_BF16 = 4, MODE_F32_FP8 = 5 };
 
@@ -216,6 +221,7 @@ struct PlanParams {
                              // of the m x n operand at A[j * lda + i], lda >= m
     int packed = 0;          // 1: C is stored as a packed lower triangle, entry
                              // (j, k) at j (j + 1) / 2 + k (ldc unused)
+    int variant = VARIANT_STRASSEN;  // coefficient tables of the off-diagonal products
 };
 
 // Element offset of entry (j, k), k <= j, of a packed lower triangle.
@@ -223,7 +229,7 @@ inline int64_t packed_index(int64_t j, int64_t k) { return j * (j + 1) / 2 + k; 
 
 struct Plan {
     PlanParams p;
-    int cutoff = 0, depth = 0, slices = 0, strassen_min = 0;
+    int cutoff = 0, depth = 0, slices = 0, strassen_min = 0, variant = VARIANT_STRASSEN;
     int64_t n_panels = 0, n_blocks = 0, n_products = 0;
     int64_t n_reused = 0;  // Strassen operands read from the planes of A
     int64_t n_tiles = 0;   // leaf tiles (tasks also holds empty balance fillers)

@@ -26,6 +26,7 @@ int main(int argc, char **argv) {
     pp.strassen_min = argc > 7 ? std::atoi(argv[7]) : 1;
     pp.split_search = argc > 8 ? std::atoi(argv[8]) : 1;
     pp.num_ctas = argc > 9 ? std::atoi(argv[9]) : 0;
+    pp.variant = argc > 10 ? std::atoi(argv[10]) : 0;
     Plan P;
     std::string err;
     if (!make_plan(pp, &P, &err)) {

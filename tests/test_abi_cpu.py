@@ -101,9 +101,9 @@ def plan_cli(lib):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", os.path.dirname(src), src, plan_cpp, "-o", out],
                    check=True)
 
-    def run(m, n, mode, cutoff, depth, slices=0, strassen_min=1, split_search=1, num_ctas=0):
+    def run(m, n, mode, cutoff, depth, slices=0, strassen_min=1, split_search=1, num_ctas=0, variant=0):
         r = subprocess.run([out, str(m), str(n), str(mode), str(cutoff), str(depth), str(slices),
-                            str(strassen_min), str(split_search), str(num_ctas)],
+                            str(strassen_min), str(split_search), str(num_ctas), str(variant)],
                            capture_output=True, text=True, check=True)
         return {k: int(v) for k, v in (kv.split("=") for kv in r.stdout.split())}
     return run
@@ -277,3 +277,36 @@ def test_plan_blocks_describe_the_recursion(lib, m, n, mode):
     # the rest of the lower triangle is diagonal panels (w (w + 1) / 2 each)
     assert covered < n * (n + 1) // 2
     assert any(d > 0 for *_, d in blocks) == (info["products"] > 0)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin", [
+    (300, 257, 1, 32, 1, 2), (1000, 1000, 1, 0, 2, 64), (777, 901, 2, 64, 3, 64),
+    (2000, 3001, 1, 0, 8, 64), (129, 515, 0, 0, 8, 16), (513, 700, 5, 100, 2, 2)])
+def test_variants_and_recursion_to_cutoff_cover_the_triangle(plan_cli, variant, m, n, mode, cutoff, depth, smin):
+    """Strassen's and Winograd's tables, and a depth budget large enough that
+    only the size cutoff (strassen_min) stops the recursion: every lower
+    entry produced exactly once, prep and combine maps consistent, and every
+    Strassen block split while both its sides reach strassen_min."""
+    r = plan_cli(m, n, mode, cutoff, depth, strassen_min=smin, variant=variant)
+    assert r["covered"] == n * (n + 1) // 2 and r["overlap"] == 0
+    assert r["prep_map_ok"] == 1 and r["comb_map_ok"] == 1
+    assert r["products"] > 0
+
+
+def test_winograd_products_and_terms(plan_cli):
+    """Same product count per level (7); Winograd's result sums have more
+    terms (2 + 4 + 4 + 4 = 14 per level against Strassen's 4 + 2 + 2 + 4 = 12)."""
+    s = plan_cli(1024, 1024, 1, 0, 1, strassen_min=64, split_search=0, variant=0)
+    w = plan_cli(1024, 1024, 1, 0, 1, strassen_min=64, split_search=0, variant=1)
+    assert s["products"] == w["products"] == 7 * s["blocks"]
+    assert s["cterms"] * 14 == w["cterms"] * 12
+
+
+def test_recursion_to_cutoff_depth(plan_cli):
+    """Depth budget 8 with strassen_min 256 on a 4096-column problem with the
+    default cutoff (1024): the top block (2048 wide) splits while both sides
+    are >= 256: 2048 -> 1024 -> 512 -> 256 -> 128, four levels."""
+    r = plan_cli(4096, 4096, 1, 0, 8, strassen_min=256, split_search=0)
+    assert r["depth"] == 8
+    assert r["products"] >= 7 ** 4
