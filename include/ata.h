@@ -104,7 +104,16 @@ typedef struct {
                             choice) or ATA_WINOGRAD (1, Winograd's variant of
                             the seven products); ATA_F32_FP8 always uses
                             Strassen's                                             */
-    int reserved[3];     /* must be zero                                          */
+    int streams;         /* 0 or 1: every leaf tile of the recursion in one
+                            persistent launch (the default); 2..16: a static
+                            partition of the recursion's units (diagonal
+                            panels, classical blocks, Strassen products) over
+                            that many leaf launches on their own streams,
+                            forked from and joined back into the caller's
+                            stream: the counterpart of the paper's static
+                            task tree of AtA-S (Section 4.1-4.2, Algorithm
+                            3).  Results are bit-identical either way.         */
+    int reserved[2];     /* must be zero                                          */
 } ata_config;
 
 #define ATA_MAX_STRASSEN_DEPTH 8

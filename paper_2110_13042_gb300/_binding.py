@@ -85,11 +85,12 @@ def version() -> int:
 class Config(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int), ("strassen_depth", ctypes.c_int),
                 ("slices", ctypes.c_int), ("strassen_min", ctypes.c_int),
-                ("strassen_variant", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("strassen_variant", ctypes.c_int), ("streams", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
-def _config(cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0) -> Config:
-    return Config(int(cutoff), int(depth), int(slices), int(strassen_min), int(variant), (ctypes.c_int * 3)())
+def _config(cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0) -> Config:
+    return Config(int(cutoff), int(depth), int(slices), int(strassen_min), int(variant), int(streams),
+                  (ctypes.c_int * 2)())
 
 
 def _check(rc: int, what: str):
@@ -131,17 +132,30 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
+def _ld(T) -> int:
+    """Leading dimension of a row-major 2-D tensor.  A tensor with a single
+    row may report any row stride (torch treats size-1 dimensions as
+    contiguous whatever their stride), so its row length stands in."""
+    return int(T.stride(0)) if T.shape[0] > 1 else max(int(T.shape[1]), 1)
+
+
+def _check_rowmajor(*Ts):
+    for T in Ts:
+        if T.dim() == 2 and T.shape[1] > 1 and T.stride(1) != 1:
+            raise ValueError("matrices must be row-major with unit column stride")
+
+
 class Handle:
     """Owns an ``ata_handle`` (workspace, plan cache, device status word)."""
 
-    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0):
+    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0):
         L = load()
         self._h = ctypes.c_void_p()
-        cfg = _config(cutoff, depth, slices, strassen_min, variant)
+        cfg = _config(cutoff, depth, slices, strassen_min, variant, streams)
         _check(L.ata_create(ctypes.byref(self._h), ctypes.byref(cfg)), "ata_create")
 
-    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0):
-        cfg = _config(cutoff, depth, slices, strassen_min, variant)
+    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0):
+        cfg = _config(cutoff, depth, slices, strassen_min, variant, streams)
         _check(load().ata_set_config(self._h, ctypes.byref(cfg)), "ata_set_config")
 
     def lower_ptr(self, m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:
@@ -155,9 +169,8 @@ class Handle:
     def lower(self, A, C, dtype, stream=None):
         """low(C) <- low(A^T A) for row-major CUDA tensors A (m x n) and C (n x n)."""
         m, n = A.shape
-        if A.stride(1) != 1 or C.stride(1) != 1:
-            raise ValueError("A and C must be row-major with unit column stride")
-        rc = self.lower_ptr(m, n, A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0), dtype, stream)
+        _check_rowmajor(A, C)
+        rc = self.lower_ptr(m, n, A.data_ptr(), _ld(A), C.data_ptr(), _ld(C), dtype, stream)
         if rc != 0:
             raise AtaError(rc, f"ata_lower [{self.last_error()}]")
 
@@ -169,9 +182,8 @@ class Handle:
     def syrk(self, A, C, dtype, alpha=1.0, beta=0.0, stream=None):
         """low(C) <- alpha low(A^T A) + beta low(C) for row-major CUDA tensors."""
         m, n = A.shape
-        if A.stride(1) != 1 or C.stride(1) != 1:
-            raise ValueError("A and C must be row-major with unit column stride")
-        rc = self.syrk_ptr(m, n, alpha, A.data_ptr(), A.stride(0), beta, C.data_ptr(), C.stride(0), dtype, stream)
+        _check_rowmajor(A, C)
+        rc = self.syrk_ptr(m, n, alpha, A.data_ptr(), _ld(A), beta, C.data_ptr(), _ld(C), dtype, stream)
         if rc != 0:
             raise AtaError(rc, f"ata_syrk [{self.last_error()}]")
 
@@ -185,21 +197,18 @@ class Handle:
         with ATA_TRANS) row-major, or a 1-D tensor of the packed lower
         triangle with ATA_PACKED."""
         m, n = A.shape
-        if A.stride(1) != 1 or (C.dim() == 2 and C.stride(1) != 1):
-            raise ValueError("A and C must be row-major with unit column stride")
-        ldc = int(C.stride(0)) if C.dim() == 2 else 0
-        rc = self.syrk_ex_ptr(flags, m, n, alpha, A.data_ptr(), A.stride(0), beta, C.data_ptr(), ldc, dtype,
-                              stream)
+        _check_rowmajor(A, C)
+        ldc = _ld(C) if C.dim() == 2 else 0
+        rc = self.syrk_ex_ptr(flags, m, n, alpha, A.data_ptr(), _ld(A), beta, C.data_ptr(), ldc, dtype, stream)
         if rc != 0:
             raise AtaError(rc, f"ata_syrk_ex [{self.last_error()}]")
 
     def lower_aat(self, A, C, dtype, stream=None):
         """low(C) <- low(A A^T) for a row-major CUDA tensor A (m x n), C m x m (ata_lower_aat)."""
         m, n = A.shape
-        if A.stride(1) != 1 or C.stride(1) != 1:
-            raise ValueError("A and C must be row-major with unit column stride")
-        rc = int(load().ata_lower_aat(self._h, int(m), int(n), A.data_ptr(), int(A.stride(0)), C.data_ptr(),
-                                      int(C.stride(0)), int(dtype), _stream_ptr(stream)))
+        _check_rowmajor(A, C)
+        rc = int(load().ata_lower_aat(self._h, int(m), int(n), A.data_ptr(), _ld(A), C.data_ptr(), _ld(C),
+                                      int(dtype), _stream_ptr(stream)))
         if rc != 0:
             raise AtaError(rc, f"ata_lower_aat [{self.last_error()}]")
 
@@ -224,12 +233,11 @@ class Handle:
         if len(As) != len(Cs):
             raise ValueError("As and Cs must have the same length")
         for A, C in zip(As, Cs):
-            if (A.dim() == 2 and A.numel() and A.stride(1) != 1) or (C.numel() and C.stride(1) != 1):
-                raise ValueError("A_i and C_i must be row-major with unit column stride")
+            _check_rowmajor(A, C)
         ms = [int(A.shape[0]) for A in As]
         ns = [int(A.shape[1]) for A in As]
-        ldas = [max(int(A.stride(0)), n, 1) for A, n in zip(As, ns)]
-        ldcs = [max(int(C.stride(0)), n, 1) for C, n in zip(Cs, ns)]
+        ldas = [max(_ld(A) if A.shape[0] else 1, n, 1) for A, n in zip(As, ns)]
+        ldcs = [max(_ld(C) if C.shape[0] else 1, n, 1) for C, n in zip(Cs, ns)]
         rc = self.batched_ptr(ms, ns, [A.data_ptr() for A in As], ldas, [C.data_ptr() for C in Cs], ldcs,
                               dtype, stream)
         if rc != 0:
@@ -240,7 +248,8 @@ class Handle:
         candidate plans, keep the fastest for this shape, leave low(A^T A) in C."""
         m, n = A.shape
         out = (ctypes.c_int64 * 4)()
-        rc = int(load().ata_tune(self._h, int(m), int(n), A.data_ptr(), A.stride(0), C.data_ptr(), C.stride(0),
+        _check_rowmajor(A, C)
+        rc = int(load().ata_tune(self._h, int(m), int(n), A.data_ptr(), _ld(A), C.data_ptr(), _ld(C),
                                  int(dtype), _stream_ptr(stream), float(budget_ms), out))
         if rc != 0:
             raise AtaError(rc, f"ata_tune [{self.last_error()}]")

@@ -82,16 +82,48 @@ struct ata_handle_s {
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // static partition (ata_config.streams > 1): the side streams of the leaf
+    // groups, the fork event and one join event per stream
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     std::string last_error;
 };
 
 namespace {
 
+constexpr int MAX_STREAMS = 16;
+
+int ensure_side_streams(ata_handle h, size_t count) {
+    if (!h->fork && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        h->fork = nullptr;
+        return ATA_ERR_CUDA;
+    }
+    while (h->side.size() < count) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return ATA_ERR_CUDA;
+        }
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamDestroy(st);
+            return ATA_ERR_CUDA;
+        }
+        h->side.push_back(st);
+        h->join.push_back(ev);
+    }
+    return ATA_OK;
+}
+
 int check_config(const ata_config *c) {
     if (!c) return ATA_OK;
     if (c->cutoff < 0 || c->strassen_depth < -1 || c->strassen_depth > ATA_MAX_STRASSEN_DEPTH || c->slices < 0 ||
         c->slices > MAX_SLICES || c->strassen_min < 0 ||
-        (c->strassen_variant != ATA_STRASSEN && c->strassen_variant != ATA_WINOGRAD))
+        (c->strassen_variant != ATA_STRASSEN && c->strassen_variant != ATA_WINOGRAD) || c->streams < 0 ||
+        c->streams > MAX_STREAMS)
         return ATA_ERR_INVALID;
     for (int r : c->reserved)
         if (r != 0) return ATA_ERR_INVALID;
@@ -110,6 +142,7 @@ PlanParams params_for(const ata_config &cfg, int64_t m, int64_t n, int64_t lda, 
     pp.slices = cfg.slices;
     pp.strassen_min = cfg.strassen_min;
     pp.variant = cfg.strassen_variant;
+    pp.streams = cfg.streams > 1 ? cfg.streams : 1;
     return pp;
 }
 
@@ -189,7 +222,7 @@ ata_config effective_cfg(ata_handle h, int64_t m, int64_t n, int dtype) {
 
 CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
     Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices, pp.strassen_min,
-            pp.trans | (pp.packed << 1) | (pp.variant << 2)};
+            pp.trans | (pp.packed << 1) | (pp.variant << 2) | (pp.streams << 8)};
     auto it = h->plans.find(key);
     if (it != h->plans.end()) return it->second.get();
     std::unique_ptr<CachedPlan> cp(new CachedPlan());
@@ -298,6 +331,9 @@ int ata_destroy(ata_handle h) {
     h->batch.reset();
     for (cudaEvent_t &e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->join) cudaEventDestroy(e);
+    for (cudaStream_t st : h->side) cudaStreamDestroy(st);
+    if (h->fork) cudaEventDestroy(h->fork);
     if (h->ws) cudaFree(h->ws);
     if (h->d_status) cudaFree(h->d_status);
     delete h;
@@ -429,8 +465,24 @@ int lower_impl(ata_handle h, int flags, int64_t m, int64_t n, double alpha, cons
     lp.beta = beta;
     lp.a_trans = trans ? 1 : 0;
     lp.packed = packed ? 1 : 0;
-    e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
-    if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "leaf launch", e);
+    if (P.groups.empty()) {
+        e = P.uses_digits() ? launch_leaf_tc(P, lp, h->num_sms, s) : launch_leaf_f64(P, lp, s);
+        if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "leaf launch", e);
+    } else {  // static partition: one leaf launch per group, each on its own stream
+        if ((rc = ensure_side_streams(h, P.groups.size())) != ATA_OK) return fail(h, rc, "side streams");
+        if ((e = cudaEventRecord(h->fork, s)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "fork event", e);
+        for (size_t g = 0; g < P.groups.size(); ++g) {
+            const LeafGroup &G = P.groups[g];
+            cudaStream_t sg = h->side[g];
+            if ((e = cudaStreamWaitEvent(sg, h->fork, 0)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "fork", e);
+            e = P.uses_digits() ? launch_leaf_tc_group(P, lp, G.first, G.count, G.ctas, sg)
+                                : launch_leaf_f64_group(lp, G.first, G.count, sg);
+            if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "leaf group launch", e);
+            if ((e = cudaEventRecord(h->join[g], sg)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, h->join[g], 0)) != cudaSuccess)
+                return fail(h, ATA_ERR_CUDA, "join", e);
+        }
+    }
     mark(3);
     if ((e = launch_combine(P, tables, ws + P.off_products, C, expo, alpha, beta, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "combine launch", e);

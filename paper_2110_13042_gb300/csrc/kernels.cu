@@ -1005,6 +1005,15 @@ cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_leaf_f64_group(const LeafParams &lp, int64_t first, int64_t count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    LeafParams g = lp;
+    g.tasks = lp.tasks + first;
+    g.ntasks = static_cast<int>(count);
+    leaf_f64_kernel<<<static_cast<unsigned>(count), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
                            const int *expo, double alpha, double beta, cudaStream_t s) {
     if (P.combs.empty() || P.comb_tiles == 0) return cudaSuccess;

@@ -54,6 +54,10 @@ cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *ex
                         const uint8_t *tables, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s);
 cudaError_t launch_leaf_f64(const Plan &P, const LeafParams &lp, cudaStream_t s);
+// One group of a static partition (Plan::groups): tasks [first, first + count).
+cudaError_t launch_leaf_tc_group(const Plan &P, const LeafParams &lp, int64_t first, int64_t count, int ctas,
+                                 cudaStream_t s);
+cudaError_t launch_leaf_f64_group(const LeafParams &lp, int64_t first, int64_t count, cudaStream_t s);
 cudaError_t launch_combine(const Plan &P, const uint8_t *tables, const void *M, void *C,
                            const int *expo, double alpha, double beta, cudaStream_t s);
 // low(C) <- beta * low(C) (beta == 0: zeros, C not read); packed: C is a

@@ -831,6 +831,24 @@ cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cud
 
 namespace ata {
 
+// One group of a static partition: tasks [first, first + count) of the plan,
+// laid out for `ctas` persistent CTAs.
+cudaError_t launch_leaf_tc_group(const Plan &P, const LeafParams &lp, int64_t first, int64_t count, int ctas,
+                                 cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    LeafParams g = lp;
+    g.tasks = lp.tasks + first;
+    g.ntasks = static_cast<int>(count);
+    if (P.p.mode == MODE_F32_FP8) {
+        cudaError_t e = ensure_leaf_attr<1, true>();
+        if (e != cudaSuccess) return e;
+        leaf_tc_kernel<1, true><<<count < ctas ? static_cast<int>(count) : ctas, NUM_THREADS, Cfg<1>::SMEM_BYTES,
+                                  s>>>(g);
+        return cudaGetLastError();
+    }
+    return launch_leaf_tc_raw(P.slices, g, g.ntasks, ctas, s);
+}
+
 cudaError_t launch_wait_check(int *status, unsigned long long budget_ns, cudaStream_t s) {
     wait_check_kernel<<<1, 32, 0, s>>>(status, budget_ns);
     return cudaGetLastError();

@@ -172,6 +172,7 @@ struct Builder {
             t.out_off = r0 * P.p.ldc + c0;
             t.out_ld = P.p.ldc;
         }
+        t.unit = P.n_units - 1;
         P.tasks.push_back(t);
         P.plain_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
         P.leaf_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
@@ -180,6 +181,7 @@ struct Builder {
     // Tiles of the diagonal panel [c0, c0 + w) that hold lower-triangle entries.
     void diag_panel(int64_t c0, int64_t w) {
         P.n_panels++;
+        P.n_units++;  // one recursion unit
         for (int64_t J = 0; J < ceil_div(w, TILE_M); ++J) {
             const int64_t rows = std::min<int64_t>(TILE_M, w - J * TILE_M);
             for (int64_t K = 0; K * TILE_N < w && K * TILE_N <= J * TILE_M + rows - 1; ++K)
@@ -190,6 +192,7 @@ struct Builder {
 
     // Classical tiles of the off-diagonal block rows [r0, r0+p) x cols [c0, c0+q).
     void classical_block(int64_t r0, int64_t p, int64_t c0, int64_t q) {
+        P.n_units++;  // one recursion unit
         for (int64_t J = 0; J < ceil_div(p, TILE_M); ++J)
             for (int64_t K = 0; K < ceil_div(q, TILE_N); ++K)
                 plain_tile(r0 + J * TILE_M, c0 + K * TILE_N, std::min<int64_t>(TILE_M, p - J * TILE_M),
@@ -289,6 +292,7 @@ struct Builder {
             prod_off[r] = prod_elems;
             prod_elems += pn * qn;
             P.n_products++;
+            const int32_t unit = P.n_units++;  // every product is one recursion unit
             for (int64_t J = 0; J < ceil_div(pn, TILE_M); ++J) {
                 for (int64_t K = 0; K < ceil_div(qn, TILE_N); ++K) {
                     LeafTask t{};
@@ -308,6 +312,7 @@ struct Builder {
                     t.eu = t.ev = -1;
                     t.out_off = prod_off[r] + J * TILE_M * qn + K * TILE_N;
                     t.out_ld = qn;
+                    t.unit = unit;
                     P.tasks.push_back(t);
                     P.leaf_madds += static_cast<double>(rn) * TILE_M * TILE_N;
                 }
@@ -468,6 +473,60 @@ static void balance_task_list(std::vector<LeafTask> &tasks, int G) {
 }
 
 void balance_tasks(Plan &P, int G) { balance_task_list(P.tasks, G); }
+
+// Static partition of the recursion over `streams` leaf launches: the
+// counterpart of the paper's shared-memory AtA (Section 4.1-4.2, Algorithm 3),
+// which simulates the recursion up front and gives each thread whole subtrees.
+// Here the units are the recursion's leaves (a diagonal panel, a classical
+// block, one Strassen product), assigned longest-first to the least-loaded
+// group; every group gets a share of the CTAs proportional to its load and
+// its tiles laid out for them as in balance_tasks.
+void partition_units(Plan &P, int streams, int num_ctas) {
+    constexpr int64_t TASK_OVERHEAD_STEPS = 3;
+    const int G = std::max(1, streams);
+    std::vector<double> unit_steps(static_cast<size_t>(std::max(P.n_units, 1)), 0.0);
+    for (const LeafTask &t : P.tasks)
+        unit_steps[static_cast<size_t>(t.unit)] += static_cast<double>(ceil_div(t.klen, KSTEP) + TASK_OVERHEAD_STEPS);
+    std::vector<int> order(unit_steps.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return unit_steps[a] > unit_steps[b]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int g = 0; g < G; ++g) heap.push({0.0, g});
+    std::vector<int> group_of(unit_steps.size(), 0);
+    std::vector<double> load(G, 0.0);
+    for (int u : order) {
+        Load l = heap.top();
+        heap.pop();
+        group_of[u] = l.second;
+        l.first += unit_steps[u];
+        load[l.second] = l.first;
+        heap.push(l);
+    }
+    std::vector<std::vector<LeafTask>> per(G);
+    for (const LeafTask &t : P.tasks) per[group_of[t.unit]].push_back(t);
+    double total = 0;
+    for (double x : load) total += x;
+    const int ctas_all = std::max(num_ctas, G);
+    std::vector<LeafTask> out;
+    P.groups.clear();
+    int given = 0;
+    for (int g = 0; g < G; ++g) {
+        if (per[g].empty()) continue;
+        int c = total > 0 ? static_cast<int>(ctas_all * load[g] / total) : 1;
+        c = std::max(1, std::min(c, ctas_all - given));
+        given += c;
+        if (per[g].size() > static_cast<size_t>(c)) balance_task_list(per[g], c);
+        LeafGroup lg{};
+        lg.first = static_cast<int64_t>(out.size());
+        lg.count = static_cast<int64_t>(per[g].size());
+        lg.ctas = c;
+        lg.steps = load[g];
+        out.insert(out.end(), per[g].begin(), per[g].end());
+        P.groups.push_back(lg);
+    }
+    P.tasks.swap(out);
+}
 
 bool make_batch_plan(int mode, int slices, int num_ctas, int64_t count, const int64_t *m, const int64_t *n,
                      const int64_t *lda, const int64_t *ldc, const void *const *A, void *const *C,
@@ -636,7 +695,9 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
 
     P.n_tiles = static_cast<int64_t>(P.tasks.size());
-    if (B.digits && pp.num_ctas > 1 && P.tasks.size() > static_cast<size_t>(pp.num_ctas))
+    if (pp.streams > 1 && !P.tasks.empty())
+        partition_units(P, pp.streams, pp.num_ctas > 1 ? pp.num_ctas : 152);
+    else if (B.digits && pp.num_ctas > 1 && P.tasks.size() > static_cast<size_t>(pp.num_ctas))
         balance_tasks(P, pp.num_ctas);
 
     // Every digit-family tile must start on a column block: the leaf loads

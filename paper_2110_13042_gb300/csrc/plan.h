@@ -118,7 +118,8 @@ struct LeafTask {
     int32_t hbits;          // extra fraction bits of T for short contractions
     int32_t k0v;            // contraction offset of the column operand (k0: row operand)
     int32_t prob;           // batched calls: problem index (planes and C of that problem)
-    int32_t pad;
+    int32_t unit;           // node of the recursion the tile belongs to (a diagonal
+                            // panel, a classical block or one Strassen product)
 };
 
 // One problem of a batched call (device table, one entry per problem).
@@ -222,6 +223,17 @@ struct PlanParams {
     int packed = 0;          // 1: C is stored as a packed lower triangle, entry
                              // (j, k) at j (j + 1) / 2 + k (ldc unused)
     int variant = VARIANT_STRASSEN;  // coefficient tables of the off-diagonal products
+    int streams = 1;         // > 1: static partition of the recursion's units over
+                             // this many leaf launches on their own streams
+};
+
+// One leaf launch of a static partition: tasks [first, first + count) of the
+// plan's task list, laid out for `ctas` persistent CTAs.
+struct LeafGroup {
+    int64_t first, count;
+    int32_t ctas;
+    int32_t pad;
+    double steps;            // K steps of its tiles (the load the partition balances)
 };
 
 // Element offset of entry (j, k), k <= j, of a packed lower triangle.
@@ -240,6 +252,8 @@ struct Plan {
     std::vector<CombDesc> combs;
     std::vector<CombTerm> cterms;
     std::vector<BlockInfo> blocks;      // off-diagonal blocks, in recursion order
+    std::vector<LeafGroup> groups;      // static partition (PlanParams::streams > 1), else empty
+    int32_t n_units = 0;                // recursion units the tiles belong to
     int64_t prep_tiles = 0, comb_tiles = 0;
     // workspace layout (byte offsets)
     int64_t off_colmax = 0, off_expo = 0, off_products = 0, product_bytes = 0;
@@ -285,5 +299,10 @@ void pack_tables(const Plan &plan, std::vector<uint8_t> *buf);
 // greedy least-loaded), padding with empty tasks; make_plan calls it when
 // PlanParams::num_ctas > 1.
 void balance_tasks(Plan &plan, int num_ctas);
+
+// Reorders plan.tasks into `streams` static groups of whole recursion units
+// (plan.groups), each laid out for its share of num_ctas CTAs; make_plan
+// calls it when PlanParams::streams > 1.
+void partition_units(Plan &plan, int streams, int num_ctas);
 
 }  // namespace ata

@@ -1,5 +1,5 @@
 // Host-only planner inspector (used by the CPU tests): builds the plan for
-//   plan_cli m n mode cutoff depth slices [strassen_min [split_search [num_ctas]]]
+//   plan_cli m n mode cutoff depth slices [strassen_min [split_search [num_ctas [variant [streams]]]]]
 // and prints key=value statistics, including a coverage check that every
 // lower-triangle entry of C is produced exactly once (by a diagonal/classical
 // tile or by one Strassen result sum) and no upper entry is produced.
@@ -27,6 +27,7 @@ int main(int argc, char **argv) {
     pp.split_search = argc > 8 ? std::atoi(argv[8]) : 1;
     pp.num_ctas = argc > 9 ? std::atoi(argv[9]) : 0;
     pp.variant = argc > 10 ? std::atoi(argv[10]) : 0;
+    pp.streams = argc > 11 ? std::atoi(argv[11]) : 1;
     Plan P;
     std::string err;
     if (!make_plan(pp, &P, &err)) {
@@ -107,14 +108,41 @@ int main(int argc, char **argv) {
             if (k <= j && v == 1) covered++;
             if (v > 1 || (k > j && v > 0)) overlap++;
         }
+    // Static partition: groups are consecutive, cover the task list, use at
+    // most the CTAs given, and every recursion unit lies in one group.
+    bool groups_ok = true;
+    int64_t group_steps_max = 0;
+    if (!P.groups.empty()) {
+        int64_t next = 0, ctas = 0;
+        std::vector<int> unit_group(static_cast<size_t>(P.n_units), -1);
+        for (size_t g = 0; g < P.groups.size(); ++g) {
+            const LeafGroup &lg = P.groups[g];
+            if (lg.first != next || lg.count <= 0 || lg.ctas < 1) groups_ok = false;
+            next = lg.first + lg.count;
+            ctas += lg.ctas;
+            std::vector<int64_t> per(static_cast<size_t>(lg.ctas), 0);
+            for (int64_t i = lg.first; i < lg.first + lg.count; ++i) {
+                const LeafTask &t = P.tasks[static_cast<size_t>(i)];
+                per[static_cast<size_t>((i - lg.first) % lg.ctas)] += (t.klen + KSTEP - 1) / KSTEP;
+                if (t.klen == 0) continue;  // balance filler
+                int &ug = unit_group[static_cast<size_t>(t.unit)];
+                if (ug >= 0 && ug != static_cast<int>(g)) groups_ok = false;
+                ug = static_cast<int>(g);
+            }
+            for (int64_t v : per) group_steps_max = std::max(group_steps_max, v);
+        }
+        if (next != static_cast<int64_t>(P.tasks.size()) || ctas > G) groups_ok = false;
+    }
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
                 "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "
-                "cta_steps_sum=%lld prep_tiles=%lld prep_groups=%lld prep_map_ok=%d comb_map_ok=%d\n",
+                "cta_steps_sum=%lld prep_tiles=%lld prep_groups=%lld prep_map_ok=%d comb_map_ok=%d "
+                "units=%d leaf_groups=%zu groups_ok=%d group_steps_max=%lld\n",
                 P.cutoff, P.depth, P.slices, (long long)P.n_panels, (long long)P.n_blocks,
                 (long long)P.n_products, (size_t)P.n_tiles, (long long)covered, (long long)overlap,
                 P.cterms.size(), P.ops.size(), P.families.size(), (long long)P.workspace_bytes, s_leaf,
                 s_plain, (long long)P.n_reused, (long long)cta_max, (long long)cta_sum, (long long)P.prep_tiles,
-                (long long)groups, prep_ok ? 1 : 0, comb_ok ? 1 : 0);
+                (long long)groups, prep_ok ? 1 : 0, comb_ok ? 1 : 0, P.n_units, P.groups.size(), groups_ok ? 1 : 0,
+                (long long)group_steps_max);
     return 0;
 }

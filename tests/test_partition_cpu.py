@@ -1,0 +1,49 @@
+"""CPU checks of the static partition over streams (ata_config.streams, the
+counterpart of the paper's static task tree, Section 4.1-4.2): the planner's
+groups cover the task list, keep every recursion unit (diagonal panel,
+classical block, Strassen product) in one group, use no more CTAs than the
+persistent launch, and leave the produced entries unchanged."""
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cli(tmp_path_factory):
+    src = os.path.join(ROOT, "paper_2110_13042_gb300", "csrc")
+    out = str(tmp_path_factory.mktemp("cli") / "plan_cli")
+    subprocess.run(["g++", "-O1", "-std=c++17", "-I", src, os.path.join(src, "plan_cli.cpp"),
+                    os.path.join(src, "plan.cpp"), "-o", out], check=True)
+
+    def run(m, n, mode, cutoff, depth, smin, streams, variant=0):
+        r = subprocess.run([out, str(m), str(n), str(mode), str(cutoff), str(depth), "0", str(smin), "1", "152",
+                            str(variant), str(streams)], capture_output=True, text=True, check=True)
+        return {k: float(v) for k, v in (kv.split("=") for kv in r.stdout.split())}
+    return run
+
+
+@pytest.mark.parametrize("streams", [2, 3, 4, 8, 16])
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin", [
+    (8192, 8192, 1, 0, 1, 4096), (3000, 5000, 2, 0, 2, 512), (700, 1300, 5, 200, 2, 2),
+    (500, 900, 0, 128, 1, 2), (1000, 300, 1, 0, 0, 4096)])
+def test_partition_covers_and_keeps_units_whole(cli, streams, m, n, mode, cutoff, depth, smin):
+    one = cli(m, n, mode, cutoff, depth, smin, 1)
+    part = cli(m, n, mode, cutoff, depth, smin, streams)
+    assert part["covered"] == n * (n + 1) // 2 and part["overlap"] == 0
+    assert part["groups_ok"] == 1
+    assert 1 <= part["leaf_groups"] <= min(streams, part["units"])
+    assert part["tiles"] == one["tiles"] and part["products"] == one["products"]
+    assert part["cta_steps_sum"] == one["cta_steps_sum"]
+
+
+def test_partition_is_a_static_comparison_not_a_speedup(cli):
+    """Whole units per group cannot balance as finely as tiles over one
+    persistent grid: the busiest CTA of the partition carries at least the
+    persistent layout's load (the paper's AtA-S has the same limit)."""
+    one = cli(8192, 8192, 1, 0, 1, 4096, 1)
+    for s in (2, 4, 8):
+        part = cli(8192, 8192, 1, 0, 1, 4096, s)
+        assert part["group_steps_max"] >= one["cta_steps_max"]
