@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--strassen-min", type=int, default=0)
     ap.add_argument("--variant", default="strassen", choices=["strassen", "winograd"])
+    ap.add_argument("--streams", type=int, default=0,
+                    help="> 1: static partition of the recursion over that many leaf launches and streams")
+    ap.add_argument("--aat", action="store_true",
+                    help="time low(A A^T) of the transposed n x m array (same operand and work) instead")
     ap.add_argument("--seed", type=int, default=2110)
     ap.add_argument("--dist", default="uniform", choices=list(DIST_DESC),
                     help="entries: U[-1,1); N(0,1) x 10^U(-3,3) per column; U[-1,1) + rank-16 part of size 1e4")
@@ -435,16 +439,24 @@ def main():
     C = torch.zeros((n, n), dtype=tdt, device=dev)
     variant = 1 if args.variant == "winograd" else 0
     h = ata.Handle(cutoff=args.cutoff, depth=args.depth, slices=args.slices, strassen_min=args.strassen_min,
-                   variant=variant)
+                   variant=variant, streams=args.streams)
     stream = torch.cuda.current_stream(dev)
     tuned = None
-    if args.depth < 0 and args.cutoff == 0 and args.strassen_min == 0 and not args.no_tune:
+    if args.aat:
+        # the A A^T product of the transposed array: the same m x n operand and
+        # work, read row by row from an n x m array
+        A = A.t().contiguous()
+        A_host = None if A_host is None else np.ascontiguousarray(A_host.T)
+    elif args.depth < 0 and args.cutoff == 0 and args.strassen_min == 0 and not args.no_tune:
         # autotuned plan for this shape (outside every timed region)
         tuned = h.tune(A, C, mode, stream, budget_ms=args.tune_budget_ms)
     info = ata.plan_info(m, n, mode, h)
 
     def step():
-        h.lower(A, C, mode, stream)
+        if args.aat:
+            h.lower_aat(A, C, mode, stream)
+        else:
+            h.lower(A, C, mode, stream)
 
     def timed(fn, k, w):
         for _ in range(w):
@@ -528,7 +540,7 @@ def main():
            "gpu_launches": args.steps * (4 + (1 if info["products"] else 0)),
            "clocks": clk}
 
-    if not args.no_extras:
+    if not args.no_extras and not args.aat:
         # plain tiled AtA (Strassen depth 0) on the same GPU, same mode
         hp = ata.Handle(cutoff=0, depth=0, slices=args.slices)
         ms_plain = timed(lambda: hp.lower(A, C, mode, stream), args.steps, args.warmup)
