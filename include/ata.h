@@ -113,7 +113,15 @@ typedef struct {
                             stream: the counterpart of the paper's static
                             task tree of AtA-S (Section 4.1-4.2, Algorithm
                             3).  Results are bit-identical either way.         */
-    int reserved[2];     /* must be zero                                          */
+    int split_k;         /* contraction chunks per plain leaf tile (not for
+                            ATA_F64): 0 = automatic (a plan with fewer than 4
+                            tiles per SM and m >= 8192 splits the contraction
+                            into chunks of >= 4096 rows), 1 = never, 2..16 =
+                            that many.  The chunks' exact partial products
+                            are summed in a fixed order by the combine pass:
+                            results stay deterministic (run to run
+                            bit-identical) and within the mode's tolerance    */
+    int reserved[1];     /* must be zero                                          */
 } ata_config;
 
 #define ATA_MAX_STRASSEN_DEPTH 8
@@ -253,8 +261,9 @@ const char *ata_last_error(ata_handle h);
  *                                                           the leaves (per digit
  *                                                           pair)
  *   [9] multiply-adds of plain tiled AtA on the same tile grid
+ *   [10] contraction chunks per plain tile (split_k; 1 = not split)
  * h may be NULL (default configuration). */
-#define ATA_PLAN_FIELDS 10
+#define ATA_PLAN_FIELDS 11
 int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out);
 
 /* Host-only description of the off-diagonal blocks of the plan ata_lower

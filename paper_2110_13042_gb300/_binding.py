@@ -16,7 +16,7 @@ ATA_TRANS, ATA_PACKED = 1, 2
 STATUS = {0: "ATA_OK", 1: "ATA_ERR_INVALID", 2: "ATA_ERR_DTYPE", 3: "ATA_ERR_ALLOC",
           4: "ATA_ERR_CUDA", 5: "ATA_ERR_TIMEOUT", 6: "ATA_ERR_UNSUPPORTED"}
 PLAN_FIELDS = ("cutoff", "depth", "slices", "panels", "blocks", "products", "tiles",
-               "workspace_bytes", "leaf_madds", "plain_madds")
+               "workspace_bytes", "leaf_madds", "plain_madds", "split_k")
 
 _lib = None
 
@@ -85,12 +85,13 @@ def version() -> int:
 class Config(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int), ("strassen_depth", ctypes.c_int),
                 ("slices", ctypes.c_int), ("strassen_min", ctypes.c_int),
-                ("strassen_variant", ctypes.c_int), ("streams", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("strassen_variant", ctypes.c_int), ("streams", ctypes.c_int), ("split_k", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
-def _config(cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0) -> Config:
+def _config(cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0, split_k=0) -> Config:
     return Config(int(cutoff), int(depth), int(slices), int(strassen_min), int(variant), int(streams),
-                  (ctypes.c_int * 2)())
+                  int(split_k), (ctypes.c_int * 1)())
 
 
 def _check(rc: int, what: str):
@@ -140,22 +141,22 @@ def _ld(T) -> int:
 
 
 def _check_rowmajor(*Ts):
-    for T in Ts:
-        if T.dim() == 2 and T.shape[1] > 1 and T.stride(1) != 1:
+    for T in Ts:  # empty tensors may report any strides
+        if T.dim() == 2 and T.numel() > 0 and T.shape[1] > 1 and T.stride(1) != 1:
             raise ValueError("matrices must be row-major with unit column stride")
 
 
 class Handle:
     """Owns an ``ata_handle`` (workspace, plan cache, device status word)."""
 
-    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0):
+    def __init__(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0, split_k=0):
         L = load()
         self._h = ctypes.c_void_p()
-        cfg = _config(cutoff, depth, slices, strassen_min, variant, streams)
+        cfg = _config(cutoff, depth, slices, strassen_min, variant, streams, split_k)
         _check(L.ata_create(ctypes.byref(self._h), ctypes.byref(cfg)), "ata_create")
 
-    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0):
-        cfg = _config(cutoff, depth, slices, strassen_min, variant, streams)
+    def set_config(self, cutoff=0, depth=-1, slices=0, strassen_min=0, variant=0, streams=0, split_k=0):
+        cfg = _config(cutoff, depth, slices, strassen_min, variant, streams, split_k)
         _check(load().ata_set_config(self._h, ctypes.byref(cfg)), "ata_set_config")
 
     def lower_ptr(self, m, n, A_ptr, lda, C_ptr, ldc, dtype, stream=None) -> int:

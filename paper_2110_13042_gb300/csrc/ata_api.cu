@@ -47,11 +47,13 @@ struct CachedBatch {
     size_t table_bytes = 0;
     int64_t off_expo = 0, off_probs = 0, off_tasks = 0, off_planes = 0, total = 0;
     bool any_empty_m = false;         // some problem has m == 0 and n > 0 (zero fill)
-    cudaEvent_t uploaded = nullptr;   // recorded after each upload from `pinned`
+    cudaEvent_t uploaded = nullptr;   // recorded after each uncaptured upload from `pinned`
+    bool recorded = false;            // `uploaded` holds a record made outside a graph capture
     ~CachedBatch() {
         if (uploaded) {
-            cudaEventSynchronize(uploaded);
+            if (recorded) cudaEventSynchronize(uploaded);
             cudaEventDestroy(uploaded);
+            cudaGetLastError();
         }
         if (pinned) cudaFreeHost(pinned);
     }
@@ -123,7 +125,7 @@ int check_config(const ata_config *c) {
     if (c->cutoff < 0 || c->strassen_depth < -1 || c->strassen_depth > ATA_MAX_STRASSEN_DEPTH || c->slices < 0 ||
         c->slices > MAX_SLICES || c->strassen_min < 0 ||
         (c->strassen_variant != ATA_STRASSEN && c->strassen_variant != ATA_WINOGRAD) || c->streams < 0 ||
-        c->streams > MAX_STREAMS)
+        c->streams > MAX_STREAMS || c->split_k < 0 || c->split_k > SPLITK_MAX)
         return ATA_ERR_INVALID;
     for (int r : c->reserved)
         if (r != 0) return ATA_ERR_INVALID;
@@ -143,6 +145,7 @@ PlanParams params_for(const ata_config &cfg, int64_t m, int64_t n, int64_t lda, 
     pp.strassen_min = cfg.strassen_min;
     pp.variant = cfg.strassen_variant;
     pp.streams = cfg.streams > 1 ? cfg.streams : 1;
+    pp.split_k = cfg.split_k;
     return pp;
 }
 
@@ -156,7 +159,11 @@ int fail(ata_handle h, int status, const char *step, cudaError_t e = cudaSuccess
     return status;
 }
 
-int ensure_workspace(ata_handle h, size_t bytes) {
+// Grow the workspace to `bytes`.  A new workspace is zeroed on the call's
+// stream, so the zeroing is ordered before the call's table upload and
+// kernels whatever kind of stream the caller uses (cudaMemset would run on
+// the legacy default stream, which a non-blocking stream does not wait for).
+int ensure_workspace(ata_handle h, size_t bytes, cudaStream_t s) {
     if (bytes <= h->ws_bytes) return ATA_OK;
     const char *inj = std::getenv("ATA_TEST_FAIL_ALLOC");
     if (inj && inj[0] == '1') return ATA_ERR_ALLOC;
@@ -176,7 +183,8 @@ int ensure_workspace(ata_handle h, size_t bytes) {
             return ATA_ERR_ALLOC;
         }
     }
-    if (cudaMemset(p, 0, want) != cudaSuccess) {
+    if (cudaMemsetAsync(p, 0, want, s) != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(p);
         return ATA_ERR_CUDA;
     }
@@ -222,7 +230,7 @@ ata_config effective_cfg(ata_handle h, int64_t m, int64_t n, int dtype) {
 
 CachedPlan *get_plan(ata_handle h, const PlanParams &pp, int *status) {
     Key key{pp.m, pp.n, pp.lda, pp.ldc, pp.mode, pp.cutoff, pp.depth, pp.slices, pp.strassen_min,
-            pp.trans | (pp.packed << 1) | (pp.variant << 2) | (pp.streams << 8)};
+            pp.trans | (pp.packed << 1) | (pp.variant << 2) | (pp.streams << 8) | (pp.split_k << 16)};
     auto it = h->plans.find(key);
     if (it != h->plans.end()) return it->second.get();
     std::unique_ptr<CachedPlan> cp(new CachedPlan());
@@ -303,7 +311,9 @@ int ata_create(ata_handle *out, const ata_config *cfg) {
         std::memset(&h->cfg, 0, sizeof(h->cfg));
         h->cfg.strassen_depth = -1;
     }
-    if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+    // the zeroed status word is complete before any call can use it, on any stream
+    if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return ATA_ERR_ALLOC;
@@ -360,6 +370,7 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     out[7] = P.workspace_bytes;
     out[8] = static_cast<int64_t>(P.leaf_madds);
     out[9] = static_cast<int64_t>(P.plain_madds);
+    out[10] = P.split_k;
     return ATA_OK;
 }
 
@@ -396,6 +407,7 @@ int lower_impl(ata_handle h, int flags, int64_t m, int64_t n, double alpha, cons
                double beta, void *C, int64_t ldc, int dtype, void *stream) {
     if (!h) return ATA_ERR_INVALID;
     h->last_error.clear();
+    cudaGetLastError();  // launch checks below report this call's launches only
     if (!valid_dtype(dtype)) return ATA_ERR_DTYPE;
     if (flags & ~(ATA_TRANS | ATA_PACKED)) return ATA_ERR_INVALID;
     if (m < 0 || n < 0) return ATA_ERR_INVALID;
@@ -424,7 +436,7 @@ int lower_impl(ata_handle h, int flags, int64_t m, int64_t n, double alpha, cons
     CachedPlan *cp = get_plan(h, pp, &status);
     if (!cp) return status;
     const Plan &P = cp->plan;
-    int rc = ensure_workspace(h, static_cast<size_t>(P.workspace_bytes));
+    int rc = ensure_workspace(h, static_cast<size_t>(P.workspace_bytes), s);
     if (rc != ATA_OK) return rc;
     rc = bind_plan(h, *cp);
     if (rc != ATA_OK) return rc;
@@ -641,6 +653,7 @@ int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, co
                  void *const *C_dev, int dtype, void *stream) {
     if (!h || count < 0) return ATA_ERR_INVALID;
     h->last_error.clear();
+    cudaGetLastError();  // launch checks below report this call's launches only
     if (count == 0) return ATA_OK;
     const bool dev = A_dev != nullptr || C_dev != nullptr;
     if (!m || !n || !lda || !ldc || (dev ? (!A_dev || !C_dev) : (!A_host || !C_host))) return ATA_ERR_INVALID;
@@ -716,7 +729,8 @@ int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, co
         bool same = cb.ptrs.size() == 2 * static_cast<size_t>(count);
         for (int i = 0; same && i < count; ++i) same = cb.ptrs[2 * i] == A_host[i] && cb.ptrs[2 * i + 1] == C_host[i];
         if (!same) {
-            if (cudaEventSynchronize(cb.uploaded) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "batch table reuse");
+            if (cb.recorded && cudaEventSynchronize(cb.uploaded) != cudaSuccess)
+                return fail(h, ATA_ERR_CUDA, "batch table reuse");
             BatchProb *pp = reinterpret_cast<BatchProb *>(cb.pinned);
             cb.ptrs.resize(2 * static_cast<size_t>(count));
             for (int i = 0; i < count; ++i) {
@@ -727,7 +741,7 @@ int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, co
             }
         }
     }
-    int rc = ensure_workspace(h, static_cast<size_t>(cb.total));
+    int rc = ensure_workspace(h, static_cast<size_t>(cb.total), s);
     if (rc != ATA_OK) return fail(h, rc, "workspace");
     h->resident = nullptr;  // the batch overwrites the single-call tables
     uint8_t *ws = h->ws;
@@ -735,7 +749,15 @@ int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, co
     int *expo = reinterpret_cast<int *>(ws + cb.off_expo);
     cudaError_t e = cudaMemcpyAsync(ws + cb.off_probs, cb.pinned, cb.table_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload", e);
-    if ((e = cudaEventRecord(cb.uploaded, s)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload event", e);
+    // Remember the upload (to wait for it before the pinned table is
+    // rewritten) only outside a graph capture: a captured upload belongs to
+    // the graph, and an event recorded in a capture cannot be waited on.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "capture status", e);
+    if (cap == cudaStreamCaptureStatusNone) {
+        if ((e = cudaEventRecord(cb.uploaded, s)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload event", e);
+        cb.recorded = true;
+    }
     if (dev && (e = launch_batched_ptrs(probs, count, A_dev, C_dev, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched pointer gather", e);
     if (cb.any_empty_m && (e = launch_batched_zero(probs, count, f32, s)) != cudaSuccess)
@@ -786,7 +808,9 @@ int ata_sync(ata_handle h, void *stream) {
     }
     int st = 0;
     if (cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ATA_ERR_CUDA;
-    if (st != 0 && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return ATA_ERR_CUDA;
+    if (st != 0 && (cudaMemsetAsync(h->d_status, 0, sizeof(int), static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+                    cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess))
+        return ATA_ERR_CUDA;
     return st;
 }
 

@@ -721,6 +721,7 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
     for (int i = 0; i < COMB_RPT; ++i) {
         const int row = r0 + 8 * i;
         if (row >= d.rows) break;
+        if (d.diag && col > row + d.diag_off) continue;  // upper triangle: never written
         const int x = xc + expo[d.e_row0 + row];
         TOut *c = packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
                          : C + d.c_off + static_cast<int64_t>(row) * ldc + col;
@@ -765,6 +766,7 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__rest
     for (int i = 0; i < COMB_RPT; ++i) {
         const int row = r0 + 8 * i;
         if (row >= d.rows) break;
+        if (d.diag && col > row + d.diag_off) continue;  // upper triangle: never written
         store_scaled(packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
                             : C + d.c_off + static_cast<int64_t>(row) * ldc + col,
                      static_cast<TOut>(sum[i] * exp2i(expo[d.e_row0 + row] + ec)), alpha, beta);

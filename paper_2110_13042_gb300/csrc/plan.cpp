@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <memory>
 #include <numeric>
 #include <queue>
 #include <string>
@@ -106,6 +107,7 @@ struct Builder {
     const int (*tV)[4] = kV;
     const int (*tW)[4] = kW;
     int64_t prod_elems = 0;
+    int split_k = 1;  // contraction chunks per plain tile (split contraction)
 
     explicit Builder(Plan &p)
         : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)) {}
@@ -142,6 +144,10 @@ struct Builder {
     }
 
     void plain_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
+        if (split_k > 1) {
+            split_tile(r0, c0, rows, cols);
+            return;
+        }
         LeafTask t{};
         t.fam_u = digits ? 0 : -1;
         t.fam_v = t.fam_u;
@@ -324,13 +330,7 @@ struct Builder {
         for (int64_t ir = 0; ir < nsub; ++ir) {
             for (int64_t ic = 0; ic < nsub; ++ic) {
                 if (preg[ir].ext == 0 || qreg[ic].ext == 0) continue;
-                CombDesc c{};
-                c.c_off = (r0 + preg[ir].off) * P.p.ldc + c0 + qreg[ic].off;
-                c.rows = static_cast<int32_t>(preg[ir].ext);
-                c.cols = static_cast<int32_t>(qreg[ic].ext);
-                c.e_row0 = static_cast<int32_t>(r0 + preg[ir].off);
-                c.e_col0 = static_cast<int32_t>(c0 + qreg[ic].off);
-                c.first_term = static_cast<int32_t>(P.cterms.size());
+                std::vector<CombTerm> terms;
                 for (int64_t r = 0; r < nprod; ++r) {
                     int64_t rr = r;
                     int w = 1;
@@ -339,33 +339,87 @@ struct Builder {
                         rr /= 7;
                         w *= tW[dg][2 * bit(ir, l, d) + bit(ic, l, d)];
                     }
-                    if (w != 0)
-                        P.cterms.push_back({prod_off[r], static_cast<int32_t>(qn), w, prod_shift[r], 0});
+                    if (w != 0) terms.push_back({prod_off[r], static_cast<int32_t>(qn), w, prod_shift[r], 0});
                 }
-                c.nterms = static_cast<int32_t>(P.cterms.size()) - c.first_term;
-                // Sum the exact products in units 2^(smin + rshift) with the
-                // worst case below 2^62: |T_r| <= 1.004 K 2^T_BOUND_LOG2.
-                int smin = 1 << 20;
-                for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
-                    smin = std::min(smin, P.cterms[i].shift);
-                c.rshift = 0;
-                if (digits && !fp8) {
-                    for (;;) {
-                        double bound = 0;
-                        for (int i = c.first_term; i < c.first_term + c.nterms; ++i)
-                            bound += 1.004 * static_cast<double>(rn) *
-                                     std::ldexp(1.0, T_BOUND_LOG2 + hbits_for(rn) + P.cterms[i].shift -
-                                                         smin - c.rshift);
-                        if (bound < std::ldexp(1.0, 62)) break;
-                        c.rshift++;
-                    }
-                }
-                c.smin = smin;
-                c.tile_base = P.comb_tiles;
-                P.comb_tiles += ceil_div(c.rows, COMB_ROWS) * ceil_div(c.cols, COMB_COLS);
-                P.combs.push_back(c);
+                add_comb(r0 + preg[ir].off, c0 + qreg[ic].off, preg[ir].ext, qreg[ic].ext, terms,
+                         std::vector<int64_t>(terms.size(), rn), false);
             }
         }
+    }
+
+    // One combine region C[r0:r0+rows, c0:c0+cols] = sum of `terms` (products
+    // in the workspace; term i over a contraction of klen[i] rows).  The exact
+    // products are summed in units 2^(smin + rshift), with rshift > 0 only if
+    // the worst case (|T| <= 1.004 K 2^(T_BOUND_LOG2 + h) per product) could
+    // reach 2^62.  diag: the region crosses the diagonal, only entries with
+    // col <= row + (r0 - c0) are written.
+    void add_comb(int64_t r0, int64_t c0, int64_t rows, int64_t cols, const std::vector<CombTerm> &terms,
+                  const std::vector<int64_t> &klen, bool diag) {
+        CombDesc c{};
+        c.c_off = r0 * P.p.ldc + c0;
+        c.rows = static_cast<int32_t>(rows);
+        c.cols = static_cast<int32_t>(cols);
+        c.e_row0 = static_cast<int32_t>(r0);
+        c.e_col0 = static_cast<int32_t>(c0);
+        c.diag = diag ? 1 : 0;
+        c.diag_off = static_cast<int32_t>(r0 - c0);
+        c.first_term = static_cast<int32_t>(P.cterms.size());
+        P.cterms.insert(P.cterms.end(), terms.begin(), terms.end());
+        c.nterms = static_cast<int32_t>(terms.size());
+        int smin = 1 << 20;
+        for (const CombTerm &t : terms) smin = std::min(smin, t.shift);
+        c.rshift = 0;
+        if (digits && !fp8) {
+            for (;;) {
+                double bound = 0;
+                for (size_t i = 0; i < terms.size(); ++i)
+                    bound += 1.004 * static_cast<double>(klen[i]) *
+                             std::ldexp(1.0, T_BOUND_LOG2 + hbits_for(klen[i]) + terms[i].shift - smin - c.rshift);
+                if (bound < std::ldexp(1.0, 62)) break;
+                c.rshift++;
+            }
+        }
+        c.smin = smin;
+        c.tile_base = P.comb_tiles;
+        P.comb_tiles += ceil_div(c.rows, COMB_ROWS) * ceil_div(c.cols, COMB_COLS);
+        P.combs.push_back(c);
+    }
+
+    // A plain tile computed as split_k contraction chunks (rows a multiple of
+    // 256, so every chunk drains its accumulators on the same row boundaries
+    // as the whole): each chunk's exact partial product goes to the product
+    // workspace, and one combine region sums them in chunk order into C.
+    void split_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
+        const int64_t m = P.p.m;
+        const int64_t chunk = round_up(ceil_div(m, split_k), 256);
+        std::vector<CombTerm> terms;
+        std::vector<int64_t> klen;
+        for (int64_t k0 = 0; k0 < m; k0 += chunk) {
+            const int64_t kl = std::min(chunk, m - k0);
+            LeafTask t{};
+            t.fam_u = t.fam_v = 0;
+            t.col_u = static_cast<int32_t>(r0);
+            t.col_v = static_cast<int32_t>(c0);
+            t.k0 = t.k0v = static_cast<int32_t>(k0);
+            t.klen = static_cast<int32_t>(kl);
+            t.rows = static_cast<int32_t>(rows);
+            t.cols = static_cast<int32_t>(cols);
+            t.diag = 0;  // the combine masks the diagonal
+            t.kind = fp8 ? OUT_M_F64 : OUT_M_I64;
+            t.hbits = fp8 ? 0 : hbits_for(kl);
+            t.shift = fp8 ? 0 : -t.hbits;  // a product of single-term operands
+            t.eu = t.ev = -1;
+            t.out_off = prod_elems;
+            t.out_ld = TILE_N;
+            t.unit = P.n_units - 1;
+            P.tasks.push_back(t);
+            terms.push_back({prod_elems, TILE_N, 1, t.shift, 0});
+            klen.push_back(kl);
+            prod_elems += static_cast<int64_t>(TILE_M) * TILE_N;
+            P.leaf_madds += static_cast<double>(kl) * TILE_M * TILE_N;
+        }
+        P.plain_madds += static_cast<double>(m) * TILE_M * TILE_N;
+        add_comb(r0, c0, rows, cols, terms, klen, c0 + cols - 1 > r0);
     }
 
     // Leaf K-steps of the lower triangle of a w-wide panel under the default
@@ -678,21 +732,55 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         return false;
     }
 
-    Builder B(P);
-    if (P.variant == VARIANT_WINOGRAD) {
-        B.tU = wU;
-        B.tV = wV;
-        B.tW = wW;
+    // Build the task lists, with `split` contraction chunks per plain tile.
+    std::unique_ptr<Builder> Bp;
+    auto build = [&](int split) {
+        P.families.clear();
+        P.ops.clear();
+        P.terms.clear();
+        P.tasks.clear();
+        P.combs.clear();
+        P.cterms.clear();
+        P.blocks.clear();
+        P.n_panels = P.n_blocks = P.n_products = P.n_reused = 0;
+        P.n_units = 0;
+        P.comb_tiles = 0;
+        P.leaf_madds = P.plain_madds = 0;
+        Bp.reset(new Builder(P));
+        Builder &B = *Bp;
+        B.split_k = split;
+        if (P.variant == VARIANT_WINOGRAD) {
+            B.tU = wU;
+            B.tV = wV;
+            B.tW = wW;
+        }
+        if (B.digits) {
+            // Family 0: digit planes of A itself (diagonal panels, classical tiles).
+            Family f0{};
+            f0.K_pitch = round_up(std::max<int64_t>(pp.m, 1), PREP_K);
+            P.families.push_back(f0);
+            B.add_op(0, {OpTerm{0, 0, static_cast<int32_t>(pp.m), static_cast<int32_t>(pp.n), 1, 0}},
+                     pp.n);
+        }
+        if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
+    };
+    // Split contraction (digit modes): when the plan has too few tiles to keep
+    // every CTA busy and the contraction is long, or when asked for.
+    int split = 1;
+    const bool can_split = pp.mode != MODE_F64;
+    if (can_split && pp.split_k > 1) split = std::min(pp.split_k, SPLITK_MAX);
+    build(split);
+    const int ctas = pp.num_ctas > 1 ? pp.num_ctas : 152;
+    if (can_split && pp.split_k == 0 && static_cast<int64_t>(P.tasks.size()) < SPLITK_TILES_PER_CTA * ctas &&
+        pp.m >= 2 * SPLITK_MIN_ROWS) {
+        int64_t s = 2;
+        while (s < SPLITK_MAX && static_cast<int64_t>(P.tasks.size()) * s < SPLITK_TILES_PER_CTA * ctas &&
+               pp.m / (2 * s) >= SPLITK_MIN_ROWS)
+            s *= 2;
+        build(static_cast<int>(s));
     }
-    if (B.digits) {
-        // Family 0: digit planes of A itself (diagonal panels, classical tiles).
-        Family f0{};
-        f0.K_pitch = round_up(std::max<int64_t>(pp.m, 1), PREP_K);
-        P.families.push_back(f0);
-        B.add_op(0, {OpTerm{0, 0, static_cast<int32_t>(pp.m), static_cast<int32_t>(pp.n), 1, 0}},
-                 pp.n);
-    }
-    if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
+    Builder &B = *Bp;
+    P.split_k = B.split_k;
 
     P.n_tiles = static_cast<int64_t>(P.tasks.size());
     if (pp.streams > 1 && !P.tasks.empty())

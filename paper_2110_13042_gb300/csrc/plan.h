@@ -193,7 +193,18 @@ struct CombDesc {
     int64_t tile_base;   // prefix count of combine tiles (COMB_ROWS x COMB_COLS)
     int32_t rshift;      // products are summed in units 2^(smin + rshift)
     int32_t smin;        // smallest term shift
+    int32_t diag;        // 1: the region crosses the diagonal: write only where
+    int32_t diag_off;    //    col <= row + diag_off (split contraction of a diagonal tile)
 };
+
+// Split contraction: plain tiles of a plan with few tiles and a long
+// contraction are computed as this many contraction chunks (exact partial
+// products in the product workspace) summed by the combine in a fixed order,
+// when the tile count is below SPLITK_TILES_PER_CTA x the CTA count and
+// every chunk keeps at least SPLITK_MIN_ROWS rows.
+constexpr int SPLITK_TILES_PER_CTA = 4;
+constexpr int64_t SPLITK_MIN_ROWS = 4096;
+constexpr int SPLITK_MAX = 16;
 constexpr int COMB_ROWS = 64;  // combine tile: 64 rows x 32 columns, 8 rows per thread
 constexpr int COMB_COLS = 32;
 
@@ -225,6 +236,8 @@ struct PlanParams {
     int variant = VARIANT_STRASSEN;  // coefficient tables of the off-diagonal products
     int streams = 1;         // > 1: static partition of the recursion's units over
                              // this many leaf launches on their own streams
+    int split_k = 0;         // contraction chunks per plain tile: 0 = automatic
+                             // (few tiles, long contraction), 1 = never, > 1 = that many
 };
 
 // One leaf launch of a static partition: tasks [first, first + count) of the
@@ -242,6 +255,7 @@ inline int64_t packed_index(int64_t j, int64_t k) { return j * (j + 1) / 2 + k; 
 struct Plan {
     PlanParams p;
     int cutoff = 0, depth = 0, slices = 0, strassen_min = 0, variant = VARIANT_STRASSEN;
+    int split_k = 1;       // contraction chunks per plain tile (1: none)
     int64_t n_panels = 0, n_blocks = 0, n_products = 0;
     int64_t n_reused = 0;  // Strassen operands read from the planes of A
     int64_t n_tiles = 0;   // leaf tiles (tasks also holds empty balance fillers)

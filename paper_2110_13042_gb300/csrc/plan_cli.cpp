@@ -28,6 +28,7 @@ int main(int argc, char **argv) {
     pp.num_ctas = argc > 9 ? std::atoi(argv[9]) : 0;
     pp.variant = argc > 10 ? std::atoi(argv[10]) : 0;
     pp.streams = argc > 11 ? std::atoi(argv[11]) : 1;
+    pp.split_k = argc > 12 ? std::atoi(argv[12]) : 0;
     Plan P;
     std::string err;
     if (!make_plan(pp, &P, &err)) {
@@ -57,7 +58,8 @@ int main(int argc, char **argv) {
         const int64_t r0 = d.c_off / ldc, c0 = d.c_off % ldc;
         s_plain += static_cast<double>(pp.m) * d.rows * d.cols;
         for (int r = 0; r < d.rows; ++r)
-            for (int c = 0; c < d.cols; ++c) cov[(r0 + r) * n + c0 + c]++;
+            for (int c = 0; c < d.cols; ++c)
+                if (!d.diag || c <= r + d.diag_off) cov[(r0 + r) * n + c0 + c]++;
     }
     // Prep tiles: walk the flat tile range the way the prep kernels map it
     // (last operand with tile_base <= tile, then the interleaved group) and
