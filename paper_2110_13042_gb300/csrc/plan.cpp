@@ -235,7 +235,11 @@ struct Builder {
             const OpTerm &t = tt[0];
             const Family &f0 = P.families[0];
             const int64_t f0_cols = round_up(std::max<int64_t>(P.p.n, 1), TILE) + TILE;
-            const bool rows_ok = t.rows == rn || (t.row0 + t.rows == P.p.m && t.row0 + rn <= f0.K_pitch);
+            // The leaf reads whole K steps: the rows from rn up to the next
+            // step boundary must be zero, i.e. rn is a whole number of steps,
+            // or the region ends at the end of A (family 0 is zero below m).
+            const bool rows_ok = (t.rows == rn && rn % kalign == 0) ||
+                                 (t.row0 + t.rows == P.p.m && t.row0 + rn <= f0.K_pitch);
             const bool cols_ok = t.cols == nominal_cols || t.col0 + t.cols == P.p.n;
             if (t.row0 % kalign == 0 && t.col0 % BLOCK_COLS == 0 && rows_ok && cols_ok &&
                 t.col0 + round_up(nominal_cols, TILE) <= f0_cols) {

@@ -135,6 +135,74 @@ int main(int argc, char **argv) {
         }
         if (next != static_cast<int64_t>(P.tasks.size()) || ctas > G) groups_ok = false;
     }
+    // Execute the plan's tables in plain FP64 on a small-integer A (every
+    // step exact): operand sums into the families, leaf tiles over them
+    // (family 0 is A itself), the result sums; compare with A^T A.
+    double verify_err = -1.0;
+    bool bounds_ok = true;  // every leaf read stays inside its family's rows
+    if (argc > 13 && std::atoi(argv[13]) == 1 && pp.mode != MODE_F64) {
+        const int64_t m = pp.m;
+        std::vector<double> A(static_cast<size_t>(m * n));
+        uint64_t z = 2110;
+        for (double &a : A) {
+            z = z * 6364136223846793005ull + 1442695040888963407ull;
+            a = static_cast<double>(static_cast<int>((z >> 33) % 9) - 4);
+        }
+        std::vector<std::vector<double>> fam(P.families.size());
+        for (size_t f = 0; f < P.families.size(); ++f)
+            fam[f].assign(static_cast<size_t>(P.families[f].K_pitch * P.families[f].cols), 0.0);
+        for (const OpDesc &o : P.ops) {
+            const Family &F = P.families[static_cast<size_t>(o.family)];
+            for (int t = 0; t < o.nterms; ++t) {
+                const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+                for (int k = 0; k < tm.rows; ++k)
+                    for (int c = 0; c < tm.cols; ++c)
+                        fam[static_cast<size_t>(o.family)][static_cast<size_t>(k * F.cols + o.out_col + c)] +=
+                            tm.coef * A[static_cast<size_t>((tm.row0 + k) * n + tm.col0 + c)];
+            }
+        }
+        std::vector<double> Cv(static_cast<size_t>(n * n), 0.0), M(static_cast<size_t>(P.product_bytes / 8 + 1), 0.0);
+        for (const LeafTask &t : P.tasks) {
+            if (t.klen == 0) continue;
+            const Family &FU = P.families[static_cast<size_t>(t.fam_u)], &FV = P.families[static_cast<size_t>(t.fam_v)];
+            const std::vector<double> &U = fam[static_cast<size_t>(t.fam_u)], &V = fam[static_cast<size_t>(t.fam_v)];
+            for (int r = 0; r < t.rows; ++r)
+                for (int c = 0; c < t.cols; ++c) {
+                    if (t.diag && c > r + t.diag_off) continue;
+                    // the leaf reads whole K steps of `ks` rows, inside the families
+                    const int ks = kstep_rows(pp.mode);
+                    const int kread = (t.klen + ks - 1) / ks * ks;
+                    if (t.k0 + kread > FU.K_pitch || t.k0v + kread > FV.K_pitch) bounds_ok = false;
+                    double s = 0;
+                    for (int k = 0; k < kread && t.k0 + k < FU.K_pitch && t.k0v + k < FV.K_pitch; ++k)
+                        s += U[static_cast<size_t>((t.k0 + k) * FU.cols + t.col_u + r)] *
+                             V[static_cast<size_t>((t.k0v + k) * FV.cols + t.col_v + c)];
+                    if (t.kind == OUT_M_I64 || t.kind == OUT_M_F64)
+                        M[static_cast<size_t>(t.out_off + r * t.out_ld + c)] = s;
+                    else
+                        Cv[static_cast<size_t>(t.out_off + r * t.out_ld + c)] = s;
+                }
+        }
+        for (const CombDesc &d : P.combs)
+            for (int r = 0; r < d.rows; ++r)
+                for (int c = 0; c < d.cols; ++c) {
+                    if (d.diag && c > r + d.diag_off) continue;
+                    double s = 0;
+                    for (int i = 0; i < d.nterms; ++i) {
+                        const CombTerm &ct = P.cterms[static_cast<size_t>(d.first_term + i)];
+                        s += ct.coef * M[static_cast<size_t>(ct.src_off + r * ct.ld + c)];
+                    }
+                    Cv[static_cast<size_t>(d.c_off + r * ldc + c)] = s;
+                }
+        verify_err = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t k = 0; k <= j; ++k) {
+                double s = 0;
+                for (int64_t i = 0; i < m; ++i) s += A[static_cast<size_t>(i * n + j)] * A[static_cast<size_t>(i * n + k)];
+                verify_err = std::max(verify_err, std::abs(s - Cv[static_cast<size_t>(j * n + k)]));
+            }
+    }
+    std::printf("verify_err=%g verify_bounds_ok=%d ", verify_err, bounds_ok ? 1 : 0);
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
                 "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "

@@ -18,9 +18,10 @@ def cli(tmp_path_factory):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", src, os.path.join(src, "plan_cli.cpp"),
                     os.path.join(src, "plan.cpp"), "-o", out], check=True)
 
-    def run(m, n, mode, cutoff, depth, smin, streams, variant=0):
+    def run(m, n, mode, cutoff, depth, smin, streams, variant=0, split=0, verify=0):
         r = subprocess.run([out, str(m), str(n), str(mode), str(cutoff), str(depth), "0", str(smin), "1", "152",
-                            str(variant), str(streams)], capture_output=True, text=True, check=True)
+                            str(variant), str(streams), str(split), str(verify)], capture_output=True, text=True,
+                           check=True)
         return {k: float(v) for k, v in (kv.split("=") for kv in r.stdout.split())}
     return run
 
@@ -47,3 +48,19 @@ def test_partition_is_a_static_comparison_not_a_speedup(cli):
     for s in (2, 4, 8):
         part = cli(8192, 8192, 1, 0, 1, 4096, s)
         assert part["group_steps_max"] >= one["cta_steps_max"]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,streams,split", [
+    (531, 700, 1, 350, 1, 2, 1, 0), (250, 330, 1, 0, 2, 16, 1, 0), (129, 515, 4, 0, 8, 16, 1, 0),
+    (300, 257, 2, 32, 1, 2, 4, 0), (1300, 200, 1, 0, 0, 4096, 1, 4), (701, 300, 5, 64, 1, 2, 3, 3),
+    (333, 401, 2, 100, 3, 8, 2, 2)])
+def test_plan_tables_compute_the_product(cli, variant, m, n, mode, cutoff, depth, smin, streams, split):
+    """plan_cli's interpreter executes the plan's operand, leaf and combine
+    tables in FP64 on a small-integer A (every step exact), reading whole K
+    steps as the leaf does, and compares with the direct A^T A: a wrong
+    coefficient, offset, term, sum or contraction tail anywhere in the planner
+    shows as a nonzero error (an odd m with both operands of a Winograd
+    product read in place from A caught one such tail)."""
+    r = cli(m, n, mode, cutoff, depth, smin, streams, variant=variant, split=split, verify=1)
+    assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
