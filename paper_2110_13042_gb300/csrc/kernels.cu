@@ -507,8 +507,14 @@ __global__ void __launch_bounds__(256, batched_prep_blocks<T, S>()) batched_prep
                                                               const int *__restrict__ expo, int64_t ntiles,
                                                               uint8_t *planes) {
     __shared__ int64_t sV[PREP_SV];
-    int64_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
+    // Each block takes a contiguous range of tiles, so its problem cursor
+    // moves by at most a few problems over the whole range (a grid-stride
+    // walk would skip gridDim.x tiles, i.e. several small problems, per step,
+    // each skip a dependent load before the tile's data loads can start).
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    int64_t tile = static_cast<int64_t>(blockIdx.x) * per;
+    const int64_t tile_end = tile + per < ntiles ? tile + per : ntiles;
+    if (tile >= tile_end) return;
     int64_t lo = 0, hi = count - 1;  // last problem with prep_base <= tile
     while (lo < hi) {
         const int64_t mid = (lo + hi + 1) >> 1;
@@ -518,7 +524,7 @@ __global__ void __launch_bounds__(256, batched_prep_blocks<T, S>()) batched_prep
             hi = mid - 1;
     }
     int64_t pi = lo;
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (; tile < tile_end; ++tile) {
         while (pi + 1 < count && probs[pi + 1].prep_base <= tile) ++pi;
         const BatchProb &bp = probs[pi];
         OpDesc od{};

@@ -804,6 +804,20 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         }
     }
 
+    // An operand summed from 2^t nonempty blocks is held with t fewer fraction
+    // bits, so a product of two such operands is t_u + t_v bits coarser than a
+    // plain tile.  Deep recursion (and Winograd's four-term operands) can lose
+    // more than the accuracy target leaves spare: with the digit count on auto,
+    // such a plan gets one more 9-bit digit (F64_EMU: 6 bits spare at 6 digits
+    // for the 1e-13 target; F32: 8 bits at 3 digits for 5e-5).
+    if (pp.slices == 0 && (pp.mode == MODE_F64_EMU || pp.mode == MODE_F32)) {
+        int tmax = 0;
+        for (const LeafTask &t : P.tasks)
+            if (t.kind == OUT_M_I64) tmax = std::max(tmax, t.shift + t.hbits);
+        const int spare = pp.mode == MODE_F64_EMU ? 6 : 8;
+        if (tmax > spare && P.slices < MAX_SLICES) P.slices += 1;
+    }
+
     // Workspace layout.
     int64_t off = 0;
     auto take = [&](int64_t bytes) {

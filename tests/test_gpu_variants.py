@@ -68,6 +68,20 @@ def test_winograd_random_within_tolerance(ata, mode, depth, m, n):
     assert float(np.max(np.abs(C[low] - ref[low]) / D[low])) <= TOL[mode]
 
 
+@pytest.mark.parametrize("mode", [F64_EMU, F32])
+def test_winograd_depth_three_keeps_the_tolerance(ata, mode):
+    """Winograd's flattened operands sum up to 4^d blocks, so at depth 3 a
+    product is up to 12 fraction bits coarser; with the digit count on auto
+    the plan adds a digit and the result stays within the mode's target."""
+    m, n = 1024, 1024
+    A = inputs.uniform(m, n, seed=77)
+    C, info = run(ata, A, mode, cutoff=0, depth=3, strassen_min=64, variant=WINOGRAD)
+    assert info["depth"] == 3 and info["slices"] == (7 if mode == F64_EMU else 4)
+    ref, D = oracle.ata_lower(A), oracle.abs_ata_lower(A)
+    low = np.tril_indices(n)
+    assert float(np.max(np.abs(C[low] - ref[low]) / D[low])) <= TOL[mode]
+
+
 @pytest.mark.parametrize("variant", [0, WINOGRAD])
 @pytest.mark.parametrize("mode", [F64_EMU, F32, F64])
 def test_recursion_to_size_cutoff(ata, variant, mode):
