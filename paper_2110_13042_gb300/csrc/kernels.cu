@@ -683,10 +683,93 @@ __device__ __forceinline__ int find_comb(const CombDesc *d, int nd, int64_t tile
 // global memory (the same entries for the whole block).
 constexpr int COMB_RPT = COMB_ROWS / 8;  // rows per thread
 
+// An int128 as the nearest double: the top 64 significant bits with a
+// sticky bit for the rest are rounded once by the 64-bit conversion (the
+// sticky bit lies 11 places below the rounding point, so ties stay exact).
+__device__ __forceinline__ double i128_to_double(__int128 s) {
+    const bool neg = s < 0;
+    const unsigned __int128 u = neg ? static_cast<unsigned __int128>(0) - static_cast<unsigned __int128>(s)
+                                    : static_cast<unsigned __int128>(s);
+    const uint64_t hi = static_cast<uint64_t>(u >> 64), lo = static_cast<uint64_t>(u);
+    double r;
+    if (hi == 0) {
+        r = __ull2double_rn(lo);
+    } else {
+        const int sh = 64 - __clzll(static_cast<long long>(hi));  // 1..64
+        const uint64_t below = sh == 64 ? lo : lo & ((1ull << sh) - 1);
+        const uint64_t top = static_cast<uint64_t>(u >> sh) | (below != 0 ? 1ull : 0ull);
+        r = __ull2double_rn(top) * exp2i(sh);
+    }
+    return neg ? -r : r;
+}
+
+// v * 2^sh in the accumulator type (the shift done on the unsigned bits).
+template <typename Acc>
+__device__ __forceinline__ Acc shl(int64_t v, int sh) {
+    if constexpr (sizeof(Acc) == 16)
+        return static_cast<__int128>(static_cast<unsigned __int128>(static_cast<__int128>(v)) << sh);
+    else
+        return static_cast<int64_t>(static_cast<uint64_t>(v) << sh);
+}
+
+template <typename Acc>
+__device__ __forceinline__ double acc_to_double(Acc s) {
+    if constexpr (sizeof(Acc) == 16) return i128_to_double(s);
+    else return static_cast<double>(s);
+}
+
+template <typename Acc>
+__device__ __forceinline__ float acc_to_float(Acc s) {
+    if constexpr (sizeof(Acc) == 16) return static_cast<float>(i128_to_double(s));
+    else return __ll2float_rn(s);
+}
+
 // Exact Strassen result sums: region = sum_r coef_r * T_r * 2^(shift_r),
-// added in int64 in units of 2^(smin + rshift) (rshift > 0 only when the
-// worst case would overflow; the dropped bits are far below FP64 resolution),
-// then one rounding to the output type and the column scale 2^(e_j + e_k).
+// added in units of 2^smin (the smallest term shift), then one rounding to
+// the output type and the column scale 2^(e_j + e_k).  The sum is exact: in
+// int64 where the region's worst case stays below 2^62, else (d.wide: deep
+// recursion and Winograd's operands give products up to 2^(t_u + t_v) above
+// a plain one, which cancel in the sum) in int128.
+template <typename Acc, typename TOut>
+__device__ __forceinline__ void combine_region(const CombDesc &d, int r0, int col,
+                                               const CombTerm *__restrict__ cterms,
+                                               const int64_t *__restrict__ M, TOut *C, int64_t ldc, bool packed,
+                                               const int *__restrict__ expo, double alpha, double beta) {
+    Acc sum[COMB_RPT];
+#pragma unroll
+    for (int i = 0; i < COMB_RPT; ++i) sum[i] = 0;
+    for (int t = 0; t < d.nterms; ++t) {
+        const CombTerm ct = cterms[d.first_term + t];
+        const int64_t *src = M + ct.src_off + col;
+        int64_t v[COMB_RPT];
+#pragma unroll
+        for (int i = 0; i < COMB_RPT; ++i) {
+            const int row = r0 + 8 * i;
+            v[i] = row < d.rows ? src[static_cast<int64_t>(row) * ct.ld] : 0;
+        }
+        const int dsh = ct.shift - d.smin;  // >= 0
+#pragma unroll
+        for (int i = 0; i < COMB_RPT; ++i) {
+            const Acc x = shl<Acc>(v[i], dsh);
+            sum[i] += ct.coef > 0 ? x : -x;
+        }
+    }
+    const int xc = -(T_FRAC + 2 * DIGIT_TOP_BITS) + d.smin + expo[d.e_col0 + col];
+#pragma unroll
+    for (int i = 0; i < COMB_RPT; ++i) {
+        const int row = r0 + 8 * i;
+        if (row >= d.rows) break;
+        if (d.diag && col > row + d.diag_off) continue;  // upper triangle: never written
+        const int x = xc + expo[d.e_row0 + row];
+        TOut *c = packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
+                         : C + d.c_off + static_cast<int64_t>(row) * ldc + col;
+        if constexpr (sizeof(TOut) == 8)
+            store_scaled(c, acc_to_double(sum[i]) * exp2i(x), alpha, beta);
+        else
+            store_scaled(c, acc_to_float(sum[i]) * exp2f_i(x), alpha, beta);
+    }
+}
+
 template <typename TOut>
 __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__restrict__ descs, int nd,
                                                           const CombTerm *__restrict__ cterms,
@@ -699,43 +782,10 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
     const int r0 = static_cast<int>(local / tcols) * COMB_ROWS + (threadIdx.x >> 5);
     const int col = static_cast<int>(local % tcols) * COMB_COLS + (threadIdx.x & 31);
     if (col >= d.cols) return;
-    int64_t sum[COMB_RPT];
-#pragma unroll
-    for (int i = 0; i < COMB_RPT; ++i) sum[i] = 0;
-    for (int t = 0; t < d.nterms; ++t) {
-        const CombTerm ct = cterms[d.first_term + t];
-        const int64_t *src = M + ct.src_off + col;
-        int64_t v[COMB_RPT];
-#pragma unroll
-        for (int i = 0; i < COMB_RPT; ++i) {
-            const int row = r0 + 8 * i;
-            v[i] = row < d.rows ? src[static_cast<int64_t>(row) * ct.ld] : 0;
-        }
-        const int dsh = ct.shift - d.smin - d.rshift;
-#pragma unroll
-        for (int i = 0; i < COMB_RPT; ++i) {
-            int64_t x = v[i];
-            if (dsh >= 0)
-                x = x * (int64_t(1) << dsh);
-            else
-                x = (x + (int64_t(1) << (-dsh - 1))) >> (-dsh);
-            sum[i] += ct.coef > 0 ? x : -x;
-        }
-    }
-    const int xc = -(T_FRAC + 2 * DIGIT_TOP_BITS) + d.smin + d.rshift + expo[d.e_col0 + col];
-#pragma unroll
-    for (int i = 0; i < COMB_RPT; ++i) {
-        const int row = r0 + 8 * i;
-        if (row >= d.rows) break;
-        if (d.diag && col > row + d.diag_off) continue;  // upper triangle: never written
-        const int x = xc + expo[d.e_row0 + row];
-        TOut *c = packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
-                         : C + d.c_off + static_cast<int64_t>(row) * ldc + col;
-        if constexpr (sizeof(TOut) == 8)
-            store_scaled(c, static_cast<double>(sum[i]) * exp2i(x), alpha, beta);
-        else
-            store_scaled(c, __ll2float_rn(sum[i]) * exp2f_i(x), alpha, beta);
-    }
+    if (d.wide)
+        combine_region<__int128>(d, r0, col, cterms, M, C, ldc, packed, expo, alpha, beta);
+    else
+        combine_region<int64_t>(d, r0, col, cterms, M, C, ldc, packed, expo, alpha, beta);
 }
 
 // Native FP64 (and FP8-mode) result sums, in the fixed term order, then the

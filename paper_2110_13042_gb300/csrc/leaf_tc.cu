@@ -206,8 +206,8 @@ __device__ __forceinline__ void issue_own(uint32_t tmem, uint64_t da0, uint64_t 
 // merged with its right neighbour when adjacent.  The issuer waits for the
 // drains of group A's accumulators before it, and of 2 and 3 only before
 // group B, so that drain overlaps group A.  (Measured: 6-11% faster for 1-4
-// digits; for 5-7 digits the variants of this scheme measured slower than the
-// fast/slow split below.)
+// digits.  With 5-7 digits one issuing thread cannot keep the pipe busy, and
+// the accumulators are split over several issuers instead: issue_own above.)
 template <int S, bool GB, int P = 1, int Q = 1>
 __device__ __forceinline__ void issue_group(uint32_t tmem, uint64_t da0, uint64_t db0) {
     if constexpr (P <= S) {

@@ -108,6 +108,7 @@ struct Builder {
     const int (*tW)[4] = kW;
     int64_t prod_elems = 0;
     int split_k = 1;  // contraction chunks per plain tile (split contraction)
+    double comb_bound_max = 0;  // largest worst-case combine sum, units 2^smin
 
     explicit Builder(Plan &p)
         : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)) {}
@@ -353,10 +354,10 @@ struct Builder {
 
     // One combine region C[r0:r0+rows, c0:c0+cols] = sum of `terms` (products
     // in the workspace; term i over a contraction of klen[i] rows).  The exact
-    // products are summed in units 2^(smin + rshift), with rshift > 0 only if
-    // the worst case (|T| <= 1.004 K 2^(T_BOUND_LOG2 + h) per product) could
-    // reach 2^62.  diag: the region crosses the diagonal, only entries with
-    // col <= row + (r0 - c0) are written.
+    // products are summed exactly in units 2^smin: in int64 when the worst case
+    // (|T| <= 1.004 K 2^(T_BOUND_LOG2 + h) per product, scaled by its shift)
+    // stays below 2^62, else in int128 (wide).  diag: the region crosses the
+    // diagonal, only entries with col <= row + (r0 - c0) are written.
     void add_comb(int64_t r0, int64_t c0, int64_t rows, int64_t cols, const std::vector<CombTerm> &terms,
                   const std::vector<int64_t> &klen, bool diag) {
         CombDesc c{};
@@ -372,16 +373,14 @@ struct Builder {
         c.nterms = static_cast<int32_t>(terms.size());
         int smin = 1 << 20;
         for (const CombTerm &t : terms) smin = std::min(smin, t.shift);
-        c.rshift = 0;
+        c.wide = 0;
         if (digits && !fp8) {
-            for (;;) {
-                double bound = 0;
-                for (size_t i = 0; i < terms.size(); ++i)
-                    bound += 1.004 * static_cast<double>(klen[i]) *
-                             std::ldexp(1.0, T_BOUND_LOG2 + hbits_for(klen[i]) + terms[i].shift - smin - c.rshift);
-                if (bound < std::ldexp(1.0, 62)) break;
-                c.rshift++;
-            }
+            double bound = 0;
+            for (size_t i = 0; i < terms.size(); ++i)
+                bound += 1.004 * static_cast<double>(klen[i]) *
+                         std::ldexp(1.0, T_BOUND_LOG2 + hbits_for(klen[i]) + terms[i].shift - smin);
+            c.wide = bound >= std::ldexp(1.0, 62) ? 1 : 0;
+            comb_bound_max = std::max(comb_bound_max, bound);
         }
         c.smin = smin;
         c.tile_base = P.comb_tiles;
@@ -785,6 +784,10 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     }
     Builder &B = *Bp;
     P.split_k = B.split_k;
+    if (B.comb_bound_max >= std::ldexp(1.0, 125)) {  // the int128 sum keeps 2 bits of margin
+        if (err) *err = "internal: a combine sum could overflow 128 bits";
+        return false;
+    }
 
     P.n_tiles = static_cast<int64_t>(P.tasks.size());
     if (pp.streams > 1 && !P.tasks.empty())

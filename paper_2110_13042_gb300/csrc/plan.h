@@ -191,8 +191,8 @@ struct CombDesc {
     int32_t e_col0;      // A column of region column 0
     int32_t first_term, nterms;
     int64_t tile_base;   // prefix count of combine tiles (COMB_ROWS x COMB_COLS)
-    int32_t rshift;      // products are summed in units 2^(smin + rshift)
-    int32_t smin;        // smallest term shift
+    int32_t wide;        // 1: the worst-case sum reaches 2^62: summed in int128
+    int32_t smin;        // smallest term shift; products are summed in units 2^smin
     int32_t diag;        // 1: the region crosses the diagonal: write only where
     int32_t diag_off;    //    col <= row + diag_off (split contraction of a diagonal tile)
 };

@@ -202,7 +202,10 @@ int main(int argc, char **argv) {
                 verify_err = std::max(verify_err, std::abs(s - Cv[static_cast<size_t>(j * n + k)]));
             }
     }
-    std::printf("verify_err=%g verify_bounds_ok=%d ", verify_err, bounds_ok ? 1 : 0);
+    int64_t wide = 0;  // combine regions summed in int128
+    for (const CombDesc &d : P.combs) wide += d.wide;
+    std::printf("verify_err=%g verify_bounds_ok=%d wide_regions=%lld ", verify_err, bounds_ok ? 1 : 0,
+                static_cast<long long>(wide));
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
                 "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "

@@ -64,3 +64,15 @@ def test_plan_tables_compute_the_product(cli, variant, m, n, mode, cutoff, depth
     product read in place from A caught one such tail)."""
     r = cli(m, n, mode, cutoff, depth, smin, streams, variant=variant, split=split, verify=1)
     assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
+
+
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,expect_wide", [
+    (600, 1111, 1, 300, 8, 64, 1, True),    # Winograd down to 64 columns: 2^16-coarser products
+    (1024, 1024, 1, 0, 3, 64, 1, True),
+    (8192, 8192, 1, 0, 0, 4096, 0, False),  # plain tiles: no combine at all
+    (700, 900, 5, 0, 2, 2, 0, False)])      # FP8 sums products in FP64
+def test_wide_combine_regions(cli, m, n, mode, cutoff, depth, smin, variant, expect_wide):
+    """A combine region whose worst-case exact sum reaches 2^62 is summed in
+    int128 (no bits dropped), as deep Winograd plans need."""
+    r = cli(m, n, mode, cutoff, depth, smin, 1, variant=variant)
+    assert (r["wide_regions"] > 0) == expect_wide
