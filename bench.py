@@ -523,6 +523,16 @@ def main():
                 "traffic_unit": "DRAM bytes per leaf launch (ncu, profiles/)",
                 "peak_source": psrc,
                 "work": f"{pairs} digit pairs x 2 x {info['leaf_madds']} tile multiply-adds"}
+        if clk and clk.get("sm_mhz"):
+            # per clock: the leaf's flops per SM per cycle at the median SM
+            # clock of the timed region, against the dense MMA rate per SM
+            # (8192 BF16 / 16384 E4M3 flops per cycle: M=128, N=256, K=16 or
+            # 32 in 128 cycles)
+            per_sm = 16384.0 if mode == 5 else 8192.0
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            fpc = achieved * 1e12 / (sms * clk["sm_mhz"] * 1e6)
+            roof["per_clock"] = {"flop_per_clk_per_sm": fpc, "of": per_sm, "frac": fpc / per_sm,
+                                 "sm_mhz": clk["sm_mhz"]}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
