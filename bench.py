@@ -547,7 +547,7 @@ def main():
                             f"C {C.numel() * C.element_size() / 2**20:.0f} MiB)"},
            "roofline": roof,
            "phases_ms": {"colexp": ph[0], "prep": ph[1], "leaf": ph[2], "combine": ph[3]},
-           "gpu_launches": args.steps * (4 + (1 if info["products"] else 0)),
+           "gpu_launches": args.steps * (4 + (1 if info["products"] else 0) + (1 if info["fused_groups"] else 0)),
            "clocks": clk}
 
     if not args.no_extras and not args.aat:

@@ -371,6 +371,7 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     out[8] = static_cast<int64_t>(P.leaf_madds);
     out[9] = static_cast<int64_t>(P.plain_madds);
     out[10] = P.split_k;
+    out[11] = P.n_fused;
     return ATA_OK;
 }
 

@@ -162,6 +162,10 @@ __device__ __forceinline__ int op_of_tile(const OpDesc *ops, int nops, int64_t t
     int i = find_desc(ops, nops, tile);
     const int64_t g = tile - ops[i].tile_base;
     const int n = ops[i].ilv_n;
+    if (ops[i].fuse_ns > 0) {  // fused group: tile g of every member, led by member 0
+        *local = g;
+        return i - ops[i].ilv_i;
+    }
     if (n > 1) {  // tile counts fit 32 bits (checked at launch): 32-bit division
         const uint32_t g32 = static_cast<uint32_t>(g);
         const uint32_t q = g32 / static_cast<uint32_t>(n);
@@ -467,12 +471,143 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     __syncthreads();  // sV is reused by the block's next tile
 }
 
+// Half an image row: contraction values 8h .. 8h + 7 of one column, digit
+// Q .. S - 1 of each, one 16-byte store per digit plane (slot h ^ swz).
+template <int S, int Q = 0, typename W>
+__device__ __forceinline__ void store_digits_half(const W (&w)[8], uint8_t *row0, int64_t plane_step, int slot) {
+    if constexpr (Q < S) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 v =
+                __floats2bfloat162_rn(digit_value<S, Q>(w[2 * i]), digit_value<S, Q>(w[2 * i + 1]));
+            pk[i] = *reinterpret_cast<const uint32_t *>(&v);
+        }
+        *reinterpret_cast<uint4 *>(row0 + Q * plane_step + (slot << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        store_digits_half<S, Q + 1, W>(w, row0, plane_step, slot);
+    }
+}
+
+// One prep tile (16 contraction rows x 256 columns, one column per thread)
+// of every operand of a fused group (OpDesc::fuse_ns): the thread loads its
+// column's rows of each of the group's source blocks once, eight rows at a
+// time, and writes its half image rows of every member's digit planes.  Each
+// member's value is the one prep_tile writes: every term rounded with the
+// member's t_shift and the terms summed exactly; with fuse_uni (one t_shift
+// for the whole group) each source value is rounded once for all members.
+template <int S, typename T, bool UNI>
+__device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t lda, bool trans,
+                                                const int *__restrict__ expo, const OpDesc *o, int lead,
+                                                const OpTerm *terms, const OpTerm *__restrict__ fsrc,
+                                                int64_t local, const Families &fams, uint8_t *ws) {
+    constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
+    constexpr bool NARROW = sizeof(T) == 4 && F <= 29;
+    using V = typename std::conditional<NARROW, int32_t, int64_t>::type;
+    using W = typename std::conditional<(S <= 3), int32_t, int64_t>::type;
+    constexpr int NS = FUSE_MAX_SRC;
+    auto fixed = [](T a, int sh) -> V {
+        if constexpr (NARROW)
+            return fixed32_of_fast<F>(static_cast<float>(a), sh);
+        else if constexpr (FastFixed<F, T>::ok)
+            return fixed_of_fast<F>(a, sh);
+        else
+            return fixed_of(a, sh);
+    };
+    constexpr int64_t CADD = [] {
+        int64_t v = 0;
+        for (int j = 0; j < S - 1; ++j) v += int64_t(256) << (DIGIT_BITS * j);
+        return v;
+    }();
+    const OpDesc &L = o[lead];
+    const int ns = L.fuse_ns, nm = L.ilv_n;
+    const int tiles_k = L.K_pitch / PREP_TK;
+    const int k0 = static_cast<int>(local % tiles_k) * PREP_TK;
+    const int c0 = static_cast<int>(local / tiles_k) * PREP_TC;
+    const int cc = threadIdx.x;
+    const int c = c0 + cc;
+    if (c >= L.P_pad) return;  // every member has the group's P_pad
+    const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
+    const T *base[NS];
+    int lim[NS], ex[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        const bool present = q < ns;
+        const OpTerm sb = present ? fsrc[L.fuse_src + q] : OpTerm{};
+        const bool cv = present && c < sb.cols;
+        base[q] = A + (sb.row0 + k0) * rs + (sb.col0 + c) * cs;
+        lim[q] = cv ? sb.rows - k0 : 0;
+        ex[q] = cv ? expo[sb.col0 + c] : 0;
+    }
+    const Family &fam = fams.f[L.family];
+    const int64_t ncb = fam.cols / BLOCK_COLS;
+    const int64_t plane_step = ncb * BLOCK_BYTES;
+    const int r = cc & (BLOCK_COLS - 1);
+    const int swz = (r >> 2) & 1;
+    const int64_t kstep = k0 / KSTEP;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        T raw[NS][8];
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) raw[q][j] = (8 * h + j) < lim[q] ? base[q][(8 * h + j) * rs] : T(0);
+        // UNI: every source value rounded once, for all members
+        V x[UNI ? NS : 1][8];
+        if constexpr (UNI) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int sh = F - L.t_shift - ex[q];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[q][j] = fixed(raw[q][j], sh);
+            }
+        }
+#pragma unroll 1
+        for (int mi = 0; mi < nm; ++mi) {
+            const OpDesc &od = o[lead + mi];
+            int cf[NS];  // the member's coefficient of each source block (0: absent)
+#pragma unroll
+            for (int q = 0; q < NS; ++q) cf[q] = 0;
+            for (int t = 0; t < od.nterms; ++t) {
+                const OpTerm tm = terms[od.first_term + t];
+#pragma unroll
+                for (int q = 0; q < NS; ++q)
+                    if (tm.src == q) cf[q] = tm.coef;
+            }
+            V v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                if (cf[q] == 0) continue;  // uniform over the block
+                const int sh = F - od.t_shift - ex[q];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    V y;
+                    if constexpr (UNI)
+                        y = x[q][j];
+                    else
+                        y = fixed(raw[q][j], sh);
+                    v[j] += cf[q] > 0 ? y : -y;
+                }
+            }
+            W w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = static_cast<W>(v[j]) + static_cast<W>(CADD);
+            const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
+            uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
+            store_digits_half<S>(w, row0, plane_step, h ^ swz);
+        }
+    }
+}
+
+// Prep tiles [tile_begin, ntiles) outside the fused groups.
 template <int S, typename T, bool F8 = false>
 __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict__ A, int64_t lda, bool trans,
                                                              const int *__restrict__ expo,
                                                              const OpDesc *__restrict__ ops, int nops,
                                                              const OpTerm *__restrict__ terms, int nterms,
-                                                             int64_t ntiles, Families fams, uint8_t *ws) {
+                                                             int64_t tile_begin, int64_t ntiles, Families fams,
+                                                             uint8_t *ws) {
     __shared__ int64_t sV[PREP_SV];
     __shared__ OpDesc s_ops[PREP_SMEM_OPS];
     __shared__ OpTerm s_terms[PREP_SMEM_TERMS];
@@ -484,12 +619,32 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     }
     const OpDesc *o = cached ? s_ops : ops;
     const OpTerm *tt = cached ? s_terms : terms;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t tile = tile_begin + blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
         const OpDesc &od = o[op_of_tile(o, nops, tile, &local)];  // read where used (register budget)
         // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
         prep_tile<S, T, F8>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV,
                             F8 ? 7 : 8);
+    }
+}
+
+// Prep tiles [0, ntiles) of the fused groups (which come first in the tile
+// range).  Two blocks per SM: a thread holds 8 rows of up to four source
+// blocks (64 registers for FP64) while it writes every member's digits.
+template <int S, typename T>
+__global__ void __launch_bounds__(256, 2) prep_fused_kernel(const T *__restrict__ A, int64_t lda, bool trans,
+                                                            const int *__restrict__ expo,
+                                                            const OpDesc *__restrict__ ops, int nops,
+                                                            const OpTerm *__restrict__ terms,
+                                                            const OpTerm *__restrict__ fsrc, int64_t ntiles,
+                                                            Families fams, uint8_t *ws) {
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int64_t local;
+        const int lead = op_of_tile(ops, nops, tile, &local);
+        if (ops[lead].fuse_uni)
+            prep_fused_tile<S, T, true>(A, lda, trans, expo, ops, lead, terms, fsrc, local, fams, ws);
+        else
+            prep_fused_tile<S, T, false>(A, lda, trans, expo, ops, lead, terms, fsrc, local, fams, ws);
     }
 }
 
@@ -703,33 +858,39 @@ __device__ __forceinline__ double i128_to_double(__int128 s) {
     return neg ? -r : r;
 }
 
-// v * 2^sh in the accumulator type (the shift done on the unsigned bits).
+// v * 2^sh in the accumulator type: int128, or uint64 for the sums taken
+// modulo 2^64 (the shift done on the unsigned bits).
 template <typename Acc>
 __device__ __forceinline__ Acc shl(int64_t v, int sh) {
     if constexpr (sizeof(Acc) == 16)
         return static_cast<__int128>(static_cast<unsigned __int128>(static_cast<__int128>(v)) << sh);
     else
-        return static_cast<int64_t>(static_cast<uint64_t>(v) << sh);
+        return static_cast<uint64_t>(v) << sh;
 }
 
+// The accumulated sum as a signed value (a uint64 sum is the two's
+// complement of the exact result, which fits in int64).
 template <typename Acc>
 __device__ __forceinline__ double acc_to_double(Acc s) {
     if constexpr (sizeof(Acc) == 16) return i128_to_double(s);
-    else return static_cast<double>(s);
+    else return static_cast<double>(static_cast<int64_t>(s));
 }
 
 template <typename Acc>
 __device__ __forceinline__ float acc_to_float(Acc s) {
     if constexpr (sizeof(Acc) == 16) return static_cast<float>(i128_to_double(s));
-    else return __ll2float_rn(s);
+    else return __ll2float_rn(static_cast<int64_t>(s));
 }
 
 // Exact Strassen result sums: region = sum_r coef_r * T_r * 2^(shift_r),
 // added in units of 2^smin (the smallest term shift), then one rounding to
-// the output type and the column scale 2^(e_j + e_k).  The sum is exact: in
-// int64 where the region's worst case stays below 2^62, else (d.wide: deep
-// recursion and Winograd's operands give products up to 2^(t_u + t_v) above
-// a plain one, which cancel in the sum) in int128.
+// the output type and the column scale 2^(e_j + e_k).  The sum is exact.
+// The terms can be far larger than the result (deep recursion and
+// Winograd's operands give products up to 2^(t_u + t_v) above a plain one,
+// and they cancel), but the result itself is an entry of A^T A, at most m
+// in scaled units.  Where that bound is below 2^63 in units of 2^smin, the
+// sum is taken modulo 2^64 (uint64 wraps; the exact result is its two's
+// complement value); else (d.wide) in int128.
 template <typename Acc, typename TOut>
 __device__ __forceinline__ void combine_region(const CombDesc &d, int r0, int col,
                                                const CombTerm *__restrict__ cterms,
@@ -785,7 +946,7 @@ __global__ void __launch_bounds__(256) combine_i64_kernel(const CombDesc *__rest
     if (d.wide)
         combine_region<__int128>(d, r0, col, cterms, M, C, ldc, packed, expo, alpha, beta);
     else
-        combine_region<int64_t>(d, r0, col, cterms, M, C, ldc, packed, expo, alpha, beta);
+        combine_region<uint64_t>(d, r0, col, cterms, M, C, ldc, packed, expo, alpha, beta);
 }
 
 // Native FP64 (and FP8-mode) result sums, in the fixed term order, then the
@@ -1016,18 +1177,30 @@ static void prep_digits_dispatch(const Plan &P, const void *A, bool is_f32, cons
                                  cudaStream_t s) {
     const OpDesc *ops = reinterpret_cast<const OpDesc *>(tables + P.t_ops);
     const OpTerm *terms = reinterpret_cast<const OpTerm *>(tables + P.t_terms);
-    const unsigned g = prep_grid(P.prep_tiles);
+    const OpTerm *fsrc = reinterpret_cast<const OpTerm *>(tables + P.t_fsrc);
     const int nops = static_cast<int>(P.ops.size()), nterms = static_cast<int>(P.terms.size());
     const bool tr = P.p.trans != 0;
+    const int64_t t0 = P.fused_tiles, nt = P.prep_tiles;
+    if (t0 > 0) {  // fused groups (digit modes other than FP8)
+        const unsigned gf = prep_grid(t0, 2);
+        if (is_f32)
+            prep_fused_kernel<S, float><<<gf, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, tr, expo, ops,
+                                                            nops, terms, fsrc, t0, F, ws);
+        else
+            prep_fused_kernel<S, double><<<gf, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, tr, expo,
+                                                             ops, nops, terms, fsrc, t0, F, ws);
+    }
+    if (nt <= t0) return;
+    const unsigned g = prep_grid(nt - t0);
     if (S == 1 && P.p.mode == MODE_F32_FP8)  // FP8 mode: float A, one E4M3 plane
         prep_digits_kernel<1, float, true><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, tr, expo,
-                                                              ops, nops, terms, nterms, P.prep_tiles, F, ws);
+                                                              ops, nops, terms, nterms, t0, nt, F, ws);
     else if (is_f32)
         prep_digits_kernel<S, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, tr, expo, ops,
-                                                        nops, terms, nterms, P.prep_tiles, F, ws);
+                                                        nops, terms, nterms, t0, nt, F, ws);
     else
         prep_digits_kernel<S, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, tr, expo, ops,
-                                                         nops, terms, nterms, P.prep_tiles, F, ws);
+                                                         nops, terms, nterms, t0, nt, F, ws);
 }
 
 cudaError_t launch_prep(const Plan &P, const void *A, bool is_f32, const int *expo,
@@ -1125,10 +1298,10 @@ cudaError_t launch_prep_digits_raw(int slices, const void *A, bool is_f32, int64
     case SS:                                                                                               \
         if (is_f32)                                                                                        \
             prep_digits_kernel<SS, float><<<g, 256, 0, s>>>(static_cast<const float *>(A), lda, false, expo, ops, \
-                                                             nops, terms, 1, prep_tiles, F, ws);           \
+                                                             nops, terms, 1, 0, prep_tiles, F, ws);           \
         else                                                                                               \
             prep_digits_kernel<SS, double><<<g, 256, 0, s>>>(static_cast<const double *>(A), lda, false, expo, \
-                                                              ops, nops, terms, 1, prep_tiles, F, ws);     \
+                                                              ops, nops, terms, 1, 0, prep_tiles, F, ws);     \
         break;
     switch (slices) {
         ATA_PREP_RAW(1)

@@ -354,10 +354,20 @@ struct Builder {
 
     // One combine region C[r0:r0+rows, c0:c0+cols] = sum of `terms` (products
     // in the workspace; term i over a contraction of klen[i] rows).  The exact
-    // products are summed exactly in units 2^smin: in int64 when the worst case
-    // (|T| <= 1.004 K 2^(T_BOUND_LOG2 + h) per product, scaled by its shift)
-    // stays below 2^62, else in int128 (wide).  diag: the region crosses the
-    // diagonal, only entries with col <= row + (r0 - c0) are written.
+    // products are summed exactly in units 2^smin.  The result is an entry of
+    // A^T A over m rows of column-scaled values below 1, so |result| <= m,
+    // i.e. <= g m 2^(T_BOUND_LOG2 - smin) in those units.  g covers the
+    // rounding of the operands: a product whose operands sum 2^t_u and 2^t_v
+    // blocks (t = t_u + t_v = shift + h) is off by at most
+    // K 2^t (2^(t_u - F) + 2^(t_v - F)) <= m 2^(2t + 1 - F) (F fraction bits
+    // of the digits at the planned digit count, which an added digit only
+    // makes finer), plus 1% for the leaf's rounded last accumulator.  Below
+    // 2^63 the kernel sums modulo 2^64, which
+    // is exact however large the terms; else in int128 (wide), whose worst
+    // case (|T| <= 1.004 K 2^(T_BOUND_LOG2 + h) per product, scaled by its
+    // shift) is checked against 2^125 once the plan is built.  diag: the
+    // region crosses the diagonal, only entries with col <= row + (r0 - c0)
+    // are written.
     void add_comb(int64_t r0, int64_t c0, int64_t rows, int64_t cols, const std::vector<CombTerm> &terms,
                   const std::vector<int64_t> &klen, bool diag) {
         CombDesc c{};
@@ -379,8 +389,13 @@ struct Builder {
             for (size_t i = 0; i < terms.size(); ++i)
                 bound += 1.004 * static_cast<double>(klen[i]) *
                          std::ldexp(1.0, T_BOUND_LOG2 + hbits_for(klen[i]) + terms[i].shift - smin);
-            c.wide = bound >= std::ldexp(1.0, 62) ? 1 : 0;
-            comb_bound_max = std::max(comb_bound_max, bound);
+            const int F = DIGIT_TOP_BITS + DIGIT_BITS * (P.slices - 1);
+            double g = 1.01;
+            for (size_t i = 0; i < terms.size(); ++i)
+                g += std::ldexp(1.0, 2 * (terms[i].shift + hbits_for(klen[i])) + 1 - F);
+            const double result_bound = g * static_cast<double>(P.p.m) * std::ldexp(1.0, T_BOUND_LOG2 - smin);
+            c.wide = result_bound >= std::ldexp(1.0, 63) ? 1 : 0;
+            if (c.wide) comb_bound_max = std::max(comb_bound_max, bound);
         }
         c.smin = smin;
         c.tile_base = P.comb_tiles;
@@ -495,6 +510,56 @@ struct Builder {
 };
 
 }  // namespace
+
+// Fuse an interleaved group of digit operands (same family and shape) when
+// its operands are sums of at most FUSE_MAX_SRC distinct blocks of A: the
+// blocks go to the plan's source list, every term records its block's index,
+// and the members are marked so that one prep tile serves them all (the
+// Strassen operand sums of one side of a block at depth 1 read the four
+// quadrants once instead of once per sum).  Returns false (nothing changed)
+// when the group does not qualify.
+static bool fuse_group(Plan &P, const std::vector<size_t> &members) {
+    if (members.size() < 2 || members.size() > static_cast<size_t>(FUSE_MAX_OPS)) return false;
+    std::vector<OpTerm> src;
+    for (size_t j : members) {
+        const OpDesc &o = P.ops[j];
+        for (int t = 0; t < o.nterms; ++t) {
+            const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+            bool found = false;
+            for (const OpTerm &s : src) {
+                if (s.row0 == tm.row0 && s.col0 == tm.col0) {
+                    if (s.rows != tm.rows || s.cols != tm.cols) return false;
+                    found = true;
+                }
+            }
+            if (!found) {
+                if (src.size() == static_cast<size_t>(FUSE_MAX_SRC)) return false;
+                src.push_back(tm);
+            }
+        }
+    }
+    const int32_t first = static_cast<int32_t>(P.fsrc.size());
+    bool uni = true;
+    for (size_t j : members) {
+        OpDesc &o = P.ops[j];
+        for (int t = 0; t < o.nterms; ++t) {
+            OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+            for (size_t s = 0; s < src.size(); ++s)
+                if (src[s].row0 == tm.row0 && src[s].col0 == tm.col0) tm.src = static_cast<int32_t>(s);
+        }
+        o.fuse_src = first;
+        o.fuse_ns = static_cast<int16_t>(src.size());
+        uni = uni && o.t_shift == P.ops[members[0]].t_shift;
+    }
+    for (size_t j : members) P.ops[j].fuse_uni = uni ? 1 : 0;
+    for (OpTerm s : src) {
+        s.coef = 1;
+        s.src = 0;
+        P.fsrc.push_back(s);
+    }
+    P.n_fused++;
+    return true;
+}
 
 // Longest-first greedy assignment of the tiles to the leaf's G persistent
 // CTAs, laid out so that the kernel's round-robin walk (task i on CTA i % G)
@@ -853,11 +918,11 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     P.off_products = take(P.product_bytes);
     // Prep tiles: operands of one family and shape are grouped (in order of
     // first appearance) and share an interleaved tile range (OpDesc::ilv_n).
+    // Fused groups (fuse_group) take the first tiles, [0, fused_tiles): the
+    // prep launches one kernel for them and one for the rest.
     {
-        std::vector<OpDesc> grouped;
-        grouped.reserve(P.ops.size());
+        std::vector<std::vector<size_t>> groups;
         std::vector<bool> taken(P.ops.size(), false);
-        P.prep_tiles = 0;
         for (size_t i = 0; i < P.ops.size(); ++i) {
             if (taken[i]) continue;
             const OpDesc &key = P.ops[i];
@@ -868,15 +933,33 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
                     members.push_back(j);
                     taken[j] = true;
                 }
-            const int64_t per = prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
-            for (size_t k = 0; k < members.size(); ++k) {
-                OpDesc o = P.ops[members[k]];
-                o.tile_base = P.prep_tiles;
-                o.ilv_n = static_cast<int32_t>(members.size());
-                o.ilv_i = static_cast<int32_t>(k);
-                grouped.push_back(o);
+            groups.push_back(members);
+        }
+        P.prep_tiles = 0;
+        P.fused_tiles = 0;
+        P.fsrc.clear();
+        P.n_fused = 0;
+        std::vector<bool> fused(groups.size(), false);
+        for (size_t g = 0; g < groups.size(); ++g)
+            fused[g] = B.digits && !B.fp8 && fuse_group(P, groups[g]);
+        std::vector<OpDesc> grouped;
+        grouped.reserve(P.ops.size());
+        for (int pass = 0; pass < 2; ++pass) {
+            for (size_t g = 0; g < groups.size(); ++g) {
+                if (fused[g] != (pass == 0)) continue;
+                const std::vector<size_t> &members = groups[g];
+                const OpDesc &key = P.ops[members[0]];
+                const int64_t per = prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
+                for (size_t k = 0; k < members.size(); ++k) {
+                    OpDesc o = P.ops[members[k]];
+                    o.tile_base = P.prep_tiles;
+                    o.ilv_n = static_cast<int32_t>(members.size());
+                    o.ilv_i = static_cast<int32_t>(k);
+                    grouped.push_back(o);
+                }
+                P.prep_tiles += per * (fused[g] ? 1 : static_cast<int64_t>(members.size()));
             }
-            P.prep_tiles += per * static_cast<int64_t>(members.size());
+            if (pass == 0) P.fused_tiles = P.prep_tiles;
         }
         P.ops.swap(grouped);
     }
@@ -885,7 +968,8 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     P.t_tasks = round_up(P.t_terms + static_cast<int64_t>(P.terms.size() * sizeof(OpTerm)), 256);
     P.t_combs = round_up(P.t_tasks + static_cast<int64_t>(P.tasks.size() * sizeof(LeafTask)), 256);
     P.t_cterms = round_up(P.t_combs + static_cast<int64_t>(P.combs.size() * sizeof(CombDesc)), 256);
-    P.table_bytes = round_up(P.t_cterms + static_cast<int64_t>(P.cterms.size() * sizeof(CombTerm)), 256);
+    P.t_fsrc = round_up(P.t_cterms + static_cast<int64_t>(P.cterms.size() * sizeof(CombTerm)), 256);
+    P.table_bytes = round_up(P.t_fsrc + static_cast<int64_t>(P.fsrc.size() * sizeof(OpTerm)), 256);
     P.off_tables = take(P.table_bytes);
     P.workspace_bytes = off;
     return true;
@@ -901,6 +985,7 @@ void pack_tables(const Plan &P, std::vector<uint8_t> *buf) {
     put(P.t_tasks, P.tasks.data(), P.tasks.size() * sizeof(LeafTask));
     put(P.t_combs, P.combs.data(), P.combs.size() * sizeof(CombDesc));
     put(P.t_cterms, P.cterms.data(), P.cterms.size() * sizeof(CombTerm));
+    put(P.t_fsrc, P.fsrc.data(), P.fsrc.size() * sizeof(OpTerm));
 }
 
 }  // namespace ata

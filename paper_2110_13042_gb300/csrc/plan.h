@@ -62,7 +62,8 @@ struct OpTerm {
     int32_t rows;   // valid rows (contraction extent); rows beyond are zero
     int32_t cols;   // valid columns; columns beyond are zero
     int32_t coef;   // +1 or -1
-    int32_t pad;
+    int32_t src;    // fused groups: index of the term's block in the group's
+                    // source list (OpDesc::fuse_src); 0 otherwise
 };
 
 // Operand generator: writes
@@ -91,7 +92,19 @@ struct OpDesc {
     // group (0 .. ilv_n - 1; ilv_n <= 1: not interleaved).
     int32_t ilv_n;
     int32_t ilv_i;
+    // Fused group (fuse_ns > 0): the group's operands draw on the same
+    // fuse_ns <= FUSE_MAX_SRC blocks of A (entries fuse_src .. of the plan's
+    // source list), and one prep tile writes tile `local` of every operand of
+    // the group from one read of those blocks; the group's tile range then
+    // has the tiles of one operand.  fuse_uni: every operand of the group has
+    // the same t_shift, so each block is converted to fixed point once.
+    int32_t fuse_src;
+    int16_t fuse_ns;
+    int16_t fuse_uni;
 };
+
+constexpr int FUSE_MAX_SRC = 4;   // source blocks of a fused prep group
+constexpr int FUSE_MAX_OPS = 8;   // operands of a fused prep group
 
 struct Family {
     int64_t K_pitch;     // contraction pitch in elements (multiple of PREP_K)
@@ -191,7 +204,8 @@ struct CombDesc {
     int32_t e_col0;      // A column of region column 0
     int32_t first_term, nterms;
     int64_t tile_base;   // prefix count of combine tiles (COMB_ROWS x COMB_COLS)
-    int32_t wide;        // 1: the worst-case sum reaches 2^62: summed in int128
+    int32_t wide;        // 1: the result bound reaches 2^63: summed in int128
+                         //    (else modulo 2^64, exact as the result fits)
     int32_t smin;        // smallest term shift; products are summed in units 2^smin
     int32_t diag;        // 1: the region crosses the diagonal: write only where
     int32_t diag_off;    //    col <= row + diag_off (split contraction of a diagonal tile)
@@ -262,6 +276,8 @@ struct Plan {
     std::vector<Family> families;       // [0] = plain digits of A (if used)
     std::vector<OpDesc> ops;
     std::vector<OpTerm> terms;
+    std::vector<OpTerm> fsrc;           // source blocks of the fused prep groups
+    int64_t n_fused = 0;                // fused prep groups
     std::vector<LeafTask> tasks;
     std::vector<CombDesc> combs;
     std::vector<CombTerm> cterms;
@@ -269,11 +285,12 @@ struct Plan {
     std::vector<LeafGroup> groups;      // static partition (PlanParams::streams > 1), else empty
     int32_t n_units = 0;                // recursion units the tiles belong to
     int64_t prep_tiles = 0, comb_tiles = 0;
+    int64_t fused_tiles = 0;            // prep tiles [0, fused_tiles) belong to fused groups
     // workspace layout (byte offsets)
     int64_t off_colmax = 0, off_expo = 0, off_products = 0, product_bytes = 0;
     int64_t off_tables = 0, table_bytes = 0, workspace_bytes = 0;
     // byte offsets of the task tables inside the table block
-    int64_t t_ops = 0, t_terms = 0, t_tasks = 0, t_combs = 0, t_cterms = 0;
+    int64_t t_ops = 0, t_terms = 0, t_tasks = 0, t_combs = 0, t_cterms = 0, t_fsrc = 0;
     double leaf_madds = 0, plain_madds = 0;   // per digit pair / per FP64 product
     bool uses_digits() const { return p.mode != MODE_F64; }
 };

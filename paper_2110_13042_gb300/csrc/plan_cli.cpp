@@ -85,6 +85,18 @@ int main(int argc, char **argv) {
                 if (P.ops[j].tile_base <= tile) i = j;
             const int64_t g = tile - P.ops[i].tile_base;
             const int64_t nn = P.ops[i].ilv_n;
+            if (P.ops[i].fuse_ns > 0) {  // fused group: tile g of every member
+                const size_t lead = i - static_cast<size_t>(P.ops[i].ilv_i);
+                if (tile >= P.fused_tiles) prep_ok = false;
+                for (int64_t mi = 0; mi < nn && prep_ok; ++mi) {
+                    const size_t op = lead + static_cast<size_t>(mi);
+                    if (P.ops[op].fuse_ns != P.ops[i].fuse_ns || P.ops[op].tile_base != P.ops[i].tile_base ||
+                        g >= static_cast<int64_t>(seen[op].size()) || seen[op][g]++)
+                        prep_ok = false;
+                }
+                continue;
+            }
+            if (tile < P.fused_tiles) prep_ok = false;
             const size_t op = nn > 1 ? i - P.ops[i].ilv_i + static_cast<size_t>(g % nn) : i;
             const int64_t local = nn > 1 ? g / nn : g;
             if (local < 0 || local >= static_cast<int64_t>(seen[op].size()) || seen[op][local]++) prep_ok = false;
@@ -92,6 +104,22 @@ int main(int argc, char **argv) {
         for (const auto &v : seen)
             for (uint8_t x : v)
                 if (x != 1) prep_ok = false;
+        // fused groups: every term names a source block that is the term's region
+        for (const OpDesc &o : P.ops) {
+            if (o.fuse_ns <= 0) continue;
+            if (o.fuse_ns > FUSE_MAX_SRC || o.fuse_src + o.fuse_ns > static_cast<int64_t>(P.fsrc.size()))
+                prep_ok = false;
+            for (int t = 0; t < o.nterms && prep_ok; ++t) {
+                const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+                if (tm.src < 0 || tm.src >= o.fuse_ns) {
+                    prep_ok = false;
+                    break;
+                }
+                const OpTerm &sb = P.fsrc[static_cast<size_t>(o.fuse_src + tm.src)];
+                if (sb.row0 != tm.row0 || sb.col0 != tm.col0 || sb.rows != tm.rows || sb.cols != tm.cols)
+                    prep_ok = false;
+            }
+        }
     }
     // Combine tiles: COMB_ROWS x COMB_COLS per block, prefix tile_base.
     bool comb_ok = true;
@@ -204,8 +232,9 @@ int main(int argc, char **argv) {
     }
     int64_t wide = 0;  // combine regions summed in int128
     for (const CombDesc &d : P.combs) wide += d.wide;
-    std::printf("verify_err=%g verify_bounds_ok=%d wide_regions=%lld ", verify_err, bounds_ok ? 1 : 0,
-                static_cast<long long>(wide));
+    std::printf("verify_err=%g verify_bounds_ok=%d wide_regions=%lld fused_groups=%lld fused_tiles=%lld ",
+                verify_err, bounds_ok ? 1 : 0, static_cast<long long>(wide), static_cast<long long>(P.n_fused),
+                static_cast<long long>(P.fused_tiles));
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
                 "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "

@@ -81,8 +81,12 @@ def test_forced_split_within_tolerance(ata, mode, split):
 
 
 @pytest.mark.parametrize("mode", [F64_EMU, F32])
-def test_split_integer_inputs_exact(ata, mode):
-    A = inputs.integer_valued(2600, 257, seed=7, lo=-4, hi=4)
+@pytest.mark.parametrize("m", [2600, 16384])
+def test_split_integer_inputs_exact(ata, mode, m):
+    """The chunks' exact sum can exceed int64 (m 2^(43 + h) >= 2^63 with h
+    the chunks' extra fraction bits), so these regions are summed in int128:
+    bit-exact on integer inputs."""
+    A = inputs.integer_valued(m, 257, seed=7, lo=-4, hi=4)
     C, _ = run(ata, A, mode, depth=0, split_k=4)
     low = np.tril_indices(257)
     assert np.array_equal(C[low], oracle.ata_lower(A)[low])

@@ -66,13 +66,30 @@ def test_plan_tables_compute_the_product(cli, variant, m, n, mode, cutoff, depth
     assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
 
 
-@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,expect_wide", [
-    (600, 1111, 1, 300, 8, 64, 1, True),    # Winograd down to 64 columns: 2^16-coarser products
-    (1024, 1024, 1, 0, 3, 64, 1, True),
-    (8192, 8192, 1, 0, 0, 4096, 0, False),  # plain tiles: no combine at all
-    (700, 900, 5, 0, 2, 2, 0, False)])      # FP8 sums products in FP64
-def test_wide_combine_regions(cli, m, n, mode, cutoff, depth, smin, variant, expect_wide):
-    """A combine region whose worst-case exact sum reaches 2^62 is summed in
-    int128 (no bits dropped), as deep Winograd plans need."""
-    r = cli(m, n, mode, cutoff, depth, smin, 1, variant=variant)
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,split,expect_wide", [
+    (600, 1111, 1, 300, 8, 64, 1, 0, False),   # Winograd down to 64 columns: huge terms, small result
+    (8192, 8192, 1, 0, 1, 4096, 0, 0, False),
+    (262144, 2048, 1, 0, 0, 4096, 0, 0, True),  # 4 contraction chunks of 65536 rows: result up to 2^64
+    (700, 900, 5, 0, 2, 2, 0, 0, False)])       # FP8 sums products in FP64
+def test_wide_combine_regions(cli, m, n, mode, cutoff, depth, smin, variant, split, expect_wide):
+    """The combine sums exactly: modulo 2^64 where the result (an entry of
+    A^T A, at most m in scaled units, plus the operands' rounding) fits in
+    int64 however large its terms, in int128 (wide) only where it may not."""
+    r = cli(m, n, mode, cutoff, depth, smin, 1, variant=variant, split=split)
     assert (r["wide_regions"] > 0) == expect_wide
+
+
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,expect", [
+    (8192, 8192, 1, 2048, 1, 4096, 0, 2),   # both sides of the top block's sums
+    (531, 700, 1, 350, 1, 2, 1, 1),         # Winograd: mixed term counts (one side in place)
+    (1000, 1100, 2, 0, 1, 64, 0, 1),         # the V side reads in place
+    (250, 330, 1, 0, 2, 16, 0, 0),          # depth 2: 16 source blocks, not fused
+    (700, 900, 5, 0, 1, 2, 0, 0)])          # FP8 planes are not fused
+def test_fused_prep_groups(cli, m, n, mode, cutoff, depth, smin, variant, expect):
+    """Operand sums of one side of a depth-1 block read their four quadrants
+    once (a fused prep group); the prep tile map still produces every tile of
+    every operand exactly once and every term names its own source block."""
+    r = cli(m, n, mode, cutoff, depth, smin, 1, variant=variant)
+    assert r["fused_groups"] == expect
+    assert r["prep_map_ok"] == 1
+    assert (r["fused_tiles"] > 0) == (expect > 0)
