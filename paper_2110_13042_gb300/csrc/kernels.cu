@@ -471,6 +471,61 @@ __device__ __forceinline__ void prep_tile(const T *__restrict__ A, int64_t lda, 
     __syncthreads();  // sV is reused by the block's next tile
 }
 
+// prep_tile for FP32 inputs with up to 3 digits, whose fixed-point values
+// and sums fit 32 bits: the thread keeps its 16 sums in registers, so there
+// is no shared-memory round trip and no block barrier, and each term's 16
+// loads are in flight together.  Same values as prep_tile.
+template <int S, typename T>
+__device__ __forceinline__ void prep_tile_narrow(const T *__restrict__ A, int64_t lda, bool trans,
+                                                 const int *__restrict__ expo, const OpDesc &od,
+                                                 const OpTerm *terms, int64_t tile, const Family &fam, uint8_t *ws,
+                                                 int lgtc) {
+    constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
+    static_assert(sizeof(T) == 4 && S <= 3 && F <= 29, "32-bit fixed point");
+    const int tc = 1 << lgtc, tk = 4096 >> lgtc;
+    const int64_t local = tile - od.tile_base;
+    const int tiles_k = od.K_pitch / tk;
+    const int k0 = static_cast<int>(local % tiles_k) * tk;
+    const int c0 = static_cast<int>(local / tiles_k) * tc;
+    const int cc = threadIdx.x & (tc - 1);
+    const int rg = threadIdx.x >> lgtc;
+    const int c = c0 + cc;
+    if (c >= od.P_pad) return;
+    const int kk = k0 + rg * KSTEP;
+    const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
+    int32_t v[KSTEP];
+#pragma unroll
+    for (int j = 0; j < KSTEP; ++j) v[j] = 0;
+    for (int t = 0; t < od.nterms; ++t) {
+        const OpTerm tm = terms[od.first_term + t];
+        const bool cv = c < tm.cols;
+        const T *base = A + (tm.row0 + kk) * rs + (tm.col0 + c) * cs;
+        const int lim = cv ? tm.rows - kk : 0;
+        T raw[KSTEP];
+#pragma unroll
+        for (int j = 0; j < KSTEP; ++j) raw[j] = j < lim ? base[j * rs] : T(0);
+        const int sh = cv ? F - od.t_shift - expo[tm.col0 + c] : 0;
+#pragma unroll
+        for (int j = 0; j < KSTEP; ++j) {
+            const int32_t x = fixed32_of_fast<F>(static_cast<float>(raw[j]), sh);
+            v[j] += tm.coef > 0 ? x : -x;
+        }
+    }
+    constexpr int32_t CADD = [] {
+        int32_t a = 0;
+        for (int j = 0; j < S - 1; ++j) a += int32_t(256) << (DIGIT_BITS * j);
+        return a;
+    }();
+    int32_t w[KSTEP];
+#pragma unroll
+    for (int j = 0; j < KSTEP; ++j) w[j] = v[j] + CADD;
+    const int64_t ncb = fam.cols / BLOCK_COLS;
+    const int r = cc & (BLOCK_COLS - 1);
+    const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
+    uint8_t *row0 = ws + fam.offset + ((static_cast<int64_t>(kk / KSTEP) * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
+    store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
+}
+
 // Half an image row: contraction values 8h .. 8h + 7 of one column, digit
 // Q .. S - 1 of each, one 16-byte store per digit plane (slot h ^ swz).
 template <int S, int Q = 0, typename W>
@@ -488,18 +543,20 @@ __device__ __forceinline__ void store_digits_half(const W (&w)[8], uint8_t *row0
     }
 }
 
-// One prep tile (16 contraction rows x 256 columns, one column per thread)
-// of every operand of a fused group (OpDesc::fuse_ns): the thread loads its
-// column's rows of each of the group's source blocks once, eight rows at a
-// time, and writes its half image rows of every member's digit planes.  Each
-// member's value is the one prep_tile writes: every term rounded with the
-// member's t_shift and the terms summed exactly; with fuse_uni (one t_shift
-// for the whole group) each source value is rounded once for all members.
+// One prep tile (16 contraction rows x FUSED_TC columns) of every operand of
+// a fused group (OpDesc::fuse_ns).  Lanes 2l and 2l + 1 of a warp own one
+// column and rows 0-7 and 8-15 of the tile: each loads its 8 rows of every
+// source block once and writes its 16-byte half of the column's 32-byte
+// image row of every member's digit planes, so one warp store fills 16
+// whole image rows (512 contiguous bytes).  Each member's value is the one
+// prep_tile writes: every term rounded with the member's t_shift and the
+// terms summed exactly; with fuse_uni (one t_shift for the whole group) each
+// source value is rounded once for all members.
 template <int S, typename T, bool UNI>
 __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t lda, bool trans,
                                                 const int *__restrict__ expo, const OpDesc *o, int lead,
-                                                const OpTerm *terms, const OpTerm *__restrict__ fsrc,
-                                                int64_t local, const Families &fams, uint8_t *ws) {
+                                                const OpTerm *__restrict__ fsrc, int64_t local,
+                                                const Families &fams, uint8_t *ws) {
     constexpr int F = DIGIT_TOP_BITS + DIGIT_BITS * (S - 1);
     constexpr bool NARROW = sizeof(T) == 4 && F <= 29;
     using V = typename std::conditional<NARROW, int32_t, int64_t>::type;
@@ -520,83 +577,71 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     }();
     const OpDesc &L = o[lead];
     const int ns = L.fuse_ns, nm = L.ilv_n;
-    const int tiles_k = L.K_pitch / PREP_TK;
-    const int k0 = static_cast<int>(local % tiles_k) * PREP_TK;
-    const int c0 = static_cast<int>(local / tiles_k) * PREP_TC;
-    const int cc = threadIdx.x;
+    const int tiles_k = L.K_pitch / KSTEP;
+    const int k0 = static_cast<int>(local % tiles_k) * KSTEP;
+    const int c0 = static_cast<int>(local / tiles_k) * FUSED_TC;
+    const int lane = threadIdx.x & 31;
+    const int cc = (threadIdx.x >> 5) * 16 + (lane >> 1);
+    const int h = lane & 1;  // rows 8h .. 8h + 7 of the tile
     const int c = c0 + cc;
     if (c >= L.P_pad) return;  // every member has the group's P_pad
     const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
-    const T *base[NS];
-    int lim[NS], ex[NS];
+    const int kh = k0 + 8 * h;
+    T raw[NS][8];
+    int ex[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const bool present = q < ns;
         const OpTerm sb = present ? fsrc[L.fuse_src + q] : OpTerm{};
         const bool cv = present && c < sb.cols;
-        base[q] = A + (sb.row0 + k0) * rs + (sb.col0 + c) * cs;
-        lim[q] = cv ? sb.rows - k0 : 0;
+        const T *base = A + (sb.row0 + kh) * rs + (sb.col0 + c) * cs;
+        const int lim = cv ? sb.rows - kh : 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) raw[q][j] = j < lim ? base[j * rs] : T(0);
         ex[q] = cv ? expo[sb.col0 + c] : 0;
+    }
+    // UNI: every source value rounded once, for all members
+    V x[UNI ? NS : 1][8];
+    if constexpr (UNI) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int sh = F - L.t_shift - ex[q];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[q][j] = fixed(raw[q][j], sh);
+        }
     }
     const Family &fam = fams.f[L.family];
     const int64_t ncb = fam.cols / BLOCK_COLS;
     const int64_t plane_step = ncb * BLOCK_BYTES;
-    const int r = cc & (BLOCK_COLS - 1);
-    const int swz = (r >> 2) & 1;
+    const int r = c & (BLOCK_COLS - 1);  // out_col is a multiple of BLOCK_COLS
+    const int slot = h ^ ((r >> 2) & 1);
     const int64_t kstep = k0 / KSTEP;
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        T raw[NS][8];
+    for (int mi = 0; mi < nm; ++mi) {
+        const OpDesc &od = o[lead + mi];
+        V v[8];
 #pragma unroll
-        for (int q = 0; q < NS; ++q)
+        for (int j = 0; j < 8; ++j) v[j] = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) raw[q][j] = (8 * h + j) < lim[q] ? base[q][(8 * h + j) * rs] : T(0);
-        // UNI: every source value rounded once, for all members
-        V x[UNI ? NS : 1][8];
-        if constexpr (UNI) {
+        for (int q = 0; q < NS; ++q) {
+            const int cf = static_cast<int8_t>(od.fuse_coef >> (8 * q));  // uniform over the block
+            if (cf == 0) continue;
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const int sh = F - L.t_shift - ex[q];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) x[q][j] = fixed(raw[q][j], sh);
+            for (int j = 0; j < 8; ++j) {
+                V y;
+                if constexpr (UNI)
+                    y = x[q][j];
+                else
+                    y = fixed(raw[q][j], F - od.t_shift - ex[q]);
+                v[j] += cf > 0 ? y : -y;
             }
         }
-#pragma unroll 1
-        for (int mi = 0; mi < nm; ++mi) {
-            const OpDesc &od = o[lead + mi];
-            int cf[NS];  // the member's coefficient of each source block (0: absent)
+        W w[8];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) cf[q] = 0;
-            for (int t = 0; t < od.nterms; ++t) {
-                const OpTerm tm = terms[od.first_term + t];
-#pragma unroll
-                for (int q = 0; q < NS; ++q)
-                    if (tm.src == q) cf[q] = tm.coef;
-            }
-            V v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = 0;
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                if (cf[q] == 0) continue;  // uniform over the block
-                const int sh = F - od.t_shift - ex[q];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    V y;
-                    if constexpr (UNI)
-                        y = x[q][j];
-                    else
-                        y = fixed(raw[q][j], sh);
-                    v[j] += cf[q] > 0 ? y : -y;
-                }
-            }
-            W w[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) w[j] = static_cast<W>(v[j]) + static_cast<W>(CADD);
-            const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
-            uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
-            store_digits_half<S>(w, row0, plane_step, h ^ swz);
-        }
+        for (int j = 0; j < 8; ++j) w[j] = static_cast<W>(v[j]) + static_cast<W>(CADD);
+        const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
+        uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
+        store_digits_half<S>(w, row0, plane_step, slot);
     }
 }
 
@@ -622,6 +667,10 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     for (int64_t tile = tile_begin + blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
         const OpDesc &od = o[op_of_tile(o, nops, tile, &local)];  // read where used (register budget)
+        if constexpr (!F8 && sizeof(T) == 4 && S <= 3) {
+            prep_tile_narrow<S, T>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, 8);
+            continue;
+        }
         // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
         prep_tile<S, T, F8>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV,
                             F8 ? 7 : 8);
@@ -629,22 +678,29 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
 }
 
 // Prep tiles [0, ntiles) of the fused groups (which come first in the tile
-// range).  Two blocks per SM: a thread holds 8 rows of up to four source
-// blocks (64 registers for FP64) while it writes every member's digits.
+// range).  A thread holds 8 rows of up to four source blocks (64 registers
+// for FP64) while it writes every member's digits: two blocks per SM (three
+// spill).
+constexpr int FUSED_PREP_BLOCKS = 2;
 template <int S, typename T>
-__global__ void __launch_bounds__(256, 2) prep_fused_kernel(const T *__restrict__ A, int64_t lda, bool trans,
-                                                            const int *__restrict__ expo,
-                                                            const OpDesc *__restrict__ ops, int nops,
-                                                            const OpTerm *__restrict__ terms,
-                                                            const OpTerm *__restrict__ fsrc, int64_t ntiles,
-                                                            Families fams, uint8_t *ws) {
+__global__ void __launch_bounds__(256, FUSED_PREP_BLOCKS) prep_fused_kernel(
+    const T *__restrict__ A, int64_t lda, bool trans, const int *__restrict__ expo,
+    const OpDesc *__restrict__ ops, int nops, const OpTerm *__restrict__ fsrc, int64_t ntiles, Families fams,
+    uint8_t *ws) {
+    __shared__ OpDesc s_ops[PREP_SMEM_OPS];
+    const bool cached = nops <= PREP_SMEM_OPS;
+    if (cached) {
+        for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops[i];
+        __syncthreads();
+    }
+    const OpDesc *o = cached ? s_ops : ops;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
-        const int lead = op_of_tile(ops, nops, tile, &local);
-        if (ops[lead].fuse_uni)
-            prep_fused_tile<S, T, true>(A, lda, trans, expo, ops, lead, terms, fsrc, local, fams, ws);
+        const int lead = op_of_tile(o, nops, tile, &local);
+        if (o[lead].fuse_uni)
+            prep_fused_tile<S, T, true>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
         else
-            prep_fused_tile<S, T, false>(A, lda, trans, expo, ops, lead, terms, fsrc, local, fams, ws);
+            prep_fused_tile<S, T, false>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
     }
 }
 
@@ -652,16 +708,19 @@ __global__ void __launch_bounds__(256, 2) prep_fused_kernel(const T *__restrict_
 // block walks its tiles in increasing order and keeps a cursor on the
 // problem table (prefix prep_base), so locating a tile's problem costs one
 // binary search per block.
-// Five resident blocks per SM (48 registers) for FP32 inputs with up to 3
-// digits, whose 32-bit arithmetic fits; four otherwise.
+// FP32 inputs with up to 3 digits (32-bit arithmetic, sums kept in
+// registers: prep_tile_narrow) take no shared memory and run six resident
+// blocks per SM (40 registers); others four.
 template <typename T, int S>
-constexpr int batched_prep_blocks() { return (sizeof(T) == 4 && S <= 3) ? 5 : 4; }
+__host__ __device__ constexpr bool batched_narrow() { return sizeof(T) == 4 && S <= 3; }
+template <typename T, int S>
+constexpr int batched_prep_blocks() { return batched_narrow<T, S>() ? 6 : 4; }
 
 template <int S, typename T>
 __global__ void __launch_bounds__(256, batched_prep_blocks<T, S>()) batched_prep_kernel(const BatchProb *__restrict__ probs, int64_t count,
                                                               const int *__restrict__ expo, int64_t ntiles,
                                                               uint8_t *planes) {
-    __shared__ int64_t sV[PREP_SV];
+    __shared__ int64_t sV[batched_narrow<T, S>() ? 1 : PREP_SV];
     // Each block takes a contiguous range of tiles, so its problem cursor
     // moves by at most a few problems over the whole range (a grid-stride
     // walk would skip gridDim.x tiles, i.e. several small problems, per step,
@@ -693,8 +752,12 @@ __global__ void __launch_bounds__(256, batched_prep_blocks<T, S>()) batched_prep
         fam.cols = bp.ncb * BLOCK_COLS;
         fam.offset = bp.plane_off;
         const int lgtc = bp.tc == 64 ? 6 : (bp.tc == 128 ? 7 : 8);
-        prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, false, expo + bp.col_off, od, &term, tile, fam,
-                        planes, sV, lgtc);
+        if constexpr (batched_narrow<T, S>())
+            prep_tile_narrow<S, T>(static_cast<const T *>(bp.A), bp.lda, false, expo + bp.col_off, od, &term, tile,
+                                   fam, planes, lgtc);
+        else
+            prep_tile<S, T>(static_cast<const T *>(bp.A), bp.lda, false, expo + bp.col_off, od, &term, tile, fam,
+                            planes, sV, lgtc);
     }
 }
 
@@ -1182,13 +1245,13 @@ static void prep_digits_dispatch(const Plan &P, const void *A, bool is_f32, cons
     const bool tr = P.p.trans != 0;
     const int64_t t0 = P.fused_tiles, nt = P.prep_tiles;
     if (t0 > 0) {  // fused groups (digit modes other than FP8)
-        const unsigned gf = prep_grid(t0, 2);
+        const unsigned gf = prep_grid(t0, FUSED_PREP_BLOCKS);
         if (is_f32)
             prep_fused_kernel<S, float><<<gf, 256, 0, s>>>(static_cast<const float *>(A), P.p.lda, tr, expo, ops,
-                                                            nops, terms, fsrc, t0, F, ws);
+                                                            nops, fsrc, t0, F, ws);
         else
             prep_fused_kernel<S, double><<<gf, 256, 0, s>>>(static_cast<const double *>(A), P.p.lda, tr, expo,
-                                                             ops, nops, terms, fsrc, t0, F, ws);
+                                                             ops, nops, fsrc, t0, F, ws);
     }
     if (nt <= t0) return;
     const unsigned g = prep_grid(nt - t0);

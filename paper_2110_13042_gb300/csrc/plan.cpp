@@ -549,6 +549,12 @@ static bool fuse_group(Plan &P, const std::vector<size_t> &members) {
         }
         o.fuse_src = first;
         o.fuse_ns = static_cast<int16_t>(src.size());
+        uint32_t packed = 0;
+        for (int t = 0; t < o.nterms; ++t) {
+            const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+            packed |= static_cast<uint32_t>(static_cast<uint8_t>(static_cast<int8_t>(tm.coef))) << (8 * tm.src);
+        }
+        o.fuse_coef = static_cast<int32_t>(packed);
         uni = uni && o.t_shift == P.ops[members[0]].t_shift;
     }
     for (size_t j : members) P.ops[j].fuse_uni = uni ? 1 : 0;
@@ -949,7 +955,8 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
                 if (fused[g] != (pass == 0)) continue;
                 const std::vector<size_t> &members = groups[g];
                 const OpDesc &key = P.ops[members[0]];
-                const int64_t per = prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
+                const int64_t per = fused[g] ? fused_tiles_for(key.K_pitch, key.P_pad)
+                                             : prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
                 for (size_t k = 0; k < members.size(); ++k) {
                     OpDesc o = P.ops[members[k]];
                     o.tile_base = P.prep_tiles;

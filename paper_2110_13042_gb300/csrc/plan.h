@@ -101,10 +101,18 @@ struct OpDesc {
     int32_t fuse_src;
     int16_t fuse_ns;
     int16_t fuse_uni;
+    int32_t fuse_coef;   // coefficient of source block q (-1, 0, +1) in byte q
+    int32_t pad;
 };
 
 constexpr int FUSE_MAX_SRC = 4;   // source blocks of a fused prep group
 constexpr int FUSE_MAX_OPS = 8;   // operands of a fused prep group
+constexpr int FUSED_TC = 128;     // fused prep tile: 16 contraction rows x 128 columns
+
+// Prep tiles of one operand of a fused group.
+inline int64_t fused_tiles_for(int64_t K_pitch, int64_t P_pad) {
+    return (K_pitch / KSTEP) * ((P_pad + FUSED_TC - 1) / FUSED_TC);
+}
 
 struct Family {
     int64_t K_pitch;     // contraction pitch in elements (multiple of PREP_K)

@@ -70,7 +70,10 @@ int main(int argc, char **argv) {
         const bool digits = pp.mode != MODE_F64, fp8 = pp.mode == MODE_F32_FP8;
         std::vector<std::vector<uint8_t>> seen(P.ops.size());
         for (size_t i = 0; i < P.ops.size(); ++i) {
-            seen[i].assign(static_cast<size_t>(prep_tiles_for(digits, P.ops[i].K_pitch, P.ops[i].P_pad, fp8)), 0);
+            seen[i].assign(static_cast<size_t>(P.ops[i].fuse_ns > 0
+                                                   ? fused_tiles_for(P.ops[i].K_pitch, P.ops[i].P_pad)
+                                                   : prep_tiles_for(digits, P.ops[i].K_pitch, P.ops[i].P_pad, fp8)),
+                           0);
             if (P.ops[i].ilv_i == 0) groups++;
             if (P.ops[i].ilv_n < 1 || P.ops[i].ilv_i >= P.ops[i].ilv_n) prep_ok = false;
             if (P.ops[i].ilv_i > 0 && (P.ops[i].tile_base != P.ops[i - 1].tile_base ||
