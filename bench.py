@@ -239,6 +239,13 @@ def batched_bench(ata, torch, dev, stream, args, timed):
     eff = float(sum(a * b * b for a, b in zip(ms, ns)))
     hb = ata.Handle()
     ms_b = timed(lambda: hb.batched(As, Cs, ata.ATA_F32, stream), 3, 2)
+    hb.set_timing(True)
+    phases = []
+    for _ in range(3):
+        hb.batched(As, Cs, ata.ATA_F32, stream)
+        phases.append(hb.phase_times())
+    hb.set_timing(False)
+    ph = [statistics.median(p[i] for p in phases) for i in range(3)]
     ms_p = None
     if not args.batched_only:  # the one-launch-per-matrix comparison
         hp = ata.Handle(depth=0)
@@ -259,7 +266,17 @@ def batched_bench(ata, torch, dev, stream, args, timed):
            "value": eff / (ms_b * 1e-3) / 1e12, "ms": ms_b, "problems": count,
            "workload": f"{count} FP32 problems, m logU[64,4096], n logU[32,1024], U[-1,1) on device (seed {args.seed})",
            "one_launch_per_matrix": ({"value": eff / (ms_p * 1e-3) / 1e12, "ms": ms_p} if ms_p else None),
-           "a_bytes": int(abuf.numel() * 4), "c_bytes": int(cbuf.numel() * 4)}
+           "a_bytes": int(abuf.numel() * 4), "c_bytes": int(cbuf.numel() * 4),
+           "phases_ms": {"expo": ph[0], "prep": ph[1], "leaf": ph[2]}}
+    # digit prep: 4 B read and 3 digits x 2 B written per element of A
+    prep_bytes = abuf.numel() * (4 + 6)
+    peaks, _ = measured_peaks()
+    if ph[1] > 0 and peaks.get("hbm_gbs"):
+        gbs = prep_bytes / (ph[1] * 1e-3) / 1e9
+        res["prep_roofline"] = {"bound": "hbm", "kernel": "batched_prep_kernel<3, float>", "achieved": gbs,
+                                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                                "frac": gbs / float(peaks["hbm_gbs"]),
+                                "work": "4 B read + 6 B of digits written per element of A (algorithmic)"}
     return res, (As, Cs)
 
 
@@ -547,7 +564,7 @@ def main():
                             f"C {C.numel() * C.element_size() / 2**20:.0f} MiB)"},
            "roofline": roof,
            "phases_ms": {"colexp": ph[0], "prep": ph[1], "leaf": ph[2], "combine": ph[3]},
-           "gpu_launches": args.steps * (4 + (1 if info["products"] else 0) + (1 if info["fused_groups"] else 0)),
+           "gpu_launches": args.steps * (4 + (1 if info["comb_regions"] else 0) + (1 if info["fused_groups"] else 0)),
            "clocks": clk}
 
     if not args.no_extras and not args.aat:

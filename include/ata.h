@@ -263,10 +263,12 @@ const char *ata_last_error(ata_handle h);
  *   [9] multiply-adds of plain tiled AtA on the same tile grid
  *   [10] contraction chunks per plain tile (split_k; 1 = not split)
  *   [11] fused operand-prep groups (Strassen operand sums of one side of a
- *        block written from one read of its blocks of A; each group with
- *        any adds one prep kernel launch)
+ *        block written from one read of its blocks of A; any adds one prep
+ *        kernel launch)
+ *   [12] combine regions (Strassen result sums and tiles computed as
+ *        contraction chunks; any adds one combine launch)
  * h may be NULL (default configuration). */
-#define ATA_PLAN_FIELDS 12
+#define ATA_PLAN_FIELDS 13
 int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out);
 
 /* Host-only description of the off-diagonal blocks of the plan ata_lower

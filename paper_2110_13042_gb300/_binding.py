@@ -16,7 +16,8 @@ ATA_TRANS, ATA_PACKED = 1, 2
 STATUS = {0: "ATA_OK", 1: "ATA_ERR_INVALID", 2: "ATA_ERR_DTYPE", 3: "ATA_ERR_ALLOC",
           4: "ATA_ERR_CUDA", 5: "ATA_ERR_TIMEOUT", 6: "ATA_ERR_UNSUPPORTED"}
 PLAN_FIELDS = ("cutoff", "depth", "slices", "panels", "blocks", "products", "tiles",
-               "workspace_bytes", "leaf_madds", "plain_madds", "split_k", "fused_groups")
+               "workspace_bytes", "leaf_madds", "plain_madds", "split_k", "fused_groups",
+               "comb_regions")
 
 _lib = None
 

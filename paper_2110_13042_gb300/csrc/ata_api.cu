@@ -372,6 +372,7 @@ int ata_plan_info(ata_handle h, int64_t m, int64_t n, int dtype, int64_t *out) {
     out[9] = static_cast<int64_t>(P.plain_madds);
     out[10] = P.split_k;
     out[11] = P.n_fused;
+    out[12] = static_cast<int64_t>(P.combs.size());
     return ATA_OK;
 }
 
@@ -759,14 +760,21 @@ int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, co
         if ((e = cudaEventRecord(cb.uploaded, s)) != cudaSuccess) return fail(h, ATA_ERR_CUDA, "table upload event", e);
         cb.recorded = true;
     }
+    // phase events (ata_set_timing): exponents, digit prep, leaf; no combine
+    auto mark = [&](int i) {
+        if (h->timing) cudaEventRecord(h->ev[i], s);
+    };
     if (dev && (e = launch_batched_ptrs(probs, count, A_dev, C_dev, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched pointer gather", e);
     if (cb.any_empty_m && (e = launch_batched_zero(probs, count, f32, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "zero fill", e);
+    mark(0);
     if ((e = launch_batched_expo(B, probs, f32, expo, h->d_status, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched exponents", e);
+    mark(1);
     if ((e = launch_batched_prep(B, probs, f32, expo, ws + cb.off_planes, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched digit prep", e);
+    mark(2);
     LeafParams lp;
     lp = LeafParams{};  // zeros, alpha = 1, beta = 0
     lp.tasks = reinterpret_cast<const LeafTask *>(ws + cb.off_tasks);
@@ -777,6 +785,9 @@ int batched_impl(ata_handle h, int count, const int64_t *m, const int64_t *n, co
     lp.batch_planes = ws + cb.off_planes;
     if ((e = launch_leaf_tc_raw(B.slices, lp, lp.ntasks, h->num_sms, s)) != cudaSuccess)
         return fail(h, ATA_ERR_CUDA, "batched leaf", e);
+    mark(3);
+    mark(4);
+    if (h->timing) h->timed = true;
     return ATA_OK;
 }
 

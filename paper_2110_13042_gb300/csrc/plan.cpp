@@ -109,6 +109,10 @@ struct Builder {
     int64_t prod_elems = 0;
     int split_k = 1;  // contraction chunks per plain tile (split contraction)
     double comb_bound_max = 0;  // largest worst-case combine sum, units 2^smin
+    // Tail split: plain tiles from number tail_from on (generation order) are
+    // computed as tail_parts contraction chunks (see make_plan).
+    int64_t n_plain = 0, tail_from = -1;
+    int tail_parts = 1;
 
     explicit Builder(Plan &p)
         : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)) {}
@@ -145,8 +149,10 @@ struct Builder {
     }
 
     void plain_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
-        if (split_k > 1) {
-            split_tile(r0, c0, rows, cols);
+        const bool tail = tail_from >= 0 && n_plain >= tail_from;
+        ++n_plain;
+        if (split_k > 1 || tail) {
+            split_tile(r0, c0, rows, cols, split_k > 1 ? split_k : tail_parts);
             return;
         }
         LeafTask t{};
@@ -403,13 +409,14 @@ struct Builder {
         P.combs.push_back(c);
     }
 
-    // A plain tile computed as split_k contraction chunks (rows a multiple of
+    // A plain tile computed as `parts` contraction chunks (rows a multiple of
     // 256, so every chunk drains its accumulators on the same row boundaries
     // as the whole): each chunk's exact partial product goes to the product
     // workspace, and one combine region sums them in chunk order into C.
-    void split_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
+    void split_tile(int64_t r0, int64_t c0, int64_t rows, int64_t cols, int parts) {
+        // (parts chunks of a multiple of 256 rows; the last may be shorter)
         const int64_t m = P.p.m;
-        const int64_t chunk = round_up(ceil_div(m, split_k), 256);
+        const int64_t chunk = round_up(ceil_div(m, parts), 256);
         std::vector<CombTerm> terms;
         std::vector<int64_t> klen;
         for (int64_t k0 = 0; k0 < m; k0 += chunk) {
@@ -510,6 +517,23 @@ struct Builder {
 };
 
 }  // namespace
+
+// The busiest CTA's K steps when tiles of the given step counts are laid out
+// longest-first on G persistent CTAs (as balance_task_list does), counting
+// each tile's final drains and stores as 3 steps.
+static int64_t lpt_makespan(std::vector<int64_t> steps, int G) {
+    std::sort(steps.begin(), steps.end(), std::greater<int64_t>());
+    std::priority_queue<int64_t, std::vector<int64_t>, std::greater<int64_t>> heap;
+    for (int b = 0; b < G; ++b) heap.push(0);
+    int64_t mx = 0;
+    for (int64_t v : steps) {
+        int64_t l = heap.top() + v + 3;
+        heap.pop();
+        heap.push(l);
+        mx = std::max(mx, l);
+    }
+    return mx;
+}
 
 // Fuse an interleaved group of digit operands (same family and shape) when
 // its operands are sums of at most FUSE_MAX_SRC distinct blocks of A: the
@@ -821,7 +845,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
 
     // Build the task lists, with `split` contraction chunks per plain tile.
     std::unique_ptr<Builder> Bp;
-    auto build = [&](int split) {
+    auto build = [&](int split, int64_t tail_from, int tail_parts) {
         P.families.clear();
         P.ops.clear();
         P.terms.clear();
@@ -836,6 +860,8 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         Bp.reset(new Builder(P));
         Builder &B = *Bp;
         B.split_k = split;
+        B.tail_from = tail_from;
+        B.tail_parts = tail_parts;
         if (P.variant == VARIANT_WINOGRAD) {
             B.tU = wU;
             B.tV = wV;
@@ -856,7 +882,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     int split = 1;
     const bool can_split = pp.mode != MODE_F64;
     if (can_split && pp.split_k > 1) split = std::min(pp.split_k, SPLITK_MAX);
-    build(split);
+    build(split, -1, 1);
     const int ctas = pp.num_ctas > 1 ? pp.num_ctas : 152;
     if (can_split && pp.split_k == 0 && static_cast<int64_t>(P.tasks.size()) < SPLITK_TILES_PER_CTA * ctas &&
         pp.m >= 2 * SPLITK_MIN_ROWS) {
@@ -864,7 +890,42 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         while (s < SPLITK_MAX && static_cast<int64_t>(P.tasks.size()) * s < SPLITK_TILES_PER_CTA * ctas &&
                pp.m / (2 * s) >= SPLITK_MIN_ROWS)
             s *= 2;
-        build(static_cast<int>(s));
+        build(static_cast<int>(s), -1, 1);
+    }
+    // Tail split: when the plain tiles (all of contraction m) leave the last
+    // wave of the persistent CTAs partly idle, the last q of them (q = plain
+    // tiles mod CTAs) are computed as contraction chunks, which the
+    // longest-first layout spreads over the idle CTAs; chosen by simulating
+    // the layout, and kept only if it shortens the busiest CTA by >= 1%.
+    if (can_split && pp.split_k == 0 && Bp->split_k == 1 && pp.streams <= 1 && Bp->n_plain > 0) {
+        const int64_t q = Bp->n_plain % ctas;
+        const int64_t m_steps = ceil_div(pp.m, KSTEP);
+        std::vector<int64_t> steps;
+        for (const LeafTask &t : P.tasks) steps.push_back(ceil_div(t.klen, KSTEP));
+        const int64_t base = lpt_makespan(steps, ctas);
+        int best_parts = 1;
+        int64_t best = base;
+        for (int parts : {2, 3, 4, 6, 8}) {
+            const int64_t chunk = round_up(ceil_div(pp.m, parts), 256);
+            if (q == 0 || chunk < 1024 || chunk >= pp.m) continue;
+            std::vector<int64_t> st;
+            int64_t removed = 0;
+            for (int64_t v : steps) {
+                if (v == m_steps && removed < q) {
+                    ++removed;
+                    for (int64_t k0 = 0; k0 < pp.m; k0 += chunk)
+                        st.push_back(ceil_div(std::min(chunk, pp.m - k0), KSTEP));
+                } else {
+                    st.push_back(v);
+                }
+            }
+            const int64_t ms = lpt_makespan(st, ctas);
+            if (ms < best) {
+                best = ms;
+                best_parts = parts;
+            }
+        }
+        if (best_parts > 1 && best * 100 <= base * 99) build(1, Bp->n_plain - q, best_parts);
     }
     Builder &B = *Bp;
     P.split_k = B.split_k;

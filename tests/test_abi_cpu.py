@@ -101,9 +101,11 @@ def plan_cli(lib):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", os.path.dirname(src), src, plan_cpp, "-o", out],
                    check=True)
 
-    def run(m, n, mode, cutoff, depth, slices=0, strassen_min=1, split_search=1, num_ctas=0, variant=0):
+    def run(m, n, mode, cutoff, depth, slices=0, strassen_min=1, split_search=1, num_ctas=0, variant=0,
+            split_k=0):
         r = subprocess.run([out, str(m), str(n), str(mode), str(cutoff), str(depth), str(slices),
-                            str(strassen_min), str(split_search), str(num_ctas), str(variant)],
+                            str(strassen_min), str(split_search), str(num_ctas), str(variant), "1",
+                            str(split_k)],
                            capture_output=True, text=True, check=True)
         return {k: int(v) for k, v in (kv.split("=") for kv in r.stdout.split())}
     return run
@@ -115,7 +117,7 @@ def test_recursion_structure(plan_cli, n, cutoff, depth):
     # With the cost-model split placement off, every split is the aligned
     # middle: panels are the leaves of that column recursion, the split point
     # the largest multiple of 32 not above w/2 (a panel if that is 0).
-    P = plan_cli(4096, n, 1, cutoff, depth, split_search=0)
+    P = plan_cli(4096, n, 1, cutoff, depth, split_search=0, split_k=1)  # whole tiles only
     def split(w):
         return (w // 64) * 32
 
@@ -172,7 +174,7 @@ def test_task_balance_for_persistent_ctas(plan_cli, m, n, depth, smin):
 @pytest.mark.parametrize("depth", [1, 2, 3])
 def test_strassen_products_and_savings(plan_cli, depth):
     n, cutoff = 8192, 2048
-    P = plan_cli(8192, n, 1, cutoff, depth)
+    P = plan_cli(8192, n, 1, cutoff, depth, split_k=1)  # whole plain tiles: no chunk products
     assert P["products"] == 7 ** depth * P["blocks"]
     # Each Strassen level replaces 8 block products by 7 on the off-diagonal
     # blocks (Section 3.2): leaf work / classical work on those blocks = (7/8)^d.
@@ -183,10 +185,10 @@ def test_strassen_products_and_savings(plan_cli, depth):
 def test_combine_terms_match_strassen_counts(plan_cli):
     # depth 1: C11 and C22 have 4 terms, C12 and C21 have 2: 12 result terms
     # per block (the 8 result additions of Section 3.2 plus one term per quadrant).
-    P = plan_cli(8192, 4096, 1, 2048, 1, split_search=0)
+    P = plan_cli(8192, 4096, 1, 2048, 1, split_search=0, split_k=1)
     assert P["blocks"] == 1
     assert P["cterms"] == 12
-    P2 = plan_cli(8192, 4096, 1, 2048, 2, split_search=0)
+    P2 = plan_cli(8192, 4096, 1, 2048, 2, split_search=0, split_k=1)
     assert P2["cterms"] == 144
 
 

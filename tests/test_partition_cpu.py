@@ -31,8 +31,8 @@ def cli(tmp_path_factory):
     (8192, 8192, 1, 0, 1, 4096), (3000, 5000, 2, 0, 2, 512), (700, 1300, 5, 200, 2, 2),
     (500, 900, 0, 128, 1, 2), (1000, 300, 1, 0, 0, 4096)])
 def test_partition_covers_and_keeps_units_whole(cli, streams, m, n, mode, cutoff, depth, smin):
-    one = cli(m, n, mode, cutoff, depth, smin, 1)
-    part = cli(m, n, mode, cutoff, depth, smin, streams)
+    one = cli(m, n, mode, cutoff, depth, smin, 1, split=1)  # no tail split: the same tiles
+    part = cli(m, n, mode, cutoff, depth, smin, streams, split=1)
     assert part["covered"] == n * (n + 1) // 2 and part["overlap"] == 0
     assert part["groups_ok"] == 1
     assert 1 <= part["leaf_groups"] <= min(streams, part["units"])
@@ -93,3 +93,21 @@ def test_fused_prep_groups(cli, m, n, mode, cutoff, depth, smin, variant, expect
     assert r["fused_groups"] == expect
     assert r["prep_map_ok"] == 1
     assert (r["fused_tiles"] > 0) == (expect > 0)
+
+
+@pytest.mark.parametrize("m,n,mode,cutoff", [(8192, 8192, 1, 8192), (4096, 4096, 2, 4096), (8192, 8192, 5, 8192)])
+def test_tail_split_balances_the_last_wave(cli, m, n, mode, cutoff):
+    """Plain tiles that leave the last wave of the 152 persistent CTAs partly
+    idle: the last (tiles mod 152) are computed as contraction chunks, and the
+    busiest CTA carries within 1% of the average load (without the split,
+    up to one whole tile more)."""
+    r = cli(m, n, mode, cutoff, 0, 4096, 1)
+    avg = r["cta_steps_sum"] / 152
+    assert r["cta_steps_max"] <= 1.01 * avg + 8
+    assert r["comb_map_ok"] == 1 and r["covered"] == n * (n + 1) // 2 and r["overlap"] == 0
+
+
+def test_tail_split_plan_computes_the_product(cli):
+    r = cli(2048, 600, 1, 0, 0, 4096, 1, verify=1)
+    assert r["wide_regions"] > 0  # the split tiles' chunks
+    assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
