@@ -116,8 +116,13 @@ typedef struct {
     int split_k;         /* contraction chunks per plain leaf tile (not for
                             ATA_F64): 0 = automatic (a plan with fewer than 4
                             tiles per SM and m >= 8192 splits the contraction
-                            into chunks of >= 4096 rows), 1 = never, 2..16 =
-                            that many.  The chunks' exact partial products
+                            into chunks of >= 4096 rows; otherwise, when the
+                            whole-contraction tiles leave the last wave of
+                            the persistent CTAs partly idle, the last
+                            (tiles mod SMs) of them are split into chunks of
+                            >= 1024 rows if that shortens the busiest CTA by
+                            >= 1%), 1 = never, 2..16 = that many for every
+                            plain tile.  The chunks' exact partial products
                             are summed in a fixed order by the combine pass:
                             results stay deterministic (run to run
                             bit-identical) and within the mode's tolerance    */
@@ -196,7 +201,8 @@ int ata_lower_aat(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda
  * HOST arrays of `count` DEVICE pointers.  Only ATA_F32, ATA_F32_BF16 and
  * ATA_F64_EMU are accepted (ATA_F64, ATA_F32_FP8: ATA_ERR_UNSUPPORTED); every problem is
  * done as plain lower-triangle tiles of its own digit planes (no Strassen),
- * with the same arithmetic and bits as a depth-0 ata_lower call.  Three
+ * with the same arithmetic and bits as an ata_lower call with
+ * strassen_depth = 0 and split_k = 1 (whole tiles).  Three
  * launches serve the whole batch: column exponents, digit planes, and one
  * persistent leaf launch over all problems' tiles (longest first).  Problems
  * with n == 0 are skipped and m == 0 zero-fills low(C_i).  The plan and its
@@ -322,7 +328,8 @@ int ata_tune_clear(ata_handle h);
  * The paper has no counterpart: this is a deployment convenience.
  *
  * Computes low(C) <- low(A^T A) exactly like ata_lower with
- * strassen_depth = 0 (plain tiled, same kernels and digit count) for dtype
+ * strassen_depth = 0 and split_k = 1 (plain whole tiles, same kernels and
+ * digit count) for dtype
  * ATA_F64_EMU, ATA_F32 or ATA_F32_BF16 (others: ATA_ERR_DTYPE).  Arguments
  * are as for ata_lower; there is no handle.  It calls no cudaMalloc, cudaFree
  * or other allocating routine: its scratch is one fixed 32 MiB device array

@@ -19,7 +19,9 @@
 // unit); h = min(9, 19 - log2 K) extra bits keep short contractions as
 // accurate as long ones.  The tile's value is T * 2^(-43 - h + shift + e_row + e_col).
 //
-// Tile 128 x 96: five 96-column FP32 accumulators fit the 512 TMEM columns.
+// Tile 128 x 96: five 96-column FP32 accumulators fit the 512 TMEM columns
+// (one digit: the single accumulator has two buffers, filled and drained in
+// turn by alternate 16-step chunks).
 // K step 16 (one MMA per digit pair per stage, 32-byte swizzle) keeps stages
 // small, so 4-10 of them are in flight.
 //
@@ -79,12 +81,16 @@ struct Cfg {
     static constexpr int STAGES_FIT = 229000 / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT < MAX_STAGES ? STAGES_FIT : MAX_STAGES;
     static constexpr int NACC = S >= MAX_ACC ? MAX_ACC : S;
-    static constexpr int TMEM_COLS = NACC == 1 ? 128 : NACC == 2 ? 256 : 512;
+    // One digit: two TMEM buffers for the one accumulator, used by
+    // alternate drain chunks, so the tensor core fills one while the
+    // epilogue drains the other (with one buffer every drain idled it).
+    static constexpr int NBUF = S == 1 ? 2 : NACC;
+    static constexpr int TMEM_COLS = NBUF == 1 ? 128 : NBUF == 2 ? 256 : 512;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + BAR_BYTES;
     static_assert(STAGES >= 2, "pipeline depth");
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
-    static_assert(NACC * TILE_N <= TMEM_COLS, "TMEM budget");
+    static_assert(NBUF * TILE_N <= TMEM_COLS, "TMEM budget");
 };
 
 __host__ __device__ constexpr int acc_of(int p, int q) {
@@ -316,37 +322,40 @@ __device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int 
 // conversion work.
 // ZERO: also clear what was read, so the next MMA into ACC accumulates onto
 // zero (the grouped issue path of S <= 4).
+// buf: the one-digit accumulator's TMEM buffer (0 for every other case).
 template <int ACC, bool WIDE, bool ZERO>
 __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh,
-                                          int h, float fold_scale) {
+                                          int h, float fold_scale, int buf = 0) {
     static_assert(EPI_COLS == 32, "two 16-column loads");
+    const uint32_t col = static_cast<uint32_t>((ACC + buf) * TILE_N + colbase);
     uint32_t r0[16], r1[16];
-    tmem_ld_32x32b_x16(tbase + ACC * TILE_N + colbase, r0);
-    tmem_ld_32x32b_x16(tbase + ACC * TILE_N + colbase + 16, r1);
+    tmem_ld_32x32b_x16(tbase + col, r0);
+    tmem_ld_32x32b_x16(tbase + col + 16, r1);
     tmem_ld_wait();
     if constexpr (ZERO) {
-        tmem_st_zero_32x32b_x16(tbase + ACC * TILE_N + colbase);
-        tmem_st_zero_32x32b_x16(tbase + ACC * TILE_N + colbase + 16);
+        tmem_st_zero_32x32b_x16(tbase + col);
+        tmem_st_zero_32x32b_x16(tbase + col + 16);
         tmem_st_wait();
     }
     tc_fence_before();
-    mbar_arrive(&sh->acce[ACC]);
+    mbar_arrive(&sh->acce[ACC + buf]);
     absorb<ACC, WIDE>(T, r0, h, fold_scale);
     absorb<ACC, WIDE>(T + 16, r1, h, fold_scale);
 }
 
 // FP8 mode: drain the single accumulator (FP32 partial sums of E4M3
 // products over the chunk) into the thread's FP32 sums, zeroing it.
-__device__ __forceinline__ void drain_f8(float (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh) {
+__device__ __forceinline__ void drain_f8(float (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh, int buf) {
+    const uint32_t col = static_cast<uint32_t>(buf * TILE_N + colbase);
     uint32_t r0[16], r1[16];
-    tmem_ld_32x32b_x16(tbase + colbase, r0);
-    tmem_ld_32x32b_x16(tbase + colbase + 16, r1);
+    tmem_ld_32x32b_x16(tbase + col, r0);
+    tmem_ld_32x32b_x16(tbase + col + 16, r1);
     tmem_ld_wait();
-    tmem_st_zero_32x32b_x16(tbase + colbase);
-    tmem_st_zero_32x32b_x16(tbase + colbase + 16);
+    tmem_st_zero_32x32b_x16(tbase + col);
+    tmem_st_zero_32x32b_x16(tbase + col + 16);
     tmem_st_wait();
     tc_fence_before();
-    mbar_arrive(&sh->acce[0]);
+    mbar_arrive(&sh->acce[buf]);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         T[i] += __uint_as_float(r0[i]);
@@ -504,9 +513,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 uint32_t phase = 0;
                 // every accumulator starts out with the epilogue, which zeroes it
                 // (grouped issue path, see issue_group)
-                IssueState st{0u, (1u << C::NACC) - 1u, 0u};
+                IssueState st{0u, (1u << C::NBUF) - 1u, 0u};
                 bool ok = true;
                 bool ready = false;  // the current stage's full barrier was already seen complete
+                int dbuf = 0;        // one digit: the accumulator buffer of the current drain chunk
                 const uint32_t smem_base = smem_u32(smem);
                 for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
                     const int nsteps = (p.tasks[ti].klen + KS - 1) / KS;
@@ -537,18 +547,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                             const uint32_t a_base = smem_base + stage * C::STAGE_BYTES;
                             const uint64_t da0 = sdesc_kmajor_sw32(a_base);
                             const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
+                            // one digit: only the current buffer must be drained
+                            const uint32_t need_a = S == 1 ? (1u << dbuf) : ~0x0Cu;
+                            const uint32_t tacc = S == 1 ? tmem + static_cast<uint32_t>(dbuf * TILE_N) : tmem;
 #pragma unroll
                             for (int kk = 0; kk < C::KPS; ++kk) {
                                 if (kk < cnt) {
                                     const uint64_t off = static_cast<uint64_t>(kk * (C::STEP_BYTES >> 4));
-                                    if (kk == 0 && (st.pending & ~0x0Cu)) {
-                                        ok = wait_drained<C::NACC>(st, ~0x0Cu, sh, abort_flag, p.status);
+                                    if (kk == 0 && (st.pending & need_a)) {
+                                        ok = wait_drained<C::NBUF>(st, need_a, sh, abort_flag, p.status);
                                         if (!ok) break;
                                     }
                                     if constexpr (F8)
-                                        umma_f8(tmem, da0 + off, db0 + off, IDESC8, 1u);
+                                        umma_f8(tacc, da0 + off, db0 + off, IDESC8, 1u);
                                     else
-                                        issue_group<S, false>(tmem, da0 + off, db0 + off);
+                                        issue_group<S, false>(tacc, da0 + off, db0 + off);
                                     if (kk == 0 && (st.pending & 0x0Cu)) {
                                         ok = wait_drained<C::NACC>(st, 0x0Cu, sh, abort_flag, p.status);
                                         if (!ok) break;
@@ -563,8 +576,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                     ? due_mask((end - 1) / CHUNK_STEPS, end >= nsteps, C::NACC)
                                     : 0u;
                             if (due) {  // hand the accumulators to the epilogue
-                                umma_commit(&sh->accf[0]);
-                                st.pending |= due;
+                                if constexpr (S == 1) {  // each buffer has its own barrier
+                                    umma_commit(&sh->accf[dbuf]);
+                                    st.pending |= 1u << dbuf;
+                                    dbuf ^= 1;
+                                } else {
+                                    umma_commit(&sh->accf[0]);
+                                    st.pending |= due;
+                                }
                             }
                         } else {
                             for (int kk = 0; kk < cnt; ++kk) {
@@ -611,17 +630,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
         const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16);
         const int colbase = EPI_COLS * third;
         uint32_t accf_phase = 0;  // bit g: parity of the next wait on accf[g]
+        int ebuf = 0;             // one digit: the buffer of the next drain
         bool ok = true;
         constexpr bool ZERO = S <= 4;  // the grouped issue path (see issue_group)
         if constexpr (ZERO) {
             // zero every accumulator once and hand it to the issuer
-            for (int a = 0; a < C::NACC; ++a) {
+            for (int a = 0; a < C::NBUF; ++a) {
                 tmem_st_zero_32x32b_x16(tbase + a * TILE_N + colbase);
                 tmem_st_zero_32x32b_x16(tbase + a * TILE_N + colbase + 16);
             }
             tmem_st_wait();
             tc_fence_before();
-            for (int a = 0; a < C::NACC; ++a) mbar_arrive(&sh->acce[a]);
+            for (int a = 0; a < C::NBUF; ++a) mbar_arrive(&sh->acce[a]);
         }
         for (int ti = blockIdx.x; ti < p.ntasks && ok; ti += gridDim.x) {
             // Only the chunk count stays live across the K loop; the rest of
@@ -666,21 +686,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     }
                     continue;
                 }
-                if (!__all_sync(0xffffffffu, mbar_wait(&sh->accf[0], accf_phase, abort_flag, p.status))) {
+                const int bar = S == 1 ? ebuf : 0;
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(&sh->accf[bar], (accf_phase >> bar) & 1u, abort_flag, p.status))) {
                     ok = false;
                     break;
                 }
-                accf_phase ^= 1u;
+                accf_phase ^= 1u << bar;
                 tc_fence_after();
                 if constexpr (F8) {
-                    drain_f8(T, tbase, colbase, sh);
+                    drain_f8(T, tbase, colbase, sh, ebuf);
                 } else {
                     if (due & 16u) drain_one<4, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                    if (due & 1u) drain_one<0, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 1u) drain_one<0, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale, S == 1 ? ebuf : 0);
                     if (due & 2u) drain_one<1, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
                     if (due & 4u) drain_one<2, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
                     if (due & 8u) drain_one<3, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
                 }
+                if constexpr (S == 1) ebuf ^= 1;
             }
             if (!ok) break;
             const LeafTask t = p.tasks[ti];

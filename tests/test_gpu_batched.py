@@ -27,7 +27,7 @@ def ata():
 
 @pytest.fixture(scope="module")
 def h(ata):
-    hd = ata.Handle(depth=0)
+    hd = ata.Handle(depth=0, split_k=1)
     yield hd
     hd.close()
 
@@ -98,7 +98,7 @@ def test_batched_matches_oracle_and_single_calls(ata, h, mode):
             continue
         check_against_oracle(A, C, mode)
     # one ata_lower per problem (depth 0): identical bits
-    single = ata.Handle(depth=0)
+    single = ata.Handle(depth=0, split_k=1)
     try:
         for A, Ab, Cb in zip(As, Ad, Cd):
             if A.shape[0] == 0 or A.shape[1] == 0:
@@ -175,7 +175,7 @@ def test_batched_dev_graph_replay_on_new_buffers(ata, mode):
     ns = [a.shape[1] for a in As1]
     ldas = [max(n, 1) for n in ns]
     ta, tc = ptr_table(A1), ptr_table(C1)
-    hd = ata.Handle(depth=0)
+    hd = ata.Handle(depth=0, split_k=1)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     assert hd.batched_dev_ptr(ms, ns, ta.data_ptr(), ldas, tc.data_ptr(), ldas, mode, s) == 0  # plan + workspace
@@ -242,7 +242,7 @@ def test_batched_full_workload_sampled(ata):
         Cs.append(cbuf[oc:oc + b * b].view(b, b))
         oa += a * b
         oc += b * b
-    hb = ata.Handle(depth=0)
+    hb = ata.Handle(depth=0, split_k=1)
     hb.batched(As, Cs, F32)
     assert hb.sync() == 0
     hb.close()
