@@ -121,7 +121,7 @@ typedef struct {
                             the persistent CTAs partly idle, the last
                             (tiles mod SMs) of them are split into chunks of
                             >= 1024 rows if that shortens the busiest CTA by
-                            >= 1%), 1 = never, 2..16 = that many for every
+                            >= 0.5%), 1 = never, 2..16 = that many for every
                             plain tile.  The chunks' exact partial products
                             are summed in a fixed order by the combine pass:
                             results stay deterministic (run to run

@@ -896,7 +896,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     // wave of the persistent CTAs partly idle, the last q of them (q = plain
     // tiles mod CTAs) are computed as contraction chunks, which the
     // longest-first layout spreads over the idle CTAs; chosen by simulating
-    // the layout, and kept only if it shortens the busiest CTA by >= 1%.
+    // the layout, and kept only if it shortens the busiest CTA by >= 0.5%.
     if (can_split && pp.split_k == 0 && Bp->split_k == 1 && pp.streams <= 1 && Bp->n_plain > 0) {
         const int64_t q = Bp->n_plain % ctas;
         const int64_t m_steps = ceil_div(pp.m, KSTEP);
@@ -925,7 +925,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
                 best_parts = parts;
             }
         }
-        if (best_parts > 1 && best * 100 <= base * 99) build(1, Bp->n_plain - q, best_parts);
+        if (best_parts > 1 && best * 200 <= base * 199) build(1, Bp->n_plain - q, best_parts);
     }
     Builder &B = *Bp;
     P.split_k = B.split_k;

@@ -68,7 +68,7 @@ def test_plan_tables_compute_the_product(cli, variant, m, n, mode, cutoff, depth
 
 @pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,split,expect_wide", [
     (600, 1111, 1, 300, 8, 64, 1, 0, False),   # Winograd down to 64 columns: huge terms, small result
-    (8192, 8192, 1, 0, 1, 4096, 0, 0, False),
+    (8192, 8192, 1, 0, 1, 4096, 0, 1, False),  # the Strassen result sums (no chunked tiles)
     (262144, 2048, 1, 0, 0, 4096, 0, 0, True),  # 4 contraction chunks of 65536 rows: result up to 2^64
     (700, 900, 5, 0, 2, 2, 0, 0, False)])       # FP8 sums products in FP64
 def test_wide_combine_regions(cli, m, n, mode, cutoff, depth, smin, variant, split, expect_wide):
