@@ -162,9 +162,12 @@ __device__ __forceinline__ int op_of_tile(const OpDesc *ops, int nops, int64_t t
     int i = find_desc(ops, nops, tile);
     const int64_t g = tile - ops[i].tile_base;
     const int n = ops[i].ilv_n;
-    if (ops[i].fuse_ns > 0) {  // fused group: tile g of every member, led by member 0
-        *local = g;
-        return i - ops[i].ilv_i;
+    if (ops[i].fuse_ns > 0) {  // fused range: sub-group g mod nsub, tile g / nsub of every member
+        const int nsub = ops[i].fuse_nsub;
+        const int sub = static_cast<int>(g % nsub);
+        while (ops[i].fuse_isub > sub) i -= ops[i].ilv_i + 1;  // back to the sub-group's last member
+        *local = g / nsub;
+        return i - ops[i].ilv_i;  // its first member
     }
     if (n > 1) {  // tile counts fit 32 bits (checked at launch): 32-bit division
         const uint32_t g32 = static_cast<uint32_t>(g);
@@ -526,33 +529,38 @@ __device__ __forceinline__ void prep_tile_narrow(const T *__restrict__ A, int64_
     store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
 }
 
-// Half an image row: contraction values 8h .. 8h + 7 of one column, digit
-// Q .. S - 1 of each, one 16-byte store per digit plane (slot h ^ swz).
-template <int S, int Q = 0, typename W>
-__device__ __forceinline__ void store_digits_half(const W (&w)[8], uint8_t *row0, int64_t plane_step, int slot) {
+// R contraction values (rows R p .. R p + R - 1 of a K step) of one column,
+// digits Q .. S - 1, one (2 R)-byte store per digit plane at byte `off` of
+// the column's 32-byte image row.
+template <int S, int R, int Q = 0, typename W>
+__device__ __forceinline__ void store_digits_part(const W (&w)[R], uint8_t *row0, int64_t plane_step, int off) {
     if constexpr (Q < S) {
-        uint32_t pk[4];
+        uint32_t pk[R / 2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < R / 2; ++i) {
             const __nv_bfloat162 v =
                 __floats2bfloat162_rn(digit_value<S, Q>(w[2 * i]), digit_value<S, Q>(w[2 * i + 1]));
             pk[i] = *reinterpret_cast<const uint32_t *>(&v);
         }
-        *reinterpret_cast<uint4 *>(row0 + Q * plane_step + (slot << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        store_digits_half<S, Q + 1, W>(w, row0, plane_step, slot);
+        uint8_t *dst = row0 + Q * plane_step + off;
+        if constexpr (R == 8)
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        else
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(pk[0], pk[1]);
+        store_digits_part<S, R, Q + 1, W>(w, row0, plane_step, off);
     }
 }
 
-// One prep tile (16 contraction rows x FUSED_TC columns) of every operand of
-// a fused group (OpDesc::fuse_ns).  Lanes 2l and 2l + 1 of a warp own one
-// column and rows 0-7 and 8-15 of the tile: each loads its 8 rows of every
-// source block once and writes its 16-byte half of the column's 32-byte
-// image row of every member's digit planes, so one warp store fills 16
-// whole image rows (512 contiguous bytes).  Each member's value is the one
-// prep_tile writes: every term rounded with the member's t_shift and the
-// terms summed exactly; with fuse_uni (one t_shift for the whole group) each
-// source value is rounded once for all members.
-template <int S, typename T, bool UNI>
+// One prep tile (16 contraction rows x 16 R columns) of every operand of a
+// fused group (OpDesc::fuse_ns <= NS sources).  The 16 / R lanes of a warp
+// that share a column own R rows each: each loads its rows of every source
+// block once and writes its part of the column's 32-byte image row of every
+// member's digit planes, so one warp store fills whole image rows (512
+// contiguous bytes for R = 8).  Each member's value is the one prep_tile
+// writes: every term rounded with the member's t_shift and the terms summed
+// exactly; with fuse_uni (one t_shift for the whole group) each source value
+// is rounded once for all members.
+template <int S, typename T, bool UNI, int R>
 __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t lda, bool trans,
                                                 const int *__restrict__ expo, const OpDesc *o, int lead,
                                                 const OpTerm *__restrict__ fsrc, int64_t local,
@@ -561,7 +569,8 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     constexpr bool NARROW = sizeof(T) == 4 && F <= 29;
     using V = typename std::conditional<NARROW, int32_t, int64_t>::type;
     using W = typename std::conditional<(S <= 3), int32_t, int64_t>::type;
-    constexpr int NS = FUSE_MAX_SRC;
+    constexpr int NS = R == 8 ? 4 : 8;  // source blocks a thread can hold
+    constexpr int LPC = KSTEP / R;      // lanes per column
     auto fixed = [](T a, int sh) -> V {
         if constexpr (NARROW)
             return fixed32_of_fast<F>(static_cast<float>(a), sh);
@@ -579,15 +588,15 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     const int ns = L.fuse_ns, nm = L.ilv_n;
     const int tiles_k = L.K_pitch / KSTEP;
     const int k0 = static_cast<int>(local % tiles_k) * KSTEP;
-    const int c0 = static_cast<int>(local / tiles_k) * FUSED_TC;
+    const int c0 = static_cast<int>(local / tiles_k) * (16 * R);
     const int lane = threadIdx.x & 31;
-    const int cc = (threadIdx.x >> 5) * 16 + (lane >> 1);
-    const int h = lane & 1;  // rows 8h .. 8h + 7 of the tile
+    const int cc = (threadIdx.x >> 5) * (32 / LPC) + lane / LPC;
+    const int part = lane % LPC;  // rows R part .. R part + R - 1 of the tile
     const int c = c0 + cc;
     if (c >= L.P_pad) return;  // every member has the group's P_pad
     const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
-    const int kh = k0 + 8 * h;
-    T raw[NS][8];
+    const int kh = k0 + R * part;
+    T raw[NS][R];
     int ex[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
@@ -597,37 +606,40 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
         const T *base = A + (sb.row0 + kh) * rs + (sb.col0 + c) * cs;
         const int lim = cv ? sb.rows - kh : 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) raw[q][j] = j < lim ? base[j * rs] : T(0);
+        for (int j = 0; j < R; ++j) raw[q][j] = j < lim ? base[j * rs] : T(0);
         ex[q] = cv ? expo[sb.col0 + c] : 0;
     }
     // UNI: every source value rounded once, for all members
-    V x[UNI ? NS : 1][8];
+    V x[UNI ? NS : 1][R];
     if constexpr (UNI) {
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int sh = F - L.t_shift - ex[q];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) x[q][j] = fixed(raw[q][j], sh);
+            for (int j = 0; j < R; ++j) x[q][j] = fixed(raw[q][j], sh);
         }
     }
     const Family &fam = fams.f[L.family];
     const int64_t ncb = fam.cols / BLOCK_COLS;
     const int64_t plane_step = ncb * BLOCK_BYTES;
     const int r = c & (BLOCK_COLS - 1);  // out_col is a multiple of BLOCK_COLS
-    const int slot = h ^ ((r >> 2) & 1);
+    // rows 8h .. 8h + 7 are 16-byte slot h ^ swz of the image row
+    const int h = (R * part) >> 3;
+    const int off = ((h ^ ((r >> 2) & 1)) << 4) + ((R * part) & 7) * 2;
     const int64_t kstep = k0 / KSTEP;
 #pragma unroll 1
     for (int mi = 0; mi < nm; ++mi) {
         const OpDesc &od = o[lead + mi];
-        V v[8];
+        V v[R];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = 0;
+        for (int j = 0; j < R; ++j) v[j] = 0;
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            const int cf = static_cast<int8_t>(od.fuse_coef >> (8 * q));  // uniform over the block
+            // 2-bit coefficient of source q (uniform over the block)
+            const int cf = static_cast<int>(static_cast<uint32_t>(od.fuse_coef) << (30 - 2 * q)) >> 30;
             if (cf == 0) continue;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < R; ++j) {
                 V y;
                 if constexpr (UNI)
                     y = x[q][j];
@@ -636,12 +648,12 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
                 v[j] += cf > 0 ? y : -y;
             }
         }
-        W w[8];
+        W w[R];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) w[j] = static_cast<W>(v[j]) + static_cast<W>(CADD);
+        for (int j = 0; j < R; ++j) w[j] = static_cast<W>(v[j]) + static_cast<W>(CADD);
         const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
         uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
-        store_digits_half<S>(w, row0, plane_step, slot);
+        store_digits_part<S, R>(w, row0, plane_step, off);
     }
 }
 
@@ -687,8 +699,9 @@ __global__ void __launch_bounds__(256, FUSED_PREP_BLOCKS) prep_fused_kernel(
     const T *__restrict__ A, int64_t lda, bool trans, const int *__restrict__ expo,
     const OpDesc *__restrict__ ops, int nops, const OpTerm *__restrict__ fsrc, int64_t ntiles, Families fams,
     uint8_t *ws) {
-    __shared__ OpDesc s_ops[PREP_SMEM_OPS];
-    const bool cached = nops <= PREP_SMEM_OPS;
+    constexpr int SMEM_OPS = 192;  // Strassen depth 2: about 2 x 49 operands per block
+    __shared__ OpDesc s_ops[SMEM_OPS];
+    const bool cached = nops <= SMEM_OPS;
     if (cached) {
         for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops[i];
         __syncthreads();
@@ -697,10 +710,18 @@ __global__ void __launch_bounds__(256, FUSED_PREP_BLOCKS) prep_fused_kernel(
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
         const int lead = op_of_tile(o, nops, tile, &local);
-        if (o[lead].fuse_uni)
-            prep_fused_tile<S, T, true>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
-        else
-            prep_fused_tile<S, T, false>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
+        const bool uni = o[lead].fuse_uni != 0;
+        if (o[lead].fuse_rows == 8) {
+            if (uni)
+                prep_fused_tile<S, T, true, 8>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
+            else
+                prep_fused_tile<S, T, false, 8>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
+        } else {
+            if (uni)
+                prep_fused_tile<S, T, true, 4>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
+            else
+                prep_fused_tile<S, T, false, 4>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
+        }
     }
 }
 

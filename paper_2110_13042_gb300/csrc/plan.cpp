@@ -535,59 +535,91 @@ static int64_t lpt_makespan(std::vector<int64_t> steps, int G) {
     return mx;
 }
 
-// Fuse an interleaved group of digit operands (same family and shape) when
-// its operands are sums of at most FUSE_MAX_SRC distinct blocks of A: the
-// blocks go to the plan's source list, every term records its block's index,
-// and the members are marked so that one prep tile serves them all (the
-// Strassen operand sums of one side of a block at depth 1 read the four
-// quadrants once instead of once per sum).  Returns false (nothing changed)
-// when the group does not qualify.
-static bool fuse_group(Plan &P, const std::vector<size_t> &members) {
-    if (members.size() < 2 || members.size() > static_cast<size_t>(FUSE_MAX_OPS)) return false;
-    std::vector<OpTerm> src;
-    for (size_t j : members) {
-        const OpDesc &o = P.ops[j];
-        for (int t = 0; t < o.nterms; ++t) {
-            const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
-            bool found = false;
-            for (const OpTerm &s : src) {
-                if (s.row0 == tm.row0 && s.col0 == tm.col0) {
-                    if (s.rows != tm.rows || s.cols != tm.cols) return false;
-                    found = true;
-                }
-            }
-            if (!found) {
-                if (src.size() == static_cast<size_t>(FUSE_MAX_SRC)) return false;
-                src.push_back(tm);
+// Distinct source blocks of operand j, appended to `src` (by row0, col0).
+// Returns false if a block appears with two different extents.
+static bool add_sources(const Plan &P, size_t j, std::vector<OpTerm> *src) {
+    const OpDesc &o = P.ops[j];
+    for (int t = 0; t < o.nterms; ++t) {
+        const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+        bool found = false;
+        for (const OpTerm &sb : *src) {
+            if (sb.row0 == tm.row0 && sb.col0 == tm.col0) {
+                if (sb.rows != tm.rows || sb.cols != tm.cols) return false;
+                found = true;
             }
         }
+        if (!found) src->push_back(tm);
     }
-    const int32_t first = static_cast<int32_t>(P.fsrc.size());
-    bool uni = true;
+    return true;
+}
+
+// Fuse a group of digit operands of one family and shape: split it (first
+// fit, in order) into sub-groups that draw on at most FUSE_MAX_SRC distinct blocks of
+// A with at most FUSE_MAX_OPS operands each (the Strassen operand sums of one
+// side of a block: at depth 1 one sub-group of four quadrants; at depth 2
+// one per outer-level pattern, up to eight blocks), put each sub-group's
+// blocks in the plan's source list, give every term its block's index, and
+// mark the operands.  *subs receives the sub-groups (member lists).  Returns
+// false (nothing changed) when no sub-group would have two operands.
+static bool fuse_group(Plan &P, const std::vector<size_t> &members, std::vector<std::vector<size_t>> *subs) {
+    std::vector<std::vector<size_t>> groups;
+    std::vector<std::vector<OpTerm>> srcs;
     for (size_t j : members) {
-        OpDesc &o = P.ops[j];
-        for (int t = 0; t < o.nterms; ++t) {
-            OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
-            for (size_t s = 0; s < src.size(); ++s)
-                if (src[s].row0 == tm.row0 && src[s].col0 == tm.col0) tm.src = static_cast<int32_t>(s);
+        std::vector<OpTerm> own;
+        if (!add_sources(P, j, &own) || own.size() > static_cast<size_t>(FUSE_MAX_SRC)) return false;
+        bool placed = false;  // first fit
+        for (size_t gi = 0; gi < groups.size() && !placed; ++gi) {
+            if (groups[gi].size() >= static_cast<size_t>(FUSE_MAX_OPS)) continue;
+            std::vector<OpTerm> u = srcs[gi];
+            if (add_sources(P, j, &u) && u.size() <= static_cast<size_t>(FUSE_MAX_SRC)) {
+                groups[gi].push_back(j);
+                srcs[gi] = u;
+                placed = true;
+            }
         }
-        o.fuse_src = first;
-        o.fuse_ns = static_cast<int16_t>(src.size());
-        uint32_t packed = 0;
-        for (int t = 0; t < o.nterms; ++t) {
-            const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
-            packed |= static_cast<uint32_t>(static_cast<uint8_t>(static_cast<int8_t>(tm.coef))) << (8 * tm.src);
+        if (!placed) {
+            groups.push_back({j});
+            srcs.push_back(own);
         }
-        o.fuse_coef = static_cast<int32_t>(packed);
-        uni = uni && o.t_shift == P.ops[members[0]].t_shift;
     }
-    for (size_t j : members) P.ops[j].fuse_uni = uni ? 1 : 0;
-    for (OpTerm s : src) {
-        s.coef = 1;
-        s.src = 0;
-        P.fsrc.push_back(s);
+    bool any_pair = false;
+    for (const auto &g : groups) any_pair = any_pair || g.size() > 1;
+    // (the prep kernel locates a tile's sub-group by walking the range's
+    // sub-groups: a few dozen at most, as at Strassen depth <= 2)
+    if (!any_pair || groups.size() > static_cast<size_t>(FUSE_MAX_SUBGROUPS)) return false;
+    size_t ns_max = 0;
+    for (const auto &sv : srcs) ns_max = std::max(ns_max, sv.size());
+    const int8_t rows = ns_max <= 4 ? 8 : 4;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const std::vector<OpTerm> &src = srcs[gi];
+        const int32_t first = static_cast<int32_t>(P.fsrc.size());
+        bool uni = true;
+        for (size_t j : groups[gi]) {
+            OpDesc &o = P.ops[j];
+            uint32_t packed = 0;
+            for (int t = 0; t < o.nterms; ++t) {
+                OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
+                for (size_t q = 0; q < src.size(); ++q)
+                    if (src[q].row0 == tm.row0 && src[q].col0 == tm.col0) tm.src = static_cast<int32_t>(q);
+                packed |= (static_cast<uint32_t>(tm.coef) & 3u) << (2 * tm.src);
+            }
+            o.fuse_src = first;
+            o.fuse_ns = static_cast<int16_t>(src.size());
+            o.fuse_rows = rows;
+            o.fuse_coef = static_cast<int32_t>(packed);
+            o.fuse_isub = static_cast<int16_t>(gi);
+            o.fuse_nsub = static_cast<int16_t>(groups.size());
+            uni = uni && o.t_shift == P.ops[groups[gi][0]].t_shift;
+        }
+        for (size_t j : groups[gi]) P.ops[j].fuse_uni = uni ? 1 : 0;
+        for (OpTerm sb : src) {
+            sb.coef = 1;
+            sb.src = 0;
+            P.fsrc.push_back(sb);
+        }
+        P.n_fused++;
     }
-    P.n_fused++;
+    *subs = groups;
     return true;
 }
 
@@ -1007,17 +1039,30 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         P.fsrc.clear();
         P.n_fused = 0;
         std::vector<bool> fused(groups.size(), false);
+        std::vector<std::vector<std::vector<size_t>>> subs(groups.size());
         for (size_t g = 0; g < groups.size(); ++g)
-            fused[g] = B.digits && !B.fp8 && fuse_group(P, groups[g]);
+            fused[g] = B.digits && !B.fp8 && fuse_group(P, groups[g], &subs[g]);
         std::vector<OpDesc> grouped;
         grouped.reserve(P.ops.size());
         for (int pass = 0; pass < 2; ++pass) {
             for (size_t g = 0; g < groups.size(); ++g) {
                 if (fused[g] != (pass == 0)) continue;
+                const OpDesc &key = P.ops[groups[g][0]];
+                if (fused[g]) {  // sub-groups back to back, sharing one interleaved tile range
+                    for (const std::vector<size_t> &members : subs[g])
+                        for (size_t k = 0; k < members.size(); ++k) {
+                            OpDesc o = P.ops[members[k]];
+                            o.tile_base = P.prep_tiles;
+                            o.ilv_n = static_cast<int32_t>(members.size());
+                            o.ilv_i = static_cast<int32_t>(k);
+                            grouped.push_back(o);
+                        }
+                    P.prep_tiles += fused_tiles_for(key.K_pitch, key.P_pad, key.fuse_rows) *
+                                    static_cast<int64_t>(subs[g].size());
+                    continue;
+                }
                 const std::vector<size_t> &members = groups[g];
-                const OpDesc &key = P.ops[members[0]];
-                const int64_t per = fused[g] ? fused_tiles_for(key.K_pitch, key.P_pad)
-                                             : prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
+                const int64_t per = prep_tiles_for(B.digits, key.K_pitch, key.P_pad, B.fp8);
                 for (size_t k = 0; k < members.size(); ++k) {
                     OpDesc o = P.ops[members[k]];
                     o.tile_base = P.prep_tiles;
@@ -1025,7 +1070,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
                     o.ilv_i = static_cast<int32_t>(k);
                     grouped.push_back(o);
                 }
-                P.prep_tiles += per * (fused[g] ? 1 : static_cast<int64_t>(members.size()));
+                P.prep_tiles += per * static_cast<int64_t>(members.size());
             }
             if (pass == 0) P.fused_tiles = P.prep_tiles;
         }

@@ -92,26 +92,35 @@ struct OpDesc {
     // group (0 .. ilv_n - 1; ilv_n <= 1: not interleaved).
     int32_t ilv_n;
     int32_t ilv_i;
-    // Fused group (fuse_ns > 0): the group's operands draw on the same
-    // fuse_ns <= FUSE_MAX_SRC blocks of A (entries fuse_src .. of the plan's
-    // source list), and one prep tile writes tile `local` of every operand of
-    // the group from one read of those blocks; the group's tile range then
-    // has the tiles of one operand.  fuse_uni: every operand of the group has
-    // the same t_shift, so each block is converted to fixed point once.
+    // Fused group (fuse_ns > 0): the group's operands (ilv_n of them, this
+    // one ilv_i-th) draw on the same fuse_ns <= FUSE_MAX_SRC blocks of A
+    // (entries fuse_src .. of the plan's source list), and one prep tile
+    // writes tile `local` of every operand of the group from one read of
+    // those blocks.  fuse_nsub groups of one family and shape share a tile
+    // range, interleaved (tile i of the range: group i mod fuse_nsub, local
+    // tile i / fuse_nsub; this one is group fuse_isub), so groups that read
+    // the same blocks read them at about the same time.  fuse_uni: every
+    // operand of the group has the same t_shift, so each block is converted
+    // to fixed point once.  fuse_rows: contraction rows per thread (8 for up
+    // to 4 sources, 4 for up to 8).
     int32_t fuse_src;
     int16_t fuse_ns;
-    int16_t fuse_uni;
-    int32_t fuse_coef;   // coefficient of source block q (-1, 0, +1) in byte q
-    int32_t pad;
+    int8_t fuse_uni;
+    int8_t fuse_rows;
+    int32_t fuse_coef;   // coefficient of source q (-1, 0, +1) in bits 2q, 2q + 1
+    int16_t fuse_isub, fuse_nsub;
 };
 
-constexpr int FUSE_MAX_SRC = 4;   // source blocks of a fused prep group
+constexpr int FUSE_MAX_SRC = 8;   // source blocks of a fused prep group
 constexpr int FUSE_MAX_OPS = 8;   // operands of a fused prep group
-constexpr int FUSED_TC = 128;     // fused prep tile: 16 contraction rows x 128 columns
+constexpr int FUSE_MAX_SUBGROUPS = 32;  // fused groups sharing one tile range
 
-// Prep tiles of one operand of a fused group.
-inline int64_t fused_tiles_for(int64_t K_pitch, int64_t P_pad) {
-    return (K_pitch / KSTEP) * ((P_pad + FUSED_TC - 1) / FUSED_TC);
+// Fused prep tiles are 16 contraction rows x (16 x rows) columns: 16 / rows
+// lanes share a column (128 columns for 8 rows per lane, 64 for 4).
+inline int fused_tile_cols(int rows) { return 16 * rows; }
+inline int64_t fused_tiles_for(int64_t K_pitch, int64_t P_pad, int rows) {
+    const int tc = fused_tile_cols(rows);
+    return (K_pitch / KSTEP) * ((P_pad + tc - 1) / tc);
 }
 
 struct Family {

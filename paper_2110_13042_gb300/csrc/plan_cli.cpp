@@ -71,7 +71,8 @@ int main(int argc, char **argv) {
         std::vector<std::vector<uint8_t>> seen(P.ops.size());
         for (size_t i = 0; i < P.ops.size(); ++i) {
             seen[i].assign(static_cast<size_t>(P.ops[i].fuse_ns > 0
-                                                   ? fused_tiles_for(P.ops[i].K_pitch, P.ops[i].P_pad)
+                                                   ? fused_tiles_for(P.ops[i].K_pitch, P.ops[i].P_pad,
+                                                                     P.ops[i].fuse_rows)
                                                    : prep_tiles_for(digits, P.ops[i].K_pitch, P.ops[i].P_pad, fp8)),
                            0);
             if (P.ops[i].ilv_i == 0) groups++;
@@ -88,13 +89,16 @@ int main(int argc, char **argv) {
                 if (P.ops[j].tile_base <= tile) i = j;
             const int64_t g = tile - P.ops[i].tile_base;
             const int64_t nn = P.ops[i].ilv_n;
-            if (P.ops[i].fuse_ns > 0) {  // fused group: tile g of every member
-                const size_t lead = i - static_cast<size_t>(P.ops[i].ilv_i);
-                if (tile >= P.fused_tiles) prep_ok = false;
-                for (int64_t mi = 0; mi < nn && prep_ok; ++mi) {
+            if (P.ops[i].fuse_ns > 0) {  // fused range: sub-group g mod nsub, tile g / nsub of every member
+                const int64_t nsub = P.ops[i].fuse_nsub, sub = g % nsub, lt = g / nsub;
+                size_t last = i;  // last operand of sub-group `sub`
+                while (P.ops[last].fuse_isub > sub) last -= static_cast<size_t>(P.ops[last].ilv_i) + 1;
+                if (P.ops[last].fuse_isub != sub || tile >= P.fused_tiles) prep_ok = false;
+                const size_t lead = last - static_cast<size_t>(P.ops[last].ilv_i);
+                for (int64_t mi = 0; mi < P.ops[last].ilv_n && prep_ok; ++mi) {
                     const size_t op = lead + static_cast<size_t>(mi);
-                    if (P.ops[op].fuse_ns != P.ops[i].fuse_ns || P.ops[op].tile_base != P.ops[i].tile_base ||
-                        g >= static_cast<int64_t>(seen[op].size()) || seen[op][g]++)
+                    if (P.ops[op].fuse_ns != P.ops[last].fuse_ns || P.ops[op].tile_base != P.ops[i].tile_base ||
+                        P.ops[op].fuse_isub != sub || lt >= static_cast<int64_t>(seen[op].size()) || seen[op][lt]++)
                         prep_ok = false;
                 }
                 continue;
