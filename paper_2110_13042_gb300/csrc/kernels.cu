@@ -983,35 +983,23 @@ __device__ __forceinline__ void combine_region(const CombDesc &d, int r0, int co
     Acc sum[COMB_RPT];
 #pragma unroll
     for (int i = 0; i < COMB_RPT; ++i) sum[i] = 0;
-    // the next term's loads are issued before the current term is added
-    auto load = [&](const CombTerm &ct, int64_t (&v)[COMB_RPT]) {
+    // (issuing the next term's loads before adding the current one doubled
+    // the registers, halved the resident blocks and measured 0.23 against
+    // 0.14 ms at 8192^2 depth 1)
+    for (int t = 0; t < d.nterms; ++t) {
+        const CombTerm ct = cterms[d.first_term + t];
         const int64_t *src = M + ct.src_off + col;
+        int64_t v[COMB_RPT];
 #pragma unroll
         for (int i = 0; i < COMB_RPT; ++i) {
             const int row = r0 + 8 * i;
             v[i] = row < d.rows ? src[static_cast<int64_t>(row) * ct.ld] : 0;
-        }
-    };
-    CombTerm ct = cterms[d.first_term];  // every region has a term
-    int64_t v[COMB_RPT];
-    load(ct, v);
-    for (int t = 0; t < d.nterms; ++t) {
-        CombTerm cn{};
-        int64_t nx[COMB_RPT];
-        if (t + 1 < d.nterms) {
-            cn = cterms[d.first_term + t + 1];
-            load(cn, nx);
         }
         const int dsh = ct.shift - d.smin;  // >= 0
 #pragma unroll
         for (int i = 0; i < COMB_RPT; ++i) {
             const Acc x = shl<Acc>(v[i], dsh);
             sum[i] += ct.coef > 0 ? x : -x;
-        }
-        if (t + 1 < d.nterms) {
-            ct = cn;
-#pragma unroll
-            for (int i = 0; i < COMB_RPT; ++i) v[i] = nx[i];
         }
     }
     const int xc = -(T_FRAC + 2 * DIGIT_TOP_BITS) + d.smin + expo[d.e_col0 + col];

@@ -113,6 +113,11 @@ struct Builder {
     // computed as tail_parts contraction chunks (see make_plan).
     int64_t n_plain = 0, tail_from = -1;
     int tail_parts = 1;
+    // Per operand (index in P.ops): the group its prep may be fused with
+    // (one side of one Strassen block; at depth >= 2 also one outer-level
+    // product pattern), -1 for none.  See fuse_group.
+    std::vector<int64_t> op_key;
+    int64_t n_strassen_blocks = 0;
 
     explicit Builder(Plan &p)
         : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)) {}
@@ -129,7 +134,8 @@ struct Builder {
     }
 
     // Add an operand descriptor; returns its first column in the family.
-    int64_t add_op(int fam, const std::vector<OpTerm> &terms, int64_t P_nominal) {
+    int64_t add_op(int fam, const std::vector<OpTerm> &terms, int64_t P_nominal, int64_t key = -1) {
+        op_key.push_back(key);
         OpDesc o{};
         o.family = fam;
         int nonempty = 0;
@@ -237,7 +243,7 @@ struct Builder {
     // digit images, and whose zero padding (if any) lies beyond the end of A,
     // is read straight from the planes of A (family 0) at its row and column
     // offsets; any other operand gets its own planes in family `fam`.
-    Operand operand(int fam, const std::vector<OpTerm> &tt, int64_t nominal_cols, int64_t rn) {
+    Operand operand(int fam, const std::vector<OpTerm> &tt, int64_t nominal_cols, int64_t rn, int64_t key) {
         if (digits && reuse_quadrants && tt.size() == 1 && tt[0].coef == 1) {
             const OpTerm &t = tt[0];
             const Family &f0 = P.families[0];
@@ -255,7 +261,7 @@ struct Builder {
             }
         }
         const size_t o = P.ops.size();
-        const int64_t col = add_op(fam, tt, nominal_cols);
+        const int64_t col = add_op(fam, tt, nominal_cols, key);
         return {fam, col, 0, P.ops[o].t_shift};
     }
 
@@ -269,6 +275,7 @@ struct Builder {
         int64_t nprod = 1;
         for (int l = 0; l < d; ++l) nprod *= 7;
         int fam = family_for(rn);
+        ++n_strassen_blocks;
 
         std::vector<int64_t> prod_off(nprod);
         std::vector<int> prod_shift(nprod);
@@ -298,7 +305,9 @@ struct Builder {
                                       static_cast<int32_t>(qreg[ib].ext), cv, 0});
                 }
             }
-            Operand U = operand(fam, ut, pn, rn), V = operand(fam, vt, qn, rn);
+            // fuse keys: this block, the side, the outermost product digit
+            const int64_t kb = n_strassen_blocks * 64 + (d >= 2 ? digit[0] : 0) * 2;
+            Operand U = operand(fam, ut, pn, rn, kb), V = operand(fam, vt, qn, rn, kb + 1);
             // Product unit: 2^(-43 - h + t_u + t_v); the combine sees it as
             // 2^(-43 + shift) with shift = t_u + t_v - h.  (FP8: the leaf
             // writes the product in units of the scaled columns, shift =
@@ -553,34 +562,35 @@ static bool add_sources(const Plan &P, size_t j, std::vector<OpTerm> *src) {
     return true;
 }
 
-// Fuse a group of digit operands of one family and shape: split it (first
-// fit, in order) into sub-groups that draw on at most FUSE_MAX_SRC distinct blocks of
-// A with at most FUSE_MAX_OPS operands each (the Strassen operand sums of one
-// side of a block: at depth 1 one sub-group of four quadrants; at depth 2
-// one per outer-level pattern, up to eight blocks), put each sub-group's
-// blocks in the plan's source list, give every term its block's index, and
-// mark the operands.  *subs receives the sub-groups (member lists).  Returns
-// false (nothing changed) when no sub-group would have two operands.
-static bool fuse_group(Plan &P, const std::vector<size_t> &members, std::vector<std::vector<size_t>> *subs) {
+// Fuse a group of digit operands of one family and shape: split it into
+// sub-groups by the planner's fuse key (the operand sums of one side of one
+// Strassen block; at depth >= 2, of one outer-level product pattern), each
+// drawing on at most FUSE_MAX_SRC distinct blocks of A with at most
+// FUSE_MAX_OPS operands (at depth 1 the four quadrants of a side; at depth 2
+// up to eight blocks), put each sub-group's blocks in the plan's source
+// list, give every term its block's index, and mark the operands.  *subs
+// receives the sub-groups (member lists).  Returns false (nothing changed)
+// when some operand has no key or some sub-group is too large, or no
+// sub-group would have two operands.
+static bool fuse_group(Plan &P, const std::vector<size_t> &members, const std::vector<int64_t> &key,
+                       std::vector<std::vector<size_t>> *subs) {
     std::vector<std::vector<size_t>> groups;
     std::vector<std::vector<OpTerm>> srcs;
+    std::vector<int64_t> gkey;
     for (size_t j : members) {
-        std::vector<OpTerm> own;
-        if (!add_sources(P, j, &own) || own.size() > static_cast<size_t>(FUSE_MAX_SRC)) return false;
-        bool placed = false;  // first fit
-        for (size_t gi = 0; gi < groups.size() && !placed; ++gi) {
-            if (groups[gi].size() >= static_cast<size_t>(FUSE_MAX_OPS)) continue;
-            std::vector<OpTerm> u = srcs[gi];
-            if (add_sources(P, j, &u) && u.size() <= static_cast<size_t>(FUSE_MAX_SRC)) {
-                groups[gi].push_back(j);
-                srcs[gi] = u;
-                placed = true;
-            }
+        if (key[j] < 0) return false;
+        size_t gi = 0;
+        while (gi < gkey.size() && gkey[gi] != key[j]) ++gi;
+        if (gi == gkey.size()) {
+            if (groups.size() == static_cast<size_t>(FUSE_MAX_SUBGROUPS)) return false;  // too many
+            groups.emplace_back();
+            srcs.emplace_back();
+            gkey.push_back(key[j]);
         }
-        if (!placed) {
-            groups.push_back({j});
-            srcs.push_back(own);
-        }
+        if (!add_sources(P, j, &srcs[gi]) || srcs[gi].size() > static_cast<size_t>(FUSE_MAX_SRC) ||
+            groups[gi].size() == static_cast<size_t>(FUSE_MAX_OPS))
+            return false;
+        groups[gi].push_back(j);
     }
     bool any_pair = false;
     for (const auto &g : groups) any_pair = any_pair || g.size() > 1;
@@ -1041,7 +1051,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         std::vector<bool> fused(groups.size(), false);
         std::vector<std::vector<std::vector<size_t>>> subs(groups.size());
         for (size_t g = 0; g < groups.size(); ++g)
-            fused[g] = B.digits && !B.fp8 && fuse_group(P, groups[g], &subs[g]);
+            fused[g] = B.digits && !B.fp8 && fuse_group(P, groups[g], B.op_key, &subs[g]);
         std::vector<OpDesc> grouped;
         grouped.reserve(P.ops.size());
         for (int pass = 0; pass < 2; ++pass) {

@@ -81,10 +81,10 @@ def test_wide_combine_regions(cli, m, n, mode, cutoff, depth, smin, variant, spl
 
 @pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,expect", [
     (8192, 8192, 1, 2048, 1, 4096, 0, 2),   # both sides of the top block's sums, four quadrants each
-    (8192, 8192, 1, 2048, 2, 2048, 0, 14),  # depth 2: one group per outer-level pattern and side
+    (8192, 8192, 1, 2048, 2, 2048, 0, 16),  # depth 2: one group per outer-level pattern and side
     (531, 700, 1, 350, 1, 2, 1, 4),         # Winograd: mixed term counts, two blocks
     (1000, 1100, 2, 0, 1, 64, 0, 8),
-    (250, 330, 1, 0, 2, 16, 0, 20),
+    (250, 330, 1, 0, 2, 16, 0, 14),
     (700, 900, 5, 0, 1, 2, 0, 0)])          # FP8 planes are not fused
 def test_fused_prep_groups(cli, m, n, mode, cutoff, depth, smin, variant, expect):
     """Operand sums that draw on the same few blocks of A are written from one
