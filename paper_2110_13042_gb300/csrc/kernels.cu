@@ -529,38 +529,34 @@ __device__ __forceinline__ void prep_tile_narrow(const T *__restrict__ A, int64_
     store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
 }
 
-// R contraction values (rows R p .. R p + R - 1 of a K step) of one column,
-// digits Q .. S - 1, one (2 R)-byte store per digit plane at byte `off` of
-// the column's 32-byte image row.
-template <int S, int R, int Q = 0, typename W>
-__device__ __forceinline__ void store_digits_part(const W (&w)[R], uint8_t *row0, int64_t plane_step, int off) {
+// Half an image row: contraction values 8h .. 8h + 7 of one column, digits
+// Q .. S - 1, one 16-byte store per digit plane at byte `off` (slot h ^ swz)
+// of the column's 32-byte image row.
+template <int S, int Q = 0, typename W>
+__device__ __forceinline__ void store_digits_half(const W (&w)[8], uint8_t *row0, int64_t plane_step, int off) {
     if constexpr (Q < S) {
-        uint32_t pk[R / 2];
+        uint32_t pk[4];
 #pragma unroll
-        for (int i = 0; i < R / 2; ++i) {
+        for (int i = 0; i < 4; ++i) {
             const __nv_bfloat162 v =
                 __floats2bfloat162_rn(digit_value<S, Q>(w[2 * i]), digit_value<S, Q>(w[2 * i + 1]));
             pk[i] = *reinterpret_cast<const uint32_t *>(&v);
         }
-        uint8_t *dst = row0 + Q * plane_step + off;
-        if constexpr (R == 8)
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        else
-            *reinterpret_cast<uint2 *>(dst) = make_uint2(pk[0], pk[1]);
-        store_digits_part<S, R, Q + 1, W>(w, row0, plane_step, off);
+        *reinterpret_cast<uint4 *>(row0 + Q * plane_step + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        store_digits_half<S, Q + 1, W>(w, row0, plane_step, off);
     }
 }
 
-// One prep tile (16 contraction rows x 16 R columns) of every operand of a
-// fused group (OpDesc::fuse_ns <= NS sources).  The 16 / R lanes of a warp
-// that share a column own R rows each: each loads its rows of every source
-// block once and writes its part of the column's 32-byte image row of every
-// member's digit planes, so one warp store fills whole image rows (512
-// contiguous bytes for R = 8).  Each member's value is the one prep_tile
+// One prep tile (16 contraction rows x FUSED_TC columns) of every operand of
+// a fused group (OpDesc::fuse_ns <= FUSE_MAX_SRC sources).  Lanes 2l and
+// 2l + 1 of a warp own one column and rows 0-7 / 8-15 of the tile: each loads
+// its rows of every source block once and writes its half of the column's
+// 32-byte image row of every member's digit planes, so one warp store fills
+// 16 whole image rows (512 contiguous bytes).  Each member's value is the one prep_tile
 // writes: every term rounded with the member's t_shift and the terms summed
 // exactly; with fuse_uni (one t_shift for the whole group) each source value
 // is rounded once for all members.
-template <int S, typename T, bool UNI, int R>
+template <int S, typename T, bool UNI>
 __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t lda, bool trans,
                                                 const int *__restrict__ expo, const OpDesc *o, int lead,
                                                 const OpTerm *__restrict__ fsrc, int64_t local,
@@ -569,8 +565,9 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     constexpr bool NARROW = sizeof(T) == 4 && F <= 29;
     using V = typename std::conditional<NARROW, int32_t, int64_t>::type;
     using W = typename std::conditional<(S <= 3), int32_t, int64_t>::type;
-    constexpr int NS = R == 8 ? 4 : 8;  // source blocks a thread can hold
-    constexpr int LPC = KSTEP / R;      // lanes per column
+    constexpr int NS = FUSE_MAX_SRC;
+    constexpr int R = 8;            // contraction rows per lane
+    constexpr int LPC = KSTEP / R;  // lanes per column
     auto fixed = [](T a, int sh) -> V {
         if constexpr (NARROW)
             return fixed32_of_fast<F>(static_cast<float>(a), sh);
@@ -588,7 +585,7 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     const int ns = L.fuse_ns, nm = L.ilv_n;
     const int tiles_k = L.K_pitch / KSTEP;
     const int k0 = static_cast<int>(local % tiles_k) * KSTEP;
-    const int c0 = static_cast<int>(local / tiles_k) * (16 * R);
+    const int c0 = static_cast<int>(local / tiles_k) * FUSED_TC;
     const int lane = threadIdx.x & 31;
     const int cc = (threadIdx.x >> 5) * (32 / LPC) + lane / LPC;
     const int part = lane % LPC;  // rows R part .. R part + R - 1 of the tile
@@ -624,8 +621,7 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     const int64_t plane_step = ncb * BLOCK_BYTES;
     const int r = c & (BLOCK_COLS - 1);  // out_col is a multiple of BLOCK_COLS
     // rows 8h .. 8h + 7 are 16-byte slot h ^ swz of the image row
-    const int h = (R * part) >> 3;
-    const int off = ((h ^ ((r >> 2) & 1)) << 4) + ((R * part) & 7) * 2;
+    const int off = (part ^ ((r >> 2) & 1)) << 4;
     const int64_t kstep = k0 / KSTEP;
 #pragma unroll 1
     for (int mi = 0; mi < nm; ++mi) {
@@ -653,7 +649,7 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
         for (int j = 0; j < R; ++j) w[j] = static_cast<W>(v[j]) + static_cast<W>(CADD);
         const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
         uint8_t *row0 = ws + fam.offset + ((kstep * S) * ncb + cblk) * BLOCK_BYTES + r * 32;
-        store_digits_part<S, R>(w, row0, plane_step, off);
+        store_digits_half<S>(w, row0, plane_step, off);
     }
 }
 
@@ -710,18 +706,10 @@ __global__ void __launch_bounds__(256, FUSED_PREP_BLOCKS) prep_fused_kernel(
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
         const int lead = op_of_tile(o, nops, tile, &local);
-        const bool uni = o[lead].fuse_uni != 0;
-        if (o[lead].fuse_rows == 8) {
-            if (uni)
-                prep_fused_tile<S, T, true, 8>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
-            else
-                prep_fused_tile<S, T, false, 8>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
-        } else {
-            if (uni)
-                prep_fused_tile<S, T, true, 4>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
-            else
-                prep_fused_tile<S, T, false, 4>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
-        }
+        if (o[lead].fuse_uni)
+            prep_fused_tile<S, T, true>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
+        else
+            prep_fused_tile<S, T, false>(A, lda, trans, expo, o, lead, fsrc, local, fams, ws);
     }
 }
 

@@ -565,10 +565,10 @@ static bool add_sources(const Plan &P, size_t j, std::vector<OpTerm> *src) {
 // Fuse a group of digit operands of one family and shape: split it into
 // sub-groups by the planner's fuse key (the operand sums of one side of one
 // Strassen block; at depth >= 2, of one outer-level product pattern), each
-// drawing on at most FUSE_MAX_SRC distinct blocks of A with at most
-// FUSE_MAX_OPS operands (at depth 1 the four quadrants of a side; at depth 2
-// up to eight blocks), put each sub-group's blocks in the plan's source
-// list, give every term its block's index, and mark the operands.  *subs
+// drawing on at most FUSE_MAX_SRC distinct blocks of A (the four quadrants
+// of a side at depth 1) with at most FUSE_MAX_OPS operands, put each
+// sub-group's blocks in the plan's source list, give every term its block's
+// index, and mark the operands.  *subs
 // receives the sub-groups (member lists).  Returns false (nothing changed)
 // when some operand has no key or some sub-group is too large, or no
 // sub-group would have two operands.
@@ -597,9 +597,6 @@ static bool fuse_group(Plan &P, const std::vector<size_t> &members, const std::v
     // (the prep kernel locates a tile's sub-group by walking the range's
     // sub-groups: a few dozen at most, as at Strassen depth <= 2)
     if (!any_pair || groups.size() > static_cast<size_t>(FUSE_MAX_SUBGROUPS)) return false;
-    size_t ns_max = 0;
-    for (const auto &sv : srcs) ns_max = std::max(ns_max, sv.size());
-    const int8_t rows = ns_max <= 4 ? 8 : 4;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const std::vector<OpTerm> &src = srcs[gi];
         const int32_t first = static_cast<int32_t>(P.fsrc.size());
@@ -615,7 +612,6 @@ static bool fuse_group(Plan &P, const std::vector<size_t> &members, const std::v
             }
             o.fuse_src = first;
             o.fuse_ns = static_cast<int16_t>(src.size());
-            o.fuse_rows = rows;
             o.fuse_coef = static_cast<int32_t>(packed);
             o.fuse_isub = static_cast<int16_t>(gi);
             o.fuse_nsub = static_cast<int16_t>(groups.size());
@@ -1067,7 +1063,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
                             o.ilv_i = static_cast<int32_t>(k);
                             grouped.push_back(o);
                         }
-                    P.prep_tiles += fused_tiles_for(key.K_pitch, key.P_pad, key.fuse_rows) *
+                    P.prep_tiles += fused_tiles_for(key.K_pitch, key.P_pad) *
                                     static_cast<int64_t>(subs[g].size());
                     continue;
                 }

@@ -101,26 +101,28 @@ struct OpDesc {
     // tile i / fuse_nsub; this one is group fuse_isub), so groups that read
     // the same blocks read them at about the same time.  fuse_uni: every
     // operand of the group has the same t_shift, so each block is converted
-    // to fixed point once.  fuse_rows: contraction rows per thread (8 for up
-    // to 4 sources, 4 for up to 8).
+    // to fixed point once.
     int32_t fuse_src;
     int16_t fuse_ns;
     int8_t fuse_uni;
-    int8_t fuse_rows;
+    int8_t pad;
     int32_t fuse_coef;   // coefficient of source q (-1, 0, +1) in bits 2q, 2q + 1
     int16_t fuse_isub, fuse_nsub;
 };
 
-constexpr int FUSE_MAX_SRC = 8;   // source blocks of a fused prep group
+// Source blocks of a fused prep group: the four quadrants of one side of a
+// depth-1 block.  (Depth-2 groups of up to eight blocks, with four lanes of 4
+// rows per column, measured slower than the one-operand path: 12.3 against
+// 8.3 ms of prep at 16384^2.)
+constexpr int FUSE_MAX_SRC = 4;
 constexpr int FUSE_MAX_OPS = 8;   // operands of a fused prep group
 constexpr int FUSE_MAX_SUBGROUPS = 32;  // fused groups sharing one tile range
 
-// Fused prep tiles are 16 contraction rows x (16 x rows) columns: 16 / rows
-// lanes share a column (128 columns for 8 rows per lane, 64 for 4).
-inline int fused_tile_cols(int rows) { return 16 * rows; }
-inline int64_t fused_tiles_for(int64_t K_pitch, int64_t P_pad, int rows) {
-    const int tc = fused_tile_cols(rows);
-    return (K_pitch / KSTEP) * ((P_pad + tc - 1) / tc);
+// Fused prep tiles are 16 contraction rows x FUSED_TC columns: two lanes of
+// 8 rows each share a column.
+constexpr int FUSED_TC = 128;
+inline int64_t fused_tiles_for(int64_t K_pitch, int64_t P_pad) {
+    return (K_pitch / KSTEP) * ((P_pad + FUSED_TC - 1) / FUSED_TC);
 }
 
 struct Family {

@@ -71,8 +71,7 @@ int main(int argc, char **argv) {
         std::vector<std::vector<uint8_t>> seen(P.ops.size());
         for (size_t i = 0; i < P.ops.size(); ++i) {
             seen[i].assign(static_cast<size_t>(P.ops[i].fuse_ns > 0
-                                                   ? fused_tiles_for(P.ops[i].K_pitch, P.ops[i].P_pad,
-                                                                     P.ops[i].fuse_rows)
+                                                   ? fused_tiles_for(P.ops[i].K_pitch, P.ops[i].P_pad)
                                                    : prep_tiles_for(digits, P.ops[i].K_pitch, P.ops[i].P_pad, fp8)),
                            0);
             if (P.ops[i].ilv_i == 0) groups++;

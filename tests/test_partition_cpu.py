@@ -81,17 +81,16 @@ def test_wide_combine_regions(cli, m, n, mode, cutoff, depth, smin, variant, spl
 
 @pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,expect", [
     (8192, 8192, 1, 2048, 1, 4096, 0, 2),   # both sides of the top block's sums, four quadrants each
-    (8192, 8192, 1, 2048, 2, 2048, 0, 16),  # depth 2: one group per outer-level pattern and side
+    (8192, 8192, 1, 2048, 2, 2048, 0, 2),   # depth 2 (up to eight blocks): not fused; a depth-1 block is
     (531, 700, 1, 350, 1, 2, 1, 4),         # Winograd: mixed term counts, two blocks
     (1000, 1100, 2, 0, 1, 64, 0, 8),
-    (250, 330, 1, 0, 2, 16, 0, 14),
+    (250, 330, 1, 0, 2, 16, 0, 0),
     (700, 900, 5, 0, 1, 2, 0, 0)])          # FP8 planes are not fused
 def test_fused_prep_groups(cli, m, n, mode, cutoff, depth, smin, variant, expect):
-    """Operand sums that draw on the same few blocks of A are written from one
-    read of those blocks (a fused prep group: at depth 1 the four quadrants
-    of one side of a block, at depth 2 the up to eight blocks of one
-    outer-level pattern); the prep tile map still produces every tile of
-    every operand exactly once and every term names its own source block."""
+    """Operand sums that draw on the same four quadrants of A (one side of a
+    depth-1 block) are written from one read of them (a fused prep group);
+    the prep tile map still produces every tile of every operand exactly
+    once and every term names its own source block."""
     r = cli(m, n, mode, cutoff, depth, smin, 1, variant=variant)
     assert r["fused_groups"] == expect
     assert r["prep_map_ok"] == 1
