@@ -229,6 +229,22 @@ class Handle:
         return int(load().ata_batched_dev(self._h, count, I64(*ms), I64(*ns), A_table_ptr, I64(*ldas), C_table_ptr,
                                           I64(*ldcs), int(dtype), _stream_ptr(stream)))
 
+    def batched_dev_call(self, ms, ns, A_table_ptr, ldas, C_table_ptr, ldcs, dtype, stream=None):
+        """A zero-argument callable that runs ata_batched_dev with these
+        arguments, marshalled once (for calls repeated on the same shapes and
+        pointer tables; the tables' contents may change between calls)."""
+        count = len(ms)
+        I64 = ctypes.c_int64 * count
+        args = (self._h, count, I64(*ms), I64(*ns), ctypes.c_void_p(A_table_ptr), I64(*ldas),
+                ctypes.c_void_p(C_table_ptr), I64(*ldcs), int(dtype), _stream_ptr(stream))
+        fn = load().ata_batched_dev
+
+        def call():
+            rc = int(fn(*args))
+            if rc != 0:
+                raise AtaError(rc, f"ata_batched_dev [{self.last_error()}]")
+        return call
+
     def batched(self, As, Cs, dtype, stream=None):
         """low(C_i) <- low(A_i^T A_i) for lists of row-major CUDA tensors in one
         persistent launch (ata_batched)."""

@@ -205,6 +205,15 @@ def test_batched_dev_graph_replay_on_new_buffers(ata, mode):
     assert hd.sync() == 0
     for a, b in zip(C2, C3):
         assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0))
+    # and so does the pre-marshalled call on a third output table, twice
+    C4 = [torch.full_like(c, float("nan")) for c in C2]
+    t4 = ptr_table(C4)
+    call = hd.batched_dev_call(ms, ns, ta.data_ptr(), ldas, t4.data_ptr(), ldas, mode)
+    for _ in range(2):
+        call()
+        assert hd.sync() == 0
+        for a, b in zip(C2, C4):
+            assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0))
     hd.close()
 
 
