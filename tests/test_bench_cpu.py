@@ -21,7 +21,7 @@ def test_traffic_key_matches_committed_sources():
     assert isinstance(t, int) and t > 2_000_000_000  # at least the algorithmic 2.3 GB
 
 
-@pytest.mark.parametrize("cfg", [(2, 8192, 8192, 1, 3), (1, 4096, 4096, 1, 6), (1, 8192, 8192, 0, 6),
+@pytest.mark.parametrize("cfg", [(2, 8192, 8192, 1, 3), (1, 4096, 4096, 1, 6), (1, 8192, 8192, 2, 6),
                                  (1, 8192, 8192, 1, 5)])
 def test_traffic_only_for_the_measured_configuration(cfg):
     assert bench.leaf_traffic(*cfg) is None
