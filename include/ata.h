@@ -90,7 +90,9 @@ typedef struct {
                             (Algorithm 1 base case); 0 = auto                     */
     int strassen_depth;  /* Strassen levels on every off-diagonal block
                             (0 = classical tiles, i.e. plain tiled AtA);
-                            -1 = auto.  At most ATA_MAX_STRASSEN_DEPTH; a
+                            -1 = auto (1 for n >= 4096 in ATA_F64, and in
+                            ATA_F64_EMU when also m >= 4096; else 0).  At
+                            most ATA_MAX_STRASSEN_DEPTH; a
                             level splits a block only while both its sides
                             are >= strassen_min, so ATA_MAX_STRASSEN_DEPTH
                             recurses Strassen down to that size cutoff, as

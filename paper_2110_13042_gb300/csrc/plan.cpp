@@ -860,7 +860,22 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         if (err) *err = "slices out of range";
         return false;
     }
-    P.depth = pp.depth >= 0 ? pp.depth : (pp.n >= 4096 ? 1 : 0);
+    // Automatic depth: one Strassen level from n = 4096 in the FP64 modes.
+    // A level saves 1/8 of the top block's leaf work and adds operand sums and
+    // exact products that are written and summed again, in proportion to the
+    // block's area, not its contraction: measured on GB300, it pays for
+    // F64_EMU only with m >= 4096 (2048 x 65536: 61.2 with, 61.9 TFLOP/s
+    // without), and the cheaper FP32, one-digit and FP8 leaves lost at 8192^2
+    // (141 / 312 / 303 against 146 / 361 / 512 TFLOP/s), so there it is 0.
+    // Native FP64 leaves are slow enough for any level to pay.
+    if (pp.depth >= 0)
+        P.depth = pp.depth;
+    else if (pp.mode == MODE_F64)
+        P.depth = pp.n >= 4096 ? 1 : 0;
+    else if (pp.mode == MODE_F64_EMU)
+        P.depth = pp.n >= 4096 && pp.m >= 4096 ? 1 : 0;
+    else
+        P.depth = 0;
     if (P.depth > MAX_STRASSEN_DEPTH) P.depth = MAX_STRASSEN_DEPTH;
     if (pp.variant != VARIANT_STRASSEN && pp.variant != VARIANT_WINOGRAD) {
         if (err) *err = "unknown Strassen variant";
