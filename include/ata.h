@@ -150,7 +150,10 @@ int ata_set_config(ata_handle h, const ata_config *cfg);
 /* low(C) <- low(A^T A) for one m x n matrix (see the header comment).
  * dtype: one of ata_dtype.  Asynchronous on `stream`.  The first call for a
  * new (m, n, dtype) may grow the workspace with cudaMalloc (synchronous);
- * make it once before capturing the call in a CUDA graph. */
+ * make it once before capturing the call in a CUDA graph.  A captured call
+ * expects the handle's workspace to hold its plan's tables when it is
+ * replayed: between capture and replay, make no call of another shape,
+ * dtype or configuration on the same handle (use a handle per graph). */
 int ata_lower(ata_handle h, int64_t m, int64_t n, const void *A, int64_t lda,
               void *C, int64_t ldc, int dtype, void *stream);
 

@@ -446,6 +446,11 @@ int lower_impl(ata_handle h, int flags, int64_t m, int64_t n, double alpha, cons
         cudaError_t ce = cudaMemcpyAsync(h->ws + P.off_tables, cp->pinned, P.table_bytes,
                                          cudaMemcpyHostToDevice, s);
         if (ce != cudaSuccess) return fail(h, ATA_ERR_CUDA, "task-table upload", ce);
+        if (P.f0_zero) {  // the planes of A's zero padding (see Plan::f0_zero)
+            const Family &f0 = P.families[0];
+            ce = cudaMemsetAsync(h->ws + f0.offset, 0, static_cast<size_t>(f0.plane_elems) * 2 * P.slices, s);
+            if (ce != cudaSuccess) return fail(h, ATA_ERR_CUDA, "plane padding", ce);
+        }
         h->resident = cp;
     }
     uint8_t *ws = h->ws;

@@ -595,6 +595,7 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
     const int kh = k0 + R * part;
     T raw[NS][R];
     int ex[NS];
+    int64_t arow[NS], acol[NS];  // A position of this lane's first element of block q (-1: none)
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const bool present = q < ns;
@@ -605,6 +606,27 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
 #pragma unroll
         for (int j = 0; j < R; ++j) raw[q][j] = j < lim ? base[j * rs] : T(0);
         ex[q] = cv ? expo[sb.col0 + c] : 0;
+        arow[q] = lim > 0 ? sb.row0 + kh : -1;
+        acol[q] = sb.col0 + c;
+    }
+    if (L.fuse_f0) {
+        // The planes of A itself (family 0, no operand sum: t = 0) for the
+        // blocks' own elements: each block starts on a K step, so this
+        // lane's 8 rows are half of one image row of A's planes; rows past a
+        // block's end belong to the next block (or are A's zero padding).
+        const Family &f0 = fams.f[0];
+        const int64_t ncb0 = f0.cols / BLOCK_COLS;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            if (arow[q] < 0) continue;
+            const int r0 = static_cast<int>(acol[q] & (BLOCK_COLS - 1));
+            W w0[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) w0[j] = static_cast<W>(fixed(raw[q][j], F - ex[q])) + static_cast<W>(CADD);
+            uint8_t *dst = ws + f0.offset + (((arow[q] / KSTEP) * S) * ncb0 + acol[q] / BLOCK_COLS) * BLOCK_BYTES +
+                           r0 * 32;
+            store_digits_half<S>(w0, dst, ncb0 * BLOCK_BYTES, (part ^ ((r0 >> 2) & 1)) << 4);
+        }
     }
     // UNI: every source value rounded once, for all members
     V x[UNI ? NS : 1][R];

@@ -1063,12 +1063,49 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         std::vector<std::vector<std::vector<size_t>>> subs(groups.size());
         for (size_t g = 0; g < groups.size(); ++g)
             fused[g] = B.digits && !B.fp8 && fuse_group(P, groups[g], B.op_key, &subs[g]);
+        // The planes of A from the same reads: when fused sub-groups whose
+        // source blocks tile A exactly (the top block's two sides, at depth 1),
+        // every block starting on a K step, write family 0 too, and drop its
+        // own operand (one pass over A instead of two).
+        bool skip_f0 = false;
+        if (B.digits && !B.fp8 && pp.m > 0 && pp.n > 0) {
+            std::vector<std::pair<size_t, size_t>> chosen;  // (group, sub-group)
+            std::vector<OpTerm> cover;
+            int64_t area = 0;
+            for (size_t g = groups.size(); g-- > 0 && area < pp.m * pp.n;) {
+                if (!fused[g]) continue;
+                for (size_t k = subs[g].size(); k-- > 0 && area < pp.m * pp.n;) {
+                    const OpDesc &o = P.ops[subs[g][k][0]];
+                    bool ok = true;
+                    int64_t a = 0;
+                    for (int q = 0; q < o.fuse_ns && ok; ++q) {
+                        const OpTerm &sb = P.fsrc[static_cast<size_t>(o.fuse_src + q)];
+                        ok = sb.row0 % KSTEP == 0 && sb.row0 + sb.rows <= pp.m && sb.col0 + sb.cols <= pp.n;
+                        for (const OpTerm &c : cover)
+                            ok = ok && (sb.row0 + sb.rows <= c.row0 || c.row0 + c.rows <= sb.row0 ||
+                                        sb.col0 + sb.cols <= c.col0 || c.col0 + c.cols <= sb.col0);
+                        a += static_cast<int64_t>(sb.rows) * sb.cols;
+                    }
+                    if (!ok) continue;
+                    for (int q = 0; q < o.fuse_ns; ++q) cover.push_back(P.fsrc[static_cast<size_t>(o.fuse_src + q)]);
+                    area += a;
+                    chosen.push_back({g, k});
+                }
+            }
+            if (area == pp.m * pp.n) {
+                for (const auto &gk : chosen)
+                    for (size_t j : subs[gk.first][gk.second]) P.ops[j].fuse_f0 = 1;
+                skip_f0 = true;
+                P.f0_zero = true;
+            }
+        }
         std::vector<OpDesc> grouped;
         grouped.reserve(P.ops.size());
         for (int pass = 0; pass < 2; ++pass) {
             for (size_t g = 0; g < groups.size(); ++g) {
                 if (fused[g] != (pass == 0)) continue;
                 const OpDesc &key = P.ops[groups[g][0]];
+                if (skip_f0 && key.family == 0) continue;  // written by the fused groups
                 if (fused[g]) {  // sub-groups back to back, sharing one interleaved tile range
                     for (const std::vector<size_t> &members : subs[g])
                         for (size_t k = 0; k < members.size(); ++k) {

@@ -101,11 +101,13 @@ struct OpDesc {
     // tile i / fuse_nsub; this one is group fuse_isub), so groups that read
     // the same blocks read them at about the same time.  fuse_uni: every
     // operand of the group has the same t_shift, so each block is converted
-    // to fixed point once.
+    // to fixed point once.  fuse_f0: the group also writes the digit planes
+    // of A (family 0) for the elements of its source blocks (the top block's
+    // two sides, whose quadrants tile A; see Plan::f0_zero).
     int32_t fuse_src;
     int16_t fuse_ns;
     int8_t fuse_uni;
-    int8_t pad;
+    int8_t fuse_f0;
     int32_t fuse_coef;   // coefficient of source q (-1, 0, +1) in bits 2q, 2q + 1
     int16_t fuse_isub, fuse_nsub;
 };
@@ -305,6 +307,11 @@ struct Plan {
     int32_t n_units = 0;                // recursion units the tiles belong to
     int64_t prep_tiles = 0, comb_tiles = 0;
     int64_t fused_tiles = 0;            // prep tiles [0, fused_tiles) belong to fused groups
+    // The planes of A are written by the top block's fused groups, which
+    // cover A's rows and columns but not the planes' zero padding: the
+    // padding is zeroed once when the plan's tables are loaded into the
+    // workspace, and nothing else writes family 0 while they stay loaded.
+    bool f0_zero = false;
     // workspace layout (byte offsets)
     int64_t off_colmax = 0, off_expo = 0, off_products = 0, product_bytes = 0;
     int64_t off_tables = 0, table_bytes = 0, workspace_bytes = 0;

@@ -187,6 +187,16 @@ int main(int argc, char **argv) {
             fam[f].assign(static_cast<size_t>(P.families[f].K_pitch * P.families[f].cols), 0.0);
         for (const OpDesc &o : P.ops) {
             const Family &F = P.families[static_cast<size_t>(o.family)];
+            if (o.fuse_f0) {  // the group also writes family 0 for its source blocks
+                const Family &F0 = P.families[0];
+                for (int q = 0; q < o.fuse_ns; ++q) {
+                    const OpTerm &sb = P.fsrc[static_cast<size_t>(o.fuse_src + q)];
+                    for (int k = 0; k < sb.rows; ++k)
+                        for (int c = 0; c < sb.cols; ++c)
+                            fam[0][static_cast<size_t>((sb.row0 + k) * F0.cols + sb.col0 + c)] =
+                                A[static_cast<size_t>((sb.row0 + k) * n + sb.col0 + c)];
+                }
+            }
             for (int t = 0; t < o.nterms; ++t) {
                 const OpTerm &tm = P.terms[static_cast<size_t>(o.first_term + t)];
                 for (int k = 0; k < tm.rows; ++k)
@@ -238,9 +248,9 @@ int main(int argc, char **argv) {
     }
     int64_t wide = 0;  // combine regions summed in int128
     for (const CombDesc &d : P.combs) wide += d.wide;
-    std::printf("verify_err=%g verify_bounds_ok=%d wide_regions=%lld fused_groups=%lld fused_tiles=%lld ",
+    std::printf("verify_err=%g verify_bounds_ok=%d wide_regions=%lld fused_groups=%lld fused_tiles=%lld f0_fused=%d ",
                 verify_err, bounds_ok ? 1 : 0, static_cast<long long>(wide), static_cast<long long>(P.n_fused),
-                static_cast<long long>(P.fused_tiles));
+                static_cast<long long>(P.fused_tiles), P.f0_zero ? 1 : 0);
     std::printf("cutoff=%d depth=%d slices=%d panels=%lld blocks=%lld products=%lld tiles=%zu "
                 "covered=%lld overlap=%lld cterms=%zu ops=%zu families=%zu workspace=%lld "
                 "strassen_leaf_madds=%.0f strassen_plain_madds=%.0f reused=%lld cta_steps_max=%lld "

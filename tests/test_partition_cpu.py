@@ -113,3 +113,22 @@ def test_tail_split_plan_computes_the_product(cli):
     r = cli(2048, 600, 1, 0, 0, 4096, 1, verify=1)
     assert r["wide_regions"] > 0  # the split tiles' chunks
     assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
+
+
+@pytest.mark.parametrize("m,n,mode,cutoff,depth,smin,variant,f0", [
+    (8192, 8192, 1, 2048, 1, 4096, 0, 1),  # the top block's quadrants tile A
+    (512, 384, 1, 0, 1, 2, 0, 1),
+    (512, 384, 2, 0, 1, 2, 1, 1),          # Winograd, FP32
+    (513, 385, 1, 0, 1, 2, 0, 0),          # second row block starts off a K step: A keeps its own pass
+    (8192, 8192, 1, 8192, 0, 4096, 0, 0),  # no Strassen block
+    (700, 900, 5, 0, 1, 2, 0, 0)])         # FP8 is not fused
+def test_planes_of_a_from_the_fused_reads(cli, m, n, mode, cutoff, depth, smin, variant, f0):
+    """Where the fused groups' source blocks tile A exactly (the top block's
+    two sides at depth 1), they also write the digit planes of A, and A's own
+    prep pass is dropped; the plan still computes the product (interpreter,
+    small cases) and produces every prep tile once."""
+    verify = 1 if m * n <= 600 * 600 else 0
+    r = cli(m, n, mode, cutoff, depth, smin, 1, variant=variant, verify=verify)
+    assert r["f0_fused"] == f0 and r["prep_map_ok"] == 1
+    if verify:
+        assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
