@@ -285,3 +285,30 @@ def test_every_digit_count(h, slices, depth):
     Ci = run(h, Ai, F64_EMU, cutoff=70, depth=depth, slices=slices)
     low = np.tril_indices(277)
     assert np.array_equal(Ci[low], reference(Ai)[0][low])
+
+
+@pytest.mark.parametrize("mode", [F64_EMU, F32, F32_BF16])
+@pytest.mark.parametrize("m,n", [(512, 700), (1024, 385), (2048, 1301)])
+def test_planes_of_a_from_the_fused_sums(h, mode, m, n):
+    """Depth 1 with the top block's row split on a K step (m / 2 a multiple
+    of 16): the fused operand-sum prep also writes the digit planes of A and
+    A's own prep pass is skipped.  Exact on small integers (F32_BF16: within
+    its bound), oracle tolerance on random data, the strict upper triangle
+    untouched; twice in a row, and after a call of another shape on the same
+    handle (the planes' zero padding is restored when a plan is loaded)."""
+    Ai = inputs.integer_valued(m, n, seed=m + n, lo=-4, hi=4).astype(np.float32 if is_f32(mode) else np.float64)
+    refi, _ = reference(Ai)
+    low = np.tril_indices(n)
+    for _ in range(2):
+        C = run(h, Ai, mode, cutoff=max(1, n // 2), depth=1)
+        assert np.array_equal(C[low], refi[low])
+        assert upper_untouched(C)
+        run(h, inputs.uniform(300, 200, seed=1).astype(Ai.dtype), mode, cutoff=0, depth=0)  # another plan
+    Ar = inputs.uniform(m, n, seed=m * 3 + n).astype(Ai.dtype)
+    ref, D = reference(Ar)
+    C = run(h, Ar, mode, cutoff=max(1, n // 2), depth=1)
+    if mode == F32_BF16:
+        assert np.all(np.abs(C[low] - ref[low]) <= bf16_bound(Ar)[low] * (1 + 1e-6) + 1e-30)
+    else:
+        assert rel_err(C, ref, D) <= (1e-13 if mode == F64_EMU else 5e-5)
+    assert upper_untouched(C)
