@@ -65,18 +65,24 @@ constexpr int MAX_ACC = 5;
 constexpr int MAX_STAGES = 10;
 constexpr uint32_t IDESC = idesc_bf16_f32(TILE_M, TILE_N);
 constexpr uint32_t IDESC2 = idesc_bf16_f32(TILE_M, 2 * TILE_N);
-constexpr uint32_t IDESC8 = idesc_e4m3_f32(TILE_M, TILE_N);
+constexpr uint32_t IDESC8 = idesc_e4m3_f32(TILE_M, TILE_N8);  // the FP8 mode's 128 x 192 tile
 
-template <int S>
+template <int S, bool F8 = false>
 struct Cfg {
+    // Tile columns (the FP8 mode: 192, TILE_N8), the B slice of one K step
+    // (32-byte rows: 16 BF16 or 32 E4M3 values) and the columns each
+    // epilogue thread owns (a third of the tile).
+    static constexpr int TN = F8 ? TILE_N8 : TILE_N;
+    static constexpr int B_SLICE = TN * 32;
+    static constexpr int EPI = TN / 3;
     // K steps per pipeline stage.  Up to 3 digits the issuing thread does
     // its bookkeeping once per stage (see the issuer), so longer stages pay:
     // measured at 8192^2, one digit 8 steps (-38% leaf time against 1-step
     // bookkeeping), two and three digits 4 steps (-24% / -19%, although only
     // 2-4 stages fit).  From 4 digits on, drains fall inside 16-step spans
-    // and every step is a stage.
-    static constexpr int KPS = S == 1 ? 8 : S <= 3 ? 4 : 1;
-    static constexpr int STEP_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);
+    // and every step is a stage.  FP8 (twice the work per step): 4 steps.
+    static constexpr int KPS = F8 ? 4 : S == 1 ? 8 : S <= 3 ? 4 : 1;
+    static constexpr int STEP_BYTES = S * (A_SLICE_BYTES + B_SLICE);
     static constexpr int STAGE_BYTES = KPS * STEP_BYTES;
     static constexpr int STAGES_FIT = 229000 / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT < MAX_STAGES ? STAGES_FIT : MAX_STAGES;
@@ -85,12 +91,13 @@ struct Cfg {
     // alternate drain chunks, so the tensor core fills one while the
     // epilogue drains the other (with one buffer every drain idled it).
     static constexpr int NBUF = S == 1 ? 2 : NACC;
-    static constexpr int TMEM_COLS = NBUF == 1 ? 128 : NBUF == 2 ? 256 : 512;
+    static constexpr int TMEM_COLS = NBUF * TN <= 128 ? 128 : NBUF * TN <= 256 ? 256 : 512;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + BAR_BYTES;
     static_assert(STAGES >= 2, "pipeline depth");
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
-    static_assert(NBUF * TILE_N <= TMEM_COLS, "TMEM budget");
+    static_assert(NBUF * TN <= TMEM_COLS, "TMEM budget");
+    static_assert(EPI % 16 == 0, "16-column TMEM loads");
 };
 
 __host__ __device__ constexpr int acc_of(int p, int q) {
@@ -259,7 +266,7 @@ __device__ __forceinline__ bool wait_drained(IssueState &st, uint32_t mask, Shar
 template <int S, int ACC>
 __device__ __forceinline__ bool step_acc(IssueState &st, Shared *sh, uint32_t tmem, uint64_t da0,
                                          uint64_t db0, volatile int *abort_flag, int *status) {
-    if constexpr (ACC >= Cfg<S>::NACC) {
+    if constexpr (ACC >= Cfg<S, false>::NACC) {
         return true;
     } else {
         constexpr uint32_t bit = 1u << ACC;
@@ -344,29 +351,30 @@ __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase
 }
 
 // FP8 mode: drain the single accumulator (FP32 partial sums of E4M3
-// products over the chunk) into the thread's FP32 sums, zeroing it.
-__device__ __forceinline__ void drain_f8(float (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh, int buf) {
-    const uint32_t col = static_cast<uint32_t>(buf * TILE_N + colbase);
-    uint32_t r0[16], r1[16];
-    tmem_ld_32x32b_x16(tbase + col, r0);
-    tmem_ld_32x32b_x16(tbase + col + 16, r1);
+// products over the chunk) from TMEM buffer `buf` into the thread's FP32
+// sums (its EC columns of the 192-column tile), zeroing what it read.
+template <int EC>
+__device__ __forceinline__ void drain_f8(float (&T)[EC], uint32_t tbase, int colbase, Shared *sh, int buf) {
+    const uint32_t col = static_cast<uint32_t>(buf * TILE_N8 + colbase);
+    uint32_t r[EC / 16][16];
+#pragma unroll
+    for (int g = 0; g < EC / 16; ++g) tmem_ld_32x32b_x16(tbase + col + 16 * g, r[g]);
     tmem_ld_wait();
-    tmem_st_zero_32x32b_x16(tbase + col);
-    tmem_st_zero_32x32b_x16(tbase + col + 16);
+#pragma unroll
+    for (int g = 0; g < EC / 16; ++g) tmem_st_zero_32x32b_x16(tbase + col + 16 * g);
     tmem_st_wait();
     tc_fence_before();
     mbar_arrive(&sh->acce[buf]);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        T[i] += __uint_as_float(r0[i]);
-        T[16 + i] += __uint_as_float(r1[i]);
-    }
+    for (int g = 0; g < EC / 16; ++g)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) T[16 * g + i] += __uint_as_float(r[g][i]);
 }
 
 // F8: one E4M3 plane per operand (S == 1), K steps of 32 rows, FP32 sums.
 template <int S, bool F8 = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_constant__ LeafParams p) {
-    using C = Cfg<S>;
+    using C = Cfg<S, F8>;
     static_assert(!F8 || S == 1, "the FP8 mode has one plane");
     constexpr int KS = F8 ? KSTEP8 : KSTEP;  // contraction rows per K step
     // 5+ digits: three issuing threads (warps 1, 2, 3) owning accumulators
@@ -440,7 +448,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         for (int q = 0; q < S; ++q) {
                             bulk_load(a_dst + q * A_SLICE_BYTES, ua + (ku * S + q) * ua_step, A_SLICE_BYTES,
                                       &sh->full[stage]);
-                            bulk_load(b_dst + q * B_SLICE_BYTES, vb + (kv * S + q) * vb_step, B_SLICE_BYTES,
+                            bulk_load(b_dst + q * C::B_SLICE, vb + (kv * S + q) * vb_step, C::B_SLICE,
                                       &sh->full[stage]);
                         }
                     }
@@ -549,7 +557,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                             const uint64_t db0 = sdesc_kmajor_sw32(a_base + S * A_SLICE_BYTES);
                             // one digit: only the current buffer must be drained
                             const uint32_t need_a = S == 1 ? (1u << dbuf) : ~0x0Cu;
-                            const uint32_t tacc = S == 1 ? tmem + static_cast<uint32_t>(dbuf * TILE_N) : tmem;
+                            const uint32_t tacc = S == 1 ? tmem + static_cast<uint32_t>(dbuf * C::TN) : tmem;
 #pragma unroll
                             for (int kk = 0; kk < C::KPS; ++kk) {
                                 if (kk < cnt) {
@@ -625,20 +633,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
     } else if (warp >= EPI_WARP0) {
         // --------------------------------------------------- epilogue --
         const int q = warp & 3;                      // TMEM lane quadrant of this warp
-        const int third = (warp - EPI_WARP0) >> 2;   // which 32 columns
+        const int third = (warp - EPI_WARP0) >> 2;   // which third of the tile's columns
         const int row = 32 * q + lane;               // tile row == TMEM lane
         const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16);
-        const int colbase = EPI_COLS * third;
+        constexpr int EC = C::EPI;                   // columns per thread: 32 (FP8: 64)
+        const int colbase = EC * third;
         uint32_t accf_phase = 0;  // bit g: parity of the next wait on accf[g]
         int ebuf = 0;             // one digit: the buffer of the next drain
         bool ok = true;
         constexpr bool ZERO = S <= 4;  // the grouped issue path (see issue_group)
         if constexpr (ZERO) {
             // zero every accumulator once and hand it to the issuer
-            for (int a = 0; a < C::NBUF; ++a) {
-                tmem_st_zero_32x32b_x16(tbase + a * TILE_N + colbase);
-                tmem_st_zero_32x32b_x16(tbase + a * TILE_N + colbase + 16);
-            }
+            for (int a = 0; a < C::NBUF; ++a)
+#pragma unroll
+                for (int g = 0; g < EC / 16; ++g) tmem_st_zero_32x32b_x16(tbase + a * C::TN + colbase + 16 * g);
             tmem_st_wait();
             tc_fence_before();
             for (int a = 0; a < C::NBUF; ++a) mbar_arrive(&sh->acce[a]);
@@ -651,9 +659,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             const int h = p.tasks[ti].hbits;
             const float fold_scale = __uint_as_float(static_cast<unsigned>(127 + 27 + h) << 23);
             using Sum = typename std::conditional<F8, float, int64_t>::type;
-            Sum T[EPI_COLS];
+            Sum T[EC];
 #pragma unroll
-            for (int i = 0; i < EPI_COLS; ++i) T[i] = 0;
+            for (int i = 0; i < EC; ++i) T[i] = 0;
             for (int c = 0; c < nchunks; ++c) {
                 const bool last = c == nchunks - 1;
                 const uint32_t due = due_mask(c, last, C::NACC);
@@ -716,7 +724,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         double *out = static_cast<double *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
                         const double sc = exp2d(t.shift - 2 * FP8_TOP);
 #pragma unroll
-                        for (int i = 0; i < EPI_COLS; ++i) {
+                        for (int i = 0; i < EC; ++i) {
                             const int col = colbase + i;
                             if (col < lim) out[col] = static_cast<double>(T[i]) * sc;
                         }
@@ -725,7 +733,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                         float *out = static_cast<float *>(p.C) + c_row_offset(t, row, p.packed);
 #pragma unroll
-                        for (int i = 0; i < EPI_COLS; ++i) {
+                        for (int i = 0; i < EC; ++i) {
                             const int col = colbase + i;
                             if (col < lim) store_scaled(out + col, T[i] * exp2f_(er + (ev ? ev[col] : 0)), p.alpha, p.beta);
                         }
@@ -737,7 +745,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 if (t.kind == OUT_M_I64) {
                     int64_t *out = static_cast<int64_t *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
 #pragma unroll
-                    for (int i = 0; i < EPI_COLS; ++i) {
+                    for (int i = 0; i < EC; ++i) {
                         const int col = colbase + i;
                         if (col < lim) out[col] = T[i];
                     }
@@ -749,7 +757,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     if (t.kind == OUT_C_F64) {
                         double *out = static_cast<double *>(cbase) + c_row_offset(t, row, p.packed);
 #pragma unroll
-                        for (int i = 0; i < EPI_COLS; ++i) {
+                        for (int i = 0; i < EC; ++i) {
                             const int col = colbase + i;
                             if (col < lim)
                                 store_scaled(out + col, static_cast<double>(T[i]) * exp2d(er + (ev ? ev[col] : 0)),
@@ -758,7 +766,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     } else {
                         float *out = static_cast<float *>(cbase) + c_row_offset(t, row, p.packed);
 #pragma unroll
-                        for (int i = 0; i < EPI_COLS; ++i) {
+                        for (int i = 0; i < EC; ++i) {
                             const int col = colbase + i;
                             if (col < lim)
                                 store_scaled(out + col, __ll2float_rn(T[i]) * exp2f_(er + (ev ? ev[col] : 0)), p.alpha,
@@ -804,14 +812,14 @@ cudaError_t ensure_leaf_attr() {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(leaf_tc_kernel<S, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Cfg<S>::SMEM_BYTES);
+                             Cfg<S, F8>::SMEM_BYTES);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }
 
 template <int S, bool F8 = false>
 cudaError_t launch_s(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s) {
-    using C = Cfg<S>;
+    using C = Cfg<S, F8>;
     cudaError_t ea = ensure_leaf_attr<S, F8>();
     if (ea != cudaSuccess) return ea;
     const int ntasks = static_cast<int>(P.tasks.size());
@@ -865,8 +873,8 @@ cudaError_t launch_leaf_tc_group(const Plan &P, const LeafParams &lp, int64_t fi
     if (P.p.mode == MODE_F32_FP8) {
         cudaError_t e = ensure_leaf_attr<1, true>();
         if (e != cudaSuccess) return e;
-        leaf_tc_kernel<1, true><<<count < ctas ? static_cast<int>(count) : ctas, NUM_THREADS, Cfg<1>::SMEM_BYTES,
-                                  s>>>(g);
+        leaf_tc_kernel<1, true><<<count < ctas ? static_cast<int>(count) : ctas, NUM_THREADS,
+                                  Cfg<1, true>::SMEM_BYTES, s>>>(g);
         return cudaGetLastError();
     }
     return launch_leaf_tc_raw(P.slices, g, g.ntasks, ctas, s);

@@ -119,8 +119,11 @@ struct Builder {
     std::vector<int64_t> op_key;
     int64_t n_strassen_blocks = 0;
 
+    int tn;  // leaf tile columns
+
     explicit Builder(Plan &p)
-        : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)) {}
+        : P(p), digits(p.p.mode != MODE_F64), fp8(p.p.mode == MODE_F32_FP8), kalign(kstep_rows(p.p.mode)),
+          tn(tile_cols(p.p.mode)) {}
 
     int family_for(int64_t K_nominal) {
         int64_t Kp = round_up(std::max<int64_t>(K_nominal, 1), PREP_K);
@@ -193,8 +196,8 @@ struct Builder {
         }
         t.unit = P.n_units - 1;
         P.tasks.push_back(t);
-        P.plain_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
-        P.leaf_madds += static_cast<double>(P.p.m) * TILE_M * TILE_N;
+        P.plain_madds += static_cast<double>(P.p.m) * TILE_M * tn;
+        P.leaf_madds += static_cast<double>(P.p.m) * TILE_M * tn;
     }
 
     // Tiles of the diagonal panel [c0, c0 + w) that hold lower-triangle entries.
@@ -203,9 +206,9 @@ struct Builder {
         P.n_units++;  // one recursion unit
         for (int64_t J = 0; J < ceil_div(w, TILE_M); ++J) {
             const int64_t rows = std::min<int64_t>(TILE_M, w - J * TILE_M);
-            for (int64_t K = 0; K * TILE_N < w && K * TILE_N <= J * TILE_M + rows - 1; ++K)
-                plain_tile(c0 + J * TILE_M, c0 + K * TILE_N, rows,
-                           std::min<int64_t>(TILE_N, w - K * TILE_N));
+            for (int64_t K = 0; K * tn < w && K * tn <= J * TILE_M + rows - 1; ++K)
+                plain_tile(c0 + J * TILE_M, c0 + K * tn, rows,
+                           std::min<int64_t>(tn, w - K * tn));
         }
     }
 
@@ -213,9 +216,9 @@ struct Builder {
     void classical_block(int64_t r0, int64_t p, int64_t c0, int64_t q) {
         P.n_units++;  // one recursion unit
         for (int64_t J = 0; J < ceil_div(p, TILE_M); ++J)
-            for (int64_t K = 0; K < ceil_div(q, TILE_N); ++K)
-                plain_tile(r0 + J * TILE_M, c0 + K * TILE_N, std::min<int64_t>(TILE_M, p - J * TILE_M),
-                           std::min<int64_t>(TILE_N, q - K * TILE_N));
+            for (int64_t K = 0; K < ceil_div(q, tn); ++K)
+                plain_tile(r0 + J * TILE_M, c0 + K * tn, std::min<int64_t>(TILE_M, p - J * TILE_M),
+                           std::min<int64_t>(tn, q - K * tn));
     }
 
     int block_depth(int64_t p, int64_t q) const {
@@ -247,7 +250,7 @@ struct Builder {
         if (digits && reuse_quadrants && tt.size() == 1 && tt[0].coef == 1) {
             const OpTerm &t = tt[0];
             const Family &f0 = P.families[0];
-            const int64_t f0_cols = round_up(std::max<int64_t>(P.p.n, 1), TILE) + TILE;
+            const int64_t f0_cols = round_up(std::max<int64_t>(P.p.n, 1), TILE) + std::max(TILE, tn);
             // The leaf reads whole K steps: the rows from rn up to the next
             // step boundary must be zero, i.e. rn is a whole number of steps,
             // or the region ends at the end of A (family 0 is zero below m).
@@ -320,31 +323,31 @@ struct Builder {
             P.n_products++;
             const int32_t unit = P.n_units++;  // every product is one recursion unit
             for (int64_t J = 0; J < ceil_div(pn, TILE_M); ++J) {
-                for (int64_t K = 0; K < ceil_div(qn, TILE_N); ++K) {
+                for (int64_t K = 0; K < ceil_div(qn, tn); ++K) {
                     LeafTask t{};
                     t.fam_u = U.fam;
                     t.fam_v = V.fam;
                     t.col_u = static_cast<int32_t>(U.col + J * TILE_M);
-                    t.col_v = static_cast<int32_t>(V.col + K * TILE_N);
+                    t.col_v = static_cast<int32_t>(V.col + K * tn);
                     t.k0 = static_cast<int32_t>(U.k0);
                     t.k0v = static_cast<int32_t>(V.k0);
                     t.klen = static_cast<int32_t>(rn);
                     t.rows = static_cast<int32_t>(std::min<int64_t>(TILE_M, pn - J * TILE_M));
-                    t.cols = static_cast<int32_t>(std::min<int64_t>(TILE_N, qn - K * TILE_N));
+                    t.cols = static_cast<int32_t>(std::min<int64_t>(tn, qn - K * tn));
                     t.diag = 0;
                     t.kind = digits && !fp8 ? OUT_M_I64 : OUT_M_F64;
                     t.shift = shift;
                     t.hbits = hb;
                     t.eu = t.ev = -1;
-                    t.out_off = prod_off[r] + J * TILE_M * qn + K * TILE_N;
+                    t.out_off = prod_off[r] + J * TILE_M * qn + K * tn;
                     t.out_ld = qn;
                     t.unit = unit;
                     P.tasks.push_back(t);
-                    P.leaf_madds += static_cast<double>(rn) * TILE_M * TILE_N;
+                    P.leaf_madds += static_cast<double>(rn) * TILE_M * tn;
                 }
             }
         }
-        P.plain_madds += static_cast<double>(P.p.m) * ceil_div(p, TILE_M) * ceil_div(q, TILE_N) * TILE_M * TILE_N;
+        P.plain_madds += static_cast<double>(P.p.m) * ceil_div(p, TILE_M) * ceil_div(q, tn) * TILE_M * tn;
 
         // Result sums, one per (row region, column region) of the C block.
         for (int64_t ir = 0; ir < nsub; ++ir) {
@@ -444,15 +447,15 @@ struct Builder {
             t.shift = fp8 ? 0 : -t.hbits;  // a product of single-term operands
             t.eu = t.ev = -1;
             t.out_off = prod_elems;
-            t.out_ld = TILE_N;
+            t.out_ld = tn;
             t.unit = P.n_units - 1;
             P.tasks.push_back(t);
-            terms.push_back({prod_elems, TILE_N, 1, t.shift, 0});
+            terms.push_back({prod_elems, tn, 1, t.shift, 0});
             klen.push_back(kl);
-            prod_elems += static_cast<int64_t>(TILE_M) * TILE_N;
-            P.leaf_madds += static_cast<double>(kl) * TILE_M * TILE_N;
+            prod_elems += static_cast<int64_t>(TILE_M) * tn;
+            P.leaf_madds += static_cast<double>(kl) * TILE_M * tn;
         }
-        P.plain_madds += static_cast<double>(m) * TILE_M * TILE_N;
+        P.plain_madds += static_cast<double>(m) * TILE_M * tn;
         add_comb(r0, c0, rows, cols, terms, klen, c0 + cols - 1 > r0);
     }
 
@@ -465,13 +468,13 @@ struct Builder {
             int64_t t = 0;
             for (int64_t J = 0; J < ceil_div(w, TILE_M); ++J) {
                 const int64_t rows = std::min<int64_t>(TILE_M, w - J * TILE_M);
-                t += std::min<int64_t>(ceil_div(w, TILE_N), (J * TILE_M + rows - 1) / TILE_N + 1);
+                t += std::min<int64_t>(ceil_div(w, tn), (J * TILE_M + rows - 1) / tn + 1);
             }
             return t * ks;
         }
         const int64_t n1 = (w / (2 * SPLIT_ALIGN)) * SPLIT_ALIGN;
         if (n1 == 0) return panel_steps(P.cutoff);
-        return panel_steps(n1) + panel_steps(w - n1) + ceil_div(w - n1, TILE_M) * ceil_div(n1, TILE_N) * ks;
+        return panel_steps(n1) + panel_steps(w - n1) + ceil_div(w - n1, TILE_M) * ceil_div(n1, tn) * ks;
     }
 
     int64_t strassen_steps(int64_t p, int64_t q, int d) const {
@@ -480,7 +483,7 @@ struct Builder {
         split_regions(p, d, &pn);
         split_regions(q, d, &qn);
         for (int l = 0; l < d; ++l) prods *= 7;
-        return prods * ceil_div(pn, TILE_M) * ceil_div(qn, TILE_N) * ceil_div(rn, KSTEP);
+        return prods * ceil_div(pn, TILE_M) * ceil_div(qn, tn) * ceil_div(rn, KSTEP);
     }
 
     void recurse(int64_t c0, int64_t w) {
@@ -982,6 +985,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     }
     Builder &B = *Bp;
     P.split_k = B.split_k;
+    P.tile_n = B.tn;
     if (B.comb_bound_max >= std::ldexp(1.0, 125)) {  // the int128 sum keeps 2 bits of margin
         if (err) *err = "internal: a combine sum could overflow 128 bits";
         return false;
@@ -1029,7 +1033,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
     P.off_colmax = take(pp.n * 8);
     P.off_expo = take(pp.n * 4);
     for (Family &f : P.families) {
-        f.cols += TILE;  // padding: a leaf box may extend up to TILE columns past the last operand
+        f.cols += std::max(TILE, B.tn);  // padding: a leaf box may extend a tile's width past the last operand
         f.plane_elems = f.cols * f.K_pitch;
         int64_t bytes = B.fp8 ? f.plane_elems : B.digits ? f.plane_elems * 2 * P.slices : f.plane_elems * 8;
         f.offset = take(bytes);

@@ -12,6 +12,12 @@ namespace ata {
 constexpr int TILE = 128;        // column padding unit of operand families
 constexpr int TILE_M = 128;      // leaf output tile rows (U-operand columns)
 constexpr int TILE_N = 96;       // leaf output tile columns (V-operand columns)
+// The FP8 mode's tiles are twice as wide (one accumulator, whose two TMEM
+// buffers take 2 x 192 of the 512 columns): its leaf is bound by operand
+// delivery, and a 128 x 192 tile moves 10 KB instead of 2 x 7 KB per K step
+// of the same work.
+constexpr int TILE_N8 = 2 * TILE_N;
+inline int tile_cols(int mode);
 constexpr int KSTEP = 16;        // contraction rows per pipeline stage (one MMA K step)
 constexpr int CHUNK_STEPS = 4;   // stages per exact-accumulation chunk (64 rows)
 // The leaf's exact int64 sum T is in units of 2^-T_FRAC of the leading digit
@@ -53,6 +59,7 @@ constexpr int KSTEP8 = 32;
 // FP8 prep tiles: 32 contraction rows (one FP8 K step) x 128 columns.
 constexpr int PREP8_TK = KSTEP8;
 constexpr int PREP8_TC = 128;
+inline int tile_cols(int mode) { return mode == MODE_F32_FP8 ? TILE_N8 : TILE_N; }
 inline int kstep_rows(int mode) { return mode == MODE_F32_FP8 ? KSTEP8 : KSTEP; }
 
 // One term of a (possibly summed) Strassen operand: a sub-block of A.
@@ -291,6 +298,7 @@ struct Plan {
     PlanParams p;
     int cutoff = 0, depth = 0, slices = 0, strassen_min = 0, variant = VARIANT_STRASSEN;
     int split_k = 1;       // contraction chunks per plain tile (1: none)
+    int tile_n = TILE_N;   // leaf tile columns (tile_cols of the mode)
     int64_t n_panels = 0, n_blocks = 0, n_products = 0;
     int64_t n_reused = 0;  // Strassen operands read from the planes of A
     int64_t n_tiles = 0;   // leaf tiles (tasks also holds empty balance fillers)

@@ -210,6 +210,8 @@ int main(int argc, char **argv) {
             if (t.klen == 0) continue;
             const Family &FU = P.families[static_cast<size_t>(t.fam_u)], &FV = P.families[static_cast<size_t>(t.fam_v)];
             const std::vector<double> &U = fam[static_cast<size_t>(t.fam_u)], &V = fam[static_cast<size_t>(t.fam_v)];
+            // the leaf loads whole TILE_M x tile_n boxes: inside the families' columns
+            if (t.col_u + TILE_M > FU.cols || t.col_v + P.tile_n > FV.cols || t.cols > P.tile_n) bounds_ok = false;
             for (int r = 0; r < t.rows; ++r)
                 for (int c = 0; c < t.cols; ++c) {
                     if (t.diag && c > r + t.diag_off) continue;

@@ -69,13 +69,15 @@ def test_create_without_gpu_is_unsupported(lib):
 TM, TN = 128, 96   # leaf tile: 128 rows (j) x 96 columns (k)
 
 
-def lower_tiles(n):
-    """Tiles of a TM x TN grid over an n x n matrix holding an entry k <= j."""
+def lower_tiles(n, tn=None):
+    """Tiles of a TM x TN grid (TN x 2 in the FP8 mode) over an n x n matrix
+    holding an entry k <= j."""
+    tn = tn or TN
     count = 0
     for J in range(-(-n // TM)):
         rows = min(TM, n - J * TM)
         K = 0
-        while K * TN < n and K * TN <= J * TM + rows - 1:
+        while K * tn < n and K * tn <= J * TM + rows - 1:
             count += 1
             K += 1
     return count
@@ -88,7 +90,7 @@ def test_plain_plan_is_all_lower_tiles(lib, n, mode):
     info = lib.plan_info(300, n, mode, h)
     # depth 0 is only chosen automatically for small n
     if info["depth"] == 0:
-        assert info["tiles"] == lower_tiles(n)
+        assert info["tiles"] == lower_tiles(n, 2 * TN if mode == 5 else TN)
         assert info["panels"] == 1 and info["products"] == 0
         assert info["leaf_madds"] == info["plain_madds"]
 
@@ -201,15 +203,18 @@ def test_invalid_parameters_rejected(plan_cli):
 
 @pytest.mark.parametrize("m,n,depth", [(1056, 2048, 1), (1000, 1024, 1), (531, 777, 2), (4099, 2048, 2)])
 def test_fp8_plan(plan_cli, m, n, depth):
-    """FP8 mode: the same tiles and Strassen products as one BF16 digit, one
-    byte per plane element (smaller workspace), and Strassen quadrants read
-    from the planes of A only where their row offset falls on a 32-row FP8
-    K step (a 16-row offset that a BF16 plane could serve is not enough)."""
-    r8 = plan_cli(m, n, 5, n // 4, depth)
-    rb = plan_cli(m, n, 4, n // 4, depth)
+    """FP8 mode: the same Strassen products as one BF16 digit on tiles twice
+    as wide (128 x 192: fewer tiles), one byte per plane element (smaller
+    workspace), and Strassen quadrants read from the planes of A only where
+    their row offset falls on a 32-row FP8 K step (a 16-row offset that a
+    BF16 plane could serve is not enough)."""
+    # (middle splits: the cost model that places Strassen splits counts tiles)
+    r8 = plan_cli(m, n, 5, n // 4, depth, split_search=0, split_k=1)
+    rb = plan_cli(m, n, 4, n // 4, depth, split_search=0, split_k=1)
     assert r8["slices"] == 1
-    for k in ("tiles", "products", "covered", "overlap", "cterms", "strassen_leaf_madds"):
+    for k in ("products", "covered", "overlap", "cterms"):
         assert r8[k] == rb[k], k
+    assert r8["tiles"] < rb["tiles"]
     assert r8["workspace"] < rb["workspace"]
     assert r8["reused"] <= rb["reused"]
     if (m + 1) // 2 % 32 == 16:
