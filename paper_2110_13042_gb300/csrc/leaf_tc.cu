@@ -67,12 +67,14 @@ constexpr uint32_t IDESC = idesc_bf16_f32(TILE_M, TILE_N);
 constexpr uint32_t IDESC2 = idesc_bf16_f32(TILE_M, 2 * TILE_N);
 constexpr uint32_t IDESC8 = idesc_e4m3_f32(TILE_M, TILE_N8);  // the FP8 mode's 128 x 192 tile
 
-template <int S, bool F8 = false>
+// W1: one BF16 digit on the wide 128 x 192 tile with 32-bit sums (plans
+// whose leaf contractions are at most ONE_DIGIT_WIDE_MAX_K rows).
+template <int S, bool F8 = false, bool W1 = false>
 struct Cfg {
-    // Tile columns (the FP8 mode: 192, TILE_N8), the B slice of one K step
-    // (32-byte rows: 16 BF16 or 32 E4M3 values) and the columns each
+    // Tile columns (one-digit wide tiles: 192, TILE_N8), the B slice of one
+    // K step (32-byte rows: 16 BF16 or 32 E4M3 values) and the columns each
     // epilogue thread owns (a third of the tile).
-    static constexpr int TN = F8 ? TILE_N8 : TILE_N;
+    static constexpr int TN = (F8 || W1) ? TILE_N8 : TILE_N;
     static constexpr int B_SLICE = TN * 32;
     static constexpr int EPI = TN / 3;
     // K steps per pipeline stage.  Up to 3 digits the issuing thread does
@@ -81,7 +83,7 @@ struct Cfg {
     // bookkeeping), two and three digits 4 steps (-24% / -19%, although only
     // 2-4 stages fit).  From 4 digits on, drains fall inside 16-step spans
     // and every step is a stage.  FP8 (twice the work per step): 4 steps.
-    static constexpr int KPS = F8 ? 4 : S == 1 ? 8 : S <= 3 ? 4 : 1;
+    static constexpr int KPS = (F8 || W1) ? 4 : S == 1 ? 8 : S <= 3 ? 4 : 1;
     static constexpr int STEP_BYTES = S * (A_SLICE_BYTES + B_SLICE);
     static constexpr int STAGE_BYTES = KPS * STEP_BYTES;
     static constexpr int STAGES_FIT = 229000 / STAGE_BYTES;
@@ -371,11 +373,34 @@ __device__ __forceinline__ void drain_f8(float (&T)[EC], uint32_t tbase, int col
         for (int i = 0; i < 16; ++i) T[16 * g + i] += __uint_as_float(r[g][i]);
 }
 
+// One BF16 digit on the wide tile: drain the accumulator (exact integer
+// digit-product sums of at most 2^24 over the 256-row chunk) from TMEM
+// buffer `buf` into the thread's 32-bit sums, zeroing what it read.
+template <int EC>
+__device__ __forceinline__ void drain_w1(int32_t (&T)[EC], uint32_t tbase, int colbase, Shared *sh, int buf) {
+    const uint32_t col = static_cast<uint32_t>(buf * TILE_N8 + colbase);
+    uint32_t r[EC / 16][16];
+#pragma unroll
+    for (int g = 0; g < EC / 16; ++g) tmem_ld_32x32b_x16(tbase + col + 16 * g, r[g]);
+    tmem_ld_wait();
+#pragma unroll
+    for (int g = 0; g < EC / 16; ++g) tmem_st_zero_32x32b_x16(tbase + col + 16 * g);
+    tmem_st_wait();
+    tc_fence_before();
+    mbar_arrive(&sh->acce[buf]);
+#pragma unroll
+    for (int g = 0; g < EC / 16; ++g)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) T[16 * g + i] += __float2int_rn(__uint_as_float(r[g][i]));
+}
+
 // F8: one E4M3 plane per operand (S == 1), K steps of 32 rows, FP32 sums.
-template <int S, bool F8 = false>
+// W1: one BF16 digit on the 128 x 192 tile, 32-bit exact sums.
+template <int S, bool F8 = false, bool W1 = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_constant__ LeafParams p) {
-    using C = Cfg<S, F8>;
+    using C = Cfg<S, F8, W1>;
     static_assert(!F8 || S == 1, "the FP8 mode has one plane");
+    static_assert(!W1 || (S == 1 && !F8), "wide 32-bit sums: one BF16 digit");
     constexpr int KS = F8 ? KSTEP8 : KSTEP;  // contraction rows per K step
     // 5+ digits: three issuing threads (warps 1, 2, 3) owning accumulators
     // {4}, {0, 1}, {2, 3} (issuer_of), so a drain wait stalls only the issuer
@@ -568,6 +593,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                     }
                                     if constexpr (F8)
                                         umma_f8(tacc, da0 + off, db0 + off, IDESC8, 1u);
+                                    else if constexpr (W1)
+                                        umma_f16(tacc, da0 + off, db0 + off, IDESC2, 1u);  // N = 192
                                     else
                                         issue_group<S, false>(tacc, da0 + off, db0 + off);
                                     if (kk == 0 && (st.pending & 0x0Cu)) {
@@ -658,7 +685,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             const int nchunks = (nsteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
             const int h = p.tasks[ti].hbits;
             const float fold_scale = __uint_as_float(static_cast<unsigned>(127 + 27 + h) << 23);
-            using Sum = typename std::conditional<F8, float, int64_t>::type;
+            using Sum = typename std::conditional<F8, float,
+                                                  typename std::conditional<W1, int32_t, int64_t>::type>::type;
             Sum T[EC];
 #pragma unroll
             for (int i = 0; i < EC; ++i) T[i] = 0;
@@ -704,6 +732,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 tc_fence_after();
                 if constexpr (F8) {
                     drain_f8(T, tbase, colbase, sh, ebuf);
+                } else if constexpr (W1) {
+                    drain_w1(T, tbase, colbase, sh, ebuf);
                 } else {
                     if (due & 16u) drain_one<4, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
                     if (due & 1u) drain_one<0, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale, S == 1 ? ebuf : 0);
@@ -742,15 +772,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
             } else if (row < t.rows) {
                 const int lim0 = t.diag ? min(t.cols, row + t.diag_off + 1) : t.cols;
                 const int lim = lim0 < 0 ? 0 : lim0;
+                // W1 sums are in units of the digit product, 2^(27 + h) of T's unit
+                const int wsh = W1 ? 27 + t.hbits : 0;
                 if (t.kind == OUT_M_I64) {
                     int64_t *out = static_cast<int64_t *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
+                    const int64_t wmul = int64_t(1) << wsh;
 #pragma unroll
                     for (int i = 0; i < EC; ++i) {
                         const int col = colbase + i;
-                        if (col < lim) out[col] = T[i];
+                        if (col < lim) out[col] = static_cast<int64_t>(T[i]) * wmul;
                     }
                 } else {
-                    const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) - t.hbits + t.shift +
+                    const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) - t.hbits + t.shift + wsh +
                                    (t.eu >= 0 ? p.expo[t.eu + row] : 0);
                     const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                     void *cbase = p.probs ? p.probs[t.prob].C : p.C;
@@ -769,8 +802,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         for (int i = 0; i < EC; ++i) {
                             const int col = colbase + i;
                             if (col < lim)
-                                store_scaled(out + col, __ll2float_rn(T[i]) * exp2f_(er + (ev ? ev[col] : 0)), p.alpha,
-                                             p.beta);
+                                store_scaled(out + col,
+                                             __ll2float_rn(static_cast<int64_t>(T[i])) * exp2f_(er + (ev ? ev[col] : 0)),
+                                             p.alpha, p.beta);
                         }
                     }
                 }
@@ -804,27 +838,27 @@ __global__ void wait_check_kernel(int *status, unsigned long long budget_ns) {
 
 // The shared-memory opt-in of leaf_tc_kernel<S>, set once per device (a
 // later call, e.g. inside a graph capture, needs no attribute change).
-template <int S, bool F8 = false>
+template <int S, bool F8 = false, bool W1 = false>
 cudaError_t ensure_leaf_attr() {
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(leaf_tc_kernel<S, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Cfg<S, F8>::SMEM_BYTES);
+    e = cudaFuncSetAttribute(leaf_tc_kernel<S, F8, W1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<S, F8, W1>::SMEM_BYTES);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }
 
-template <int S, bool F8 = false>
+template <int S, bool F8 = false, bool W1 = false>
 cudaError_t launch_s(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s) {
-    using C = Cfg<S, F8>;
-    cudaError_t ea = ensure_leaf_attr<S, F8>();
+    using C = Cfg<S, F8, W1>;
+    cudaError_t ea = ensure_leaf_attr<S, F8, W1>();
     if (ea != cudaSuccess) return ea;
     const int ntasks = static_cast<int>(P.tasks.size());
     const int grid = ntasks < num_sms ? ntasks : num_sms;
-    leaf_tc_kernel<S, F8><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(lp);
+    leaf_tc_kernel<S, F8, W1><<<grid, NUM_THREADS, C::SMEM_BYTES, s>>>(lp);
     return cudaGetLastError();
 }
 
@@ -846,6 +880,7 @@ int leaf_tc_smem_bytes(int slices) {
 cudaError_t launch_leaf_tc(const Plan &P, const LeafParams &lp, int num_sms, cudaStream_t s) {
     if (P.tasks.empty()) return cudaSuccess;
     if (P.p.mode == MODE_F32_FP8) return launch_s<1, true>(P, lp, num_sms, s);
+    if (P.slices == 1 && P.tile_n == TILE_N8) return launch_s<1, false, true>(P, lp, num_sms, s);
     switch (P.slices) {
         case 1: return launch_s<1>(P, lp, num_sms, s);
         case 2: return launch_s<2>(P, lp, num_sms, s);
@@ -875,6 +910,13 @@ cudaError_t launch_leaf_tc_group(const Plan &P, const LeafParams &lp, int64_t fi
         if (e != cudaSuccess) return e;
         leaf_tc_kernel<1, true><<<count < ctas ? static_cast<int>(count) : ctas, NUM_THREADS,
                                   Cfg<1, true>::SMEM_BYTES, s>>>(g);
+        return cudaGetLastError();
+    }
+    if (P.slices == 1 && P.tile_n == TILE_N8) {
+        cudaError_t e = ensure_leaf_attr<1, false, true>();
+        if (e != cudaSuccess) return e;
+        leaf_tc_kernel<1, false, true><<<count < ctas ? static_cast<int>(count) : ctas, NUM_THREADS,
+                                         Cfg<1, false, true>::SMEM_BYTES, s>>>(g);
         return cudaGetLastError();
     }
     return launch_leaf_tc_raw(P.slices, g, g.ntasks, ctas, s);

@@ -901,6 +901,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
 
     // Build the task lists, with `split` contraction chunks per plain tile.
     std::unique_ptr<Builder> Bp;
+    int tn_use = tile_cols(pp.mode);
     auto build = [&](int split, int64_t tail_from, int tail_parts) {
         P.families.clear();
         P.ops.clear();
@@ -915,6 +916,7 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         P.leaf_madds = P.plain_madds = 0;
         Bp.reset(new Builder(P));
         Builder &B = *Bp;
+        B.tn = tn_use;
         B.split_k = split;
         B.tail_from = tail_from;
         B.tail_parts = tail_parts;
@@ -933,55 +935,70 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
         }
         if (pp.n > 0 && pp.m > 0) B.recurse(0, pp.n);
     };
-    // Split contraction (digit modes): when the plan has too few tiles to keep
-    // every CTA busy and the contraction is long, or when asked for.
-    int split = 1;
-    const bool can_split = pp.mode != MODE_F64;
-    if (can_split && pp.split_k > 1) split = std::min(pp.split_k, SPLITK_MAX);
-    build(split, -1, 1);
+    // The tile layout: whole tiles, then an automatic split contraction and
+    // tail split (below); for the one-digit BF16 mode, redone with 96-column
+    // tiles if a leaf contraction came out longer than its wide tiles' 32-bit
+    // sums allow.
     const int ctas = pp.num_ctas > 1 ? pp.num_ctas : 152;
-    if (can_split && pp.split_k == 0 && static_cast<int64_t>(P.tasks.size()) < SPLITK_TILES_PER_CTA * ctas &&
-        pp.m >= 2 * SPLITK_MIN_ROWS) {
-        int64_t s = 2;
-        while (s < SPLITK_MAX && static_cast<int64_t>(P.tasks.size()) * s < SPLITK_TILES_PER_CTA * ctas &&
-               pp.m / (2 * s) >= SPLITK_MIN_ROWS)
-            s *= 2;
-        build(static_cast<int>(s), -1, 1);
-    }
-    // Tail split: when the plain tiles (all of contraction m) leave the last
-    // wave of the persistent CTAs partly idle, the last q of them (q = plain
-    // tiles mod CTAs) are computed as contraction chunks, which the
-    // longest-first layout spreads over the idle CTAs; chosen by simulating
-    // the layout, and kept only if it shortens the busiest CTA by >= 0.5%.
-    if (can_split && pp.split_k == 0 && Bp->split_k == 1 && pp.streams <= 1 && Bp->n_plain > 0) {
-        const int64_t q = Bp->n_plain % ctas;
-        const int64_t m_steps = ceil_div(pp.m, KSTEP);
-        std::vector<int64_t> steps;
-        for (const LeafTask &t : P.tasks) steps.push_back(ceil_div(t.klen, KSTEP));
-        const int64_t base = lpt_makespan(steps, ctas);
-        int best_parts = 1;
-        int64_t best = base;
-        for (int parts : {2, 3, 4, 6, 8}) {
-            const int64_t chunk = round_up(ceil_div(pp.m, parts), 256);
-            if (q == 0 || chunk < 1024 || chunk >= pp.m) continue;
-            std::vector<int64_t> st;
-            int64_t removed = 0;
-            for (int64_t v : steps) {
-                if (v == m_steps && removed < q) {
-                    ++removed;
-                    for (int64_t k0 = 0; k0 < pp.m; k0 += chunk)
-                        st.push_back(ceil_div(std::min(chunk, pp.m - k0), KSTEP));
-                } else {
-                    st.push_back(v);
+    auto layout = [&]() {
+        // Split contraction (digit modes): when the plan has too few tiles to keep
+        // every CTA busy and the contraction is long, or when asked for.
+        int split = 1;
+        const bool can_split = pp.mode != MODE_F64;
+        if (can_split && pp.split_k > 1) split = std::min(pp.split_k, SPLITK_MAX);
+        build(split, -1, 1);
+        if (can_split && pp.split_k == 0 && static_cast<int64_t>(P.tasks.size()) < SPLITK_TILES_PER_CTA * ctas &&
+            pp.m >= 2 * SPLITK_MIN_ROWS) {
+            int64_t s = 2;
+            while (s < SPLITK_MAX && static_cast<int64_t>(P.tasks.size()) * s < SPLITK_TILES_PER_CTA * ctas &&
+                   pp.m / (2 * s) >= SPLITK_MIN_ROWS)
+                s *= 2;
+            build(static_cast<int>(s), -1, 1);
+        }
+        // Tail split: when the plain tiles (all of contraction m) leave the last
+        // wave of the persistent CTAs partly idle, the last q of them (q = plain
+        // tiles mod CTAs) are computed as contraction chunks, which the
+        // longest-first layout spreads over the idle CTAs; chosen by simulating
+        // the layout, and kept only if it shortens the busiest CTA by >= 0.5%.
+        if (can_split && pp.split_k == 0 && Bp->split_k == 1 && pp.streams <= 1 && Bp->n_plain > 0) {
+            const int64_t q = Bp->n_plain % ctas;
+            const int64_t m_steps = ceil_div(pp.m, KSTEP);
+            std::vector<int64_t> steps;
+            for (const LeafTask &t : P.tasks) steps.push_back(ceil_div(t.klen, KSTEP));
+            const int64_t base = lpt_makespan(steps, ctas);
+            int best_parts = 1;
+            int64_t best = base;
+            for (int parts : {2, 3, 4, 6, 8}) {
+                const int64_t chunk = round_up(ceil_div(pp.m, parts), 256);
+                if (q == 0 || chunk < 1024 || chunk >= pp.m) continue;
+                std::vector<int64_t> st;
+                int64_t removed = 0;
+                for (int64_t v : steps) {
+                    if (v == m_steps && removed < q) {
+                        ++removed;
+                        for (int64_t k0 = 0; k0 < pp.m; k0 += chunk)
+                            st.push_back(ceil_div(std::min(chunk, pp.m - k0), KSTEP));
+                    } else {
+                        st.push_back(v);
+                    }
+                }
+                const int64_t ms = lpt_makespan(st, ctas);
+                if (ms < best) {
+                    best = ms;
+                    best_parts = parts;
                 }
             }
-            const int64_t ms = lpt_makespan(st, ctas);
-            if (ms < best) {
-                best = ms;
-                best_parts = parts;
-            }
+            if (best_parts > 1 && best * 200 <= base * 199) build(1, Bp->n_plain - q, best_parts);
         }
-        if (best_parts > 1 && best * 200 <= base * 199) build(1, Bp->n_plain - q, best_parts);
+    };
+    layout();
+    if (pp.mode == MODE_F32_BF16 && tn_use != TILE_N) {
+        int64_t kmax = 0;
+        for (const LeafTask &t : P.tasks) kmax = std::max<int64_t>(kmax, t.klen);
+        if (kmax > ONE_DIGIT_WIDE_MAX_K) {
+            tn_use = TILE_N;
+            layout();
+        }
     }
     Builder &B = *Bp;
     P.split_k = B.split_k;

@@ -12,10 +12,10 @@ namespace ata {
 constexpr int TILE = 128;        // column padding unit of operand families
 constexpr int TILE_M = 128;      // leaf output tile rows (U-operand columns)
 constexpr int TILE_N = 96;       // leaf output tile columns (V-operand columns)
-// The FP8 mode's tiles are twice as wide (one accumulator, whose two TMEM
-// buffers take 2 x 192 of the 512 columns): its leaf is bound by operand
-// delivery, and a 128 x 192 tile moves 10 KB instead of 2 x 7 KB per K step
-// of the same work.
+// The one-digit modes' tiles (FP8, and BF16 when every contraction is short
+// enough) are twice as wide (one accumulator, whose two TMEM buffers take
+// 2 x 192 of the 512 columns): their leaf is bound by operand delivery, and a
+// 128 x 192 tile moves 10 KB instead of 2 x 7 KB per K step of the same work.
 constexpr int TILE_N8 = 2 * TILE_N;
 inline int tile_cols(int mode);
 constexpr int KSTEP = 16;        // contraction rows per pipeline stage (one MMA K step)
@@ -59,7 +59,12 @@ constexpr int KSTEP8 = 32;
 // FP8 prep tiles: 32 contraction rows (one FP8 K step) x 128 columns.
 constexpr int PREP8_TK = KSTEP8;
 constexpr int PREP8_TC = 128;
-inline int tile_cols(int mode) { return mode == MODE_F32_FP8 ? TILE_N8 : TILE_N; }
+inline int tile_cols(int mode) { return mode == MODE_F32_FP8 || mode == MODE_F32_BF16 ? TILE_N8 : TILE_N; }
+// The one-digit BF16 mode's wide tiles keep their exact sums in 32 bits: each
+// 256-row chunk adds at most 2^24 (in units of the digit product), so a
+// contraction of up to 16384 rows stays below 2^30.  A plan with a longer
+// leaf contraction uses the 96-column tiles and 64-bit sums.
+constexpr int64_t ONE_DIGIT_WIDE_MAX_K = 16384;
 inline int kstep_rows(int mode) { return mode == MODE_F32_FP8 ? KSTEP8 : KSTEP; }
 
 // One term of a (possibly summed) Strassen operand: a sub-block of A.

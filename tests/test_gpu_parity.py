@@ -312,3 +312,18 @@ def test_planes_of_a_from_the_fused_sums(h, mode, m, n):
     else:
         assert rel_err(C, ref, D) <= (1e-13 if mode == F64_EMU else 5e-5)
     assert upper_untouched(C)
+
+
+def test_one_digit_wide_tile_at_its_contraction_limit(h):
+    """One BF16 digit on 128 x 192 tiles keeps 32-bit sums for contractions
+    of up to 16384 rows: with every digit at its largest (|x| = 256, from
+    entries just below the column's power of two) the sum reaches 2^30 and
+    must not wrap.  The result is then exactly m (each entry rounds to 1)."""
+    m, n = 16384, 200
+    A = np.full((m, n), 0.999, dtype=np.float32)
+    A[::2, 1::2] = -0.999  # mixed signs in some columns
+    C = run(h, A, F32_BF16, cutoff=0, depth=0)
+    ref = oracle.ata_lower(np.where(A > 0, 1.0, -1.0))  # the digit-rounded matrix, exactly
+    low = np.tril_indices(n)
+    assert np.array_equal(C[low], ref[low])
+    assert upper_untouched(C)

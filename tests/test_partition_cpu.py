@@ -132,3 +132,15 @@ def test_planes_of_a_from_the_fused_reads(cli, m, n, mode, cutoff, depth, smin, 
     assert r["f0_fused"] == f0 and r["prep_map_ok"] == 1
     if verify:
         assert r["verify_err"] == 0.0 and r["verify_bounds_ok"] == 1
+
+
+@pytest.mark.parametrize("m,expect_wide", [(300, True), (16384, True), (16385, False), (40000, False)])
+def test_one_digit_bf16_tile_width(cli, m, expect_wide):
+    """One BF16 digit runs on 128 x 192 tiles with 32-bit sums only while
+    every leaf contraction is at most 16384 rows (each 256-row chunk adds at
+    most 2^24); longer plans keep the 96-column tiles and 64-bit sums."""
+    n = 700
+    wide = cli(m, n, 4, 0, 0, 4096, 1, split=1)
+    narrow = cli(m, n, 2, 0, 0, 4096, 1, split=1)  # FP32 (3 digits): always 96 columns
+    assert (wide["tiles"] < narrow["tiles"]) == expect_wide
+    assert wide["covered"] == n * (n + 1) // 2 and wide["overlap"] == 0
