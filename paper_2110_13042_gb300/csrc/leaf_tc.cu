@@ -19,9 +19,13 @@
 // unit); h = min(9, 19 - log2 K) extra bits keep short contractions as
 // accurate as long ones.  The tile's value is T * 2^(-43 - h + shift + e_row + e_col).
 //
-// Tile 128 x 96: five 96-column FP32 accumulators fit the 512 TMEM columns
-// (one digit: the single accumulator has two buffers, filled and drained in
-// turn by alternate 16-step chunks).
+// Tile 128 x 96: five 96-column FP32 accumulators fit the 512 TMEM columns.
+// One digit (FP8, and one BF16 digit when every contraction is at most
+// ONE_DIGIT_WIDE_MAX_K rows): tile 128 x 192, whose single accumulator has two
+// 192-column buffers, filled and drained in turn by alternate 16-step chunks;
+// these leaves are bound by operand delivery, and the wide tile moves 10 KB
+// per K step instead of 2 x 7 KB for the same work.  One BF16 digit keeps its
+// exact sums in 32 bits there (at most 2^24 per 256-row chunk).
 // K step 16 (one MMA per digit pair per stage, 32-byte swizzle) keeps stages
 // small, so 4-10 of them are in flight.
 //
