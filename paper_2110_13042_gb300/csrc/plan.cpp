@@ -953,6 +953,9 @@ bool make_plan(const PlanParams &pp, Plan *plan, std::string *err) {
             while (s < SPLITK_MAX && static_cast<int64_t>(P.tasks.size()) * s < SPLITK_TILES_PER_CTA * ctas &&
                    pp.m / (2 * s) >= SPLITK_MIN_ROWS)
                 s *= 2;
+            // one BF16 digit on wide tiles: chunks short enough for 32-bit sums
+            if (pp.mode == MODE_F32_BF16 && tn_use != TILE_N)
+                while (s < SPLITK_MAX && round_up(ceil_div(pp.m, s), 256) > ONE_DIGIT_WIDE_MAX_K) s *= 2;
             build(static_cast<int>(s), -1, 1);
         }
         // Tail split: when the plain tiles (all of contraction m) leave the last
