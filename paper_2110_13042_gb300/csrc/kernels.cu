@@ -405,11 +405,18 @@ constexpr int PREP_SV = 4096 + 256;  // shared sums: (4096 / tc) x (tc + 1) entr
 // its subnormal grid) exact (Boldo and Melquiond, "Emulation of FMA and
 // correctly rounded sums: proved algorithms using rounding to odd", 2008).
 // |V| <= 2^FP8_FIX, so the scaled value stays below 2^FP8_TOP.
+// The truncation and the sticky bit are taken from the integer's bits (its
+// top 24 significant bits, and whether any bit below them is set), so the
+// only conversion is a 32-bit one: the 64-bit integer-float conversions ran
+// at a small fraction of the rate and bounded this kernel (same codes).
 __device__ __forceinline__ uint32_t e4m3_of_fixed(int64_t V) {
     const unsigned long long mag = V < 0 ? 0ull - static_cast<unsigned long long>(V) : static_cast<unsigned long long>(V);
-    float f = __ull2float_rz(mag);
-    if (__float2ull_rz(f) != mag) f = __uint_as_float(__float_as_uint(f) | 1u);
-    f *= __uint_as_float(static_cast<unsigned>(127 + FP8_TOP - FP8_FIX) << 23);
+    const int p = 63 - __clzll(static_cast<long long>(mag | 1ull));  // leading bit (mag < 2^48)
+    const int sh = p > 23 ? p - 23 : 0;
+    uint32_t m24 = static_cast<uint32_t>(mag >> sh);                  // truncated to 24 bits
+    if (sh > 0 && (mag & ((1ull << sh) - 1ull)) != 0ull) m24 |= 1u;   // round to odd
+    float f = __uint2float_rn(m24);                                    // exact: m24 < 2^24
+    f *= __uint_as_float(static_cast<unsigned>(127 + sh + FP8_TOP - FP8_FIX) << 23);
     return static_cast<uint32_t>(__nv_cvt_float_to_fp8(V < 0 ? -f : f, __NV_SATFINITE, __NV_E4M3));
 }
 
