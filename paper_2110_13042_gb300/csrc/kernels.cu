@@ -536,6 +536,59 @@ __device__ __forceinline__ void prep_tile_narrow(const T *__restrict__ A, int64_
     store_digits<S>(w, row0, ncb * BLOCK_BYTES, (r >> 2) & 1);
 }
 
+// FP8 prep tile (32 contraction rows x 128 columns) of a single-term
+// operand: each E4M3 value is the scaled entry a 2^(FP8_TOP - e) rounded to
+// nearest even directly.  The scaling is exact in FP32 (an entry that leaves
+// FP32's normal range lies far below E4M3's smallest subnormal), so this is
+// the same rounding as the oracle's quantisation; only sums of several
+// blocks (Strassen operands) need the exact fixed-point detour of prep_tile.
+// Each thread converts 16 rows of one column, with its 16 loads in flight,
+// and writes its 16-byte half of the column's 32-byte image row.
+template <typename T>
+__device__ __forceinline__ void prep_tile_f8_single(const T *__restrict__ A, int64_t lda, bool trans,
+                                                    const int *__restrict__ expo, const OpDesc &od,
+                                                    const OpTerm *terms, int64_t tile, const Family &fam,
+                                                    uint8_t *ws) {
+    constexpr int lgtc = 7, tc = 1 << lgtc, tk = 4096 >> lgtc;
+    const int64_t local = tile - od.tile_base;
+    const int tiles_k = od.K_pitch / tk;
+    const int k0 = static_cast<int>(local % tiles_k) * tk;
+    const int c0 = static_cast<int>(local / tiles_k) * tc;
+    const int cc = threadIdx.x & (tc - 1);
+    const int rg = threadIdx.x >> lgtc;
+    const int c = c0 + cc;
+    if (c >= od.P_pad) return;
+    const int kk = k0 + rg * KSTEP;
+    const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
+    const OpTerm tm = terms[od.first_term];
+    const bool cv = c < tm.cols;
+    const int lim = cv ? tm.rows - kk : 0;
+    const T *base = A + (tm.row0 + kk) * rs + (tm.col0 + c) * cs;
+    float raw[KSTEP];
+#pragma unroll
+    for (int j = 0; j < KSTEP; ++j) raw[j] = j < lim ? static_cast<float>(base[j * rs]) : 0.0f;
+    // 2^(FP8_TOP - e) (and the term's sign), built from its exponent bits
+    const int x = cv ? FP8_TOP - expo[tm.col0 + c] : 0;
+    const float sc = (x >= -126 && x <= 127 ? __uint_as_float(static_cast<unsigned>(x + 127) << 23)
+                                            : scalbnf(1.0f, x)) * (tm.coef < 0 ? -1.0f : 1.0f);
+    uint32_t pk[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        uint32_t w = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            w |= static_cast<uint32_t>(__nv_cvt_float_to_fp8(raw[4 * i + j] * sc, __NV_SATFINITE, __NV_E4M3))
+                 << (8 * j);
+        pk[i] = w;
+    }
+    const int64_t ncb = fam.cols / BLOCK_COLS;
+    const int r = cc & (BLOCK_COLS - 1);
+    const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
+    const int slot = ((kk / KSTEP) & 1) ^ ((r >> 2) & 1);
+    uint8_t *dst = ws + fam.offset + (static_cast<int64_t>(kk / KSTEP8) * ncb + cblk) * BLOCK_BYTES + r * 32 + slot * 16;
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+
 // Half an image row: contraction values 8h .. 8h + 7 of one column, digits
 // Q .. S - 1, one 16-byte store per digit plane at byte `off` (slot h ^ swz)
 // of the column's 32-byte image row.
@@ -707,6 +760,12 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
         if constexpr (!F8 && sizeof(T) == 4 && S <= 3) {
             prep_tile_narrow<S, T>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, 8);
             continue;
+        }
+        if constexpr (F8) {
+            if (od.nterms == 1) {
+                prep_tile_f8_single<T>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws);
+                continue;
+            }
         }
         // 16 x 256 tiles; FP8: 32 x 128 (one K step of the plane)
         prep_tile<S, T, F8>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, sV,
