@@ -589,6 +589,55 @@ __device__ __forceinline__ void prep_tile_f8_single(const T *__restrict__ A, int
     *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 
+// One-digit BF16 prep tile (16 contraction rows x 256 columns) of a
+// single-term operand: the digit is round(a 2^(8 - e)) (half away from zero,
+// as the fixed-point path rounds), an integer of at most 256 in magnitude
+// that BF16 holds exactly, computed directly from the scaled FP32 value (the
+// scaling is exact, and an entry below FP32's normal range scales to well
+// under 1/2, i.e. a zero digit).  Each thread converts 16 rows of one column
+// and writes its 32-byte image row as two 16-byte stores.
+template <typename T>
+__device__ __forceinline__ void prep_tile_bf16_single(const T *__restrict__ A, int64_t lda, bool trans,
+                                                      const int *__restrict__ expo, const OpDesc &od,
+                                                      const OpTerm *terms, int64_t tile, const Family &fam,
+                                                      uint8_t *ws, int lgtc) {
+    const int tc = 1 << lgtc, tk = 4096 >> lgtc;
+    const int64_t local = tile - od.tile_base;
+    const int tiles_k = od.K_pitch / tk;
+    const int k0 = static_cast<int>(local % tiles_k) * tk;
+    const int c0 = static_cast<int>(local / tiles_k) * tc;
+    const int cc = threadIdx.x & (tc - 1);
+    const int rg = threadIdx.x >> lgtc;
+    const int c = c0 + cc;
+    if (c >= od.P_pad) return;
+    const int kk = k0 + rg * KSTEP;
+    const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
+    const OpTerm tm = terms[od.first_term];
+    const bool cv = c < tm.cols;
+    const int lim = cv ? tm.rows - kk : 0;
+    const T *base = A + (tm.row0 + kk) * rs + (tm.col0 + c) * cs;
+    float raw[KSTEP];
+#pragma unroll
+    for (int j = 0; j < KSTEP; ++j) raw[j] = j < lim ? static_cast<float>(base[j * rs]) : 0.0f;
+    const int x = cv ? DIGIT_TOP_BITS - expo[tm.col0 + c] : 0;
+    const float sc = (x >= -126 && x <= 127 ? __uint_as_float(static_cast<unsigned>(x + 127) << 23)
+                                            : scalbnf(1.0f, x)) * (tm.coef < 0 ? -1.0f : 1.0f);
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(roundf(raw[2 * i] * sc), roundf(raw[2 * i + 1] * sc));
+        pk[i] = *reinterpret_cast<const uint32_t *>(&v);
+    }
+    const int64_t ncb = fam.cols / BLOCK_COLS;
+    const int r = cc & (BLOCK_COLS - 1);
+    const int swz = (r >> 2) & 1;
+    const int64_t cblk = (od.out_col + c) / BLOCK_COLS;
+    uint8_t *row0 = ws + fam.offset + (static_cast<int64_t>(kk / KSTEP) * ncb + cblk) * BLOCK_BYTES + r * 32;
+    // rows 8h .. 8h + 7 sit at 16-byte slot h ^ swz
+    *reinterpret_cast<uint4 *>(row0 + (swz << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4 *>(row0 + ((swz ^ 1) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
 // Half an image row: contraction values 8h .. 8h + 7 of one column, digits
 // Q .. S - 1, one 16-byte store per digit plane at byte `off` (slot h ^ swz)
 // of the column's 32-byte image row.
@@ -757,6 +806,12 @@ __global__ void __launch_bounds__(256, 4) prep_digits_kernel(const T *__restrict
     for (int64_t tile = tile_begin + blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t local;
         const OpDesc &od = o[op_of_tile(o, nops, tile, &local)];  // read where used (register budget)
+        if constexpr (!F8 && S == 1 && sizeof(T) == 4) {  // (FP64 inputs keep the exact fixed point)
+            if (od.nterms == 1) {
+                prep_tile_bf16_single<T>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, 8);
+                continue;
+            }
+        }
         if constexpr (!F8 && sizeof(T) == 4 && S <= 3) {
             prep_tile_narrow<S, T>(A, lda, trans, expo, od, tt, od.tile_base + local, fams.f[od.family], ws, 8);
             continue;
