@@ -53,6 +53,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "fixconv.h"
 #include "kernels.h"
 #include "ptx.cuh"
 
@@ -149,6 +150,82 @@ __device__ __forceinline__ int64_t c_row_offset(const LeafTask &t, int row, int 
         return j * (j + 1) / 2 + t.out_ld;
     }
     return t.out_off + static_cast<int64_t>(row) * t.out_ld;
+}
+
+// 16-byte vector stores and loads of C / M values.
+__device__ __forceinline__ void st16(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st16(double *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+__device__ __forceinline__ void st16(int64_t *p, const int64_t (&v)[2]) {
+    *reinterpret_cast<longlong2 *>(p) = make_longlong2(v[0], v[1]);
+}
+__device__ __forceinline__ void ld16(const float *p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+}
+__device__ __forceinline__ void ld16(const double *p, double (&v)[2]) {
+    const double2 x = *reinterpret_cast<const double2 *>(p);
+    v[0] = x.x, v[1] = x.y;
+}
+__device__ __forceinline__ void ld16(const int64_t *, int64_t (&v)[2]) { v[0] = v[1] = 0; }  // (never scaled)
+// alpha * v + beta * old, as store_scaled computes it
+__device__ __forceinline__ float scaled_val(float v, float old, double alpha, double beta) {
+    const float r = static_cast<float>(alpha) * v;
+    return beta != 0.0 ? fmaf(static_cast<float>(beta), old, r) : r;
+}
+__device__ __forceinline__ double scaled_val(double v, double old, double alpha, double beta) {
+    const double r = alpha * v;
+    return beta != 0.0 ? fma(beta, old, r) : r;
+}
+__device__ __forceinline__ int64_t scaled_val(int64_t v, int64_t, double, double) { return v; }
+
+// Write columns [colbase, colbase + EC) of one tile row, those below lim:
+// out[colbase + i] = val(i) (SCALED: alpha * val(i) + beta * out, the old
+// value read only when beta != 0).  A thread owns a row, so each warp store
+// instruction touches 32 rows of C; 16-byte vectors (where the row segment is
+// 16-byte aligned and the whole vector lies below lim) cut those instructions
+// two- to fourfold.  Other columns are written one at a time.
+template <int EC, bool SCALED, typename O, typename F>
+__device__ __forceinline__ void store_row(O *out, int colbase, int lim, const F &val, double alpha, double beta) {
+    constexpr int VW = 16 / static_cast<int>(sizeof(O));
+    static_assert(EC % VW == 0, "whole vectors");
+    const bool vec = (reinterpret_cast<uintptr_t>(out + colbase) & 15u) == 0;
+#pragma unroll
+    for (int g = 0; g < EC; g += VW) {
+        O *dst = out + colbase + g;
+        if (vec && colbase + g + VW <= lim) {
+            O v[VW];
+#pragma unroll
+            for (int j = 0; j < VW; ++j) v[j] = val(g + j);
+            if constexpr (SCALED) {
+                if (alpha != 1.0 || beta != 0.0) {  // (alpha = 1, beta = 0 store v as it is)
+                    O old[VW];
+                    if (beta != 0.0) {
+                        ld16(dst, old);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < VW; ++j) old[j] = O(0);
+                    }
+#pragma unroll
+                    for (int j = 0; j < VW; ++j) v[j] = scaled_val(v[j], old[j], alpha, beta);
+                }
+            }
+            st16(dst, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                if (colbase + g + j < lim) {
+                    if constexpr (SCALED)
+                        store_scaled(dst + j, val(g + j), alpha, beta);
+                    else
+                        dst[j] = val(g + j);
+                }
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ double exp2d(int x) {
@@ -757,20 +834,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     if (t.kind == OUT_M_F64) {  // Strassen product, in units of the scaled columns
                         double *out = static_cast<double *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
                         const double sc = exp2d(t.shift - 2 * FP8_TOP);
-#pragma unroll
-                        for (int i = 0; i < EC; ++i) {
-                            const int col = colbase + i;
-                            if (col < lim) out[col] = static_cast<double>(T[i]) * sc;
-                        }
+                        store_row<EC, false>(out, colbase, lim, [&](int i) { return static_cast<double>(T[i]) * sc; },
+                                             p.alpha, p.beta);
                     } else {
                         const int er = -2 * FP8_TOP + t.shift + (t.eu >= 0 ? p.expo[t.eu + row] : 0);
                         const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                         float *out = static_cast<float *>(p.C) + c_row_offset(t, row, p.packed);
-#pragma unroll
-                        for (int i = 0; i < EC; ++i) {
-                            const int col = colbase + i;
-                            if (col < lim) store_scaled(out + col, T[i] * exp2f_(er + (ev ? ev[col] : 0)), p.alpha, p.beta);
-                        }
+                        store_row<EC, true>(
+                            out, colbase, lim, [&](int i) { return T[i] * exp2f_(er + (ev ? ev[colbase + i] : 0)); },
+                            p.alpha, p.beta);
                     }
                 }
             } else if (row < t.rows) {
@@ -781,11 +853,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 if (t.kind == OUT_M_I64) {
                     int64_t *out = static_cast<int64_t *>(p.M) + t.out_off + static_cast<int64_t>(row) * t.out_ld;
                     const int64_t wmul = int64_t(1) << wsh;
-#pragma unroll
-                    for (int i = 0; i < EC; ++i) {
-                        const int col = colbase + i;
-                        if (col < lim) out[col] = static_cast<int64_t>(T[i]) * wmul;
-                    }
+                    store_row<EC, false>(out, colbase, lim, [&](int i) { return static_cast<int64_t>(T[i]) * wmul; },
+                                         p.alpha, p.beta);
                 } else {
                     const int er = -(T_FRAC + 2 * DIGIT_TOP_BITS) - t.hbits + t.shift + wsh +
                                    (t.eu >= 0 ? p.expo[t.eu + row] : 0);
@@ -793,23 +862,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                     void *cbase = p.probs ? p.probs[t.prob].C : p.C;
                     if (t.kind == OUT_C_F64) {
                         double *out = static_cast<double *>(cbase) + c_row_offset(t, row, p.packed);
-#pragma unroll
-                        for (int i = 0; i < EC; ++i) {
-                            const int col = colbase + i;
-                            if (col < lim)
-                                store_scaled(out + col, static_cast<double>(T[i]) * exp2d(er + (ev ? ev[col] : 0)),
-                                             p.alpha, p.beta);
-                        }
+                        store_row<EC, true>(
+                            out, colbase, lim,
+                            [&](int i) {
+                                // T 2^x rounded once, on the integer pipe (GB300's FP64 rate is low)
+                                const int x = er + (ev ? ev[colbase + i] : 0);
+                                double v;
+                                if (!ldexp_i64_rn(static_cast<int64_t>(T[i]), x, v))
+                                    v = static_cast<double>(T[i]) * exp2d(x);
+                                return v;
+                            },
+                            p.alpha, p.beta);
                     } else {
                         float *out = static_cast<float *>(cbase) + c_row_offset(t, row, p.packed);
-#pragma unroll
-                        for (int i = 0; i < EC; ++i) {
-                            const int col = colbase + i;
-                            if (col < lim)
-                                store_scaled(out + col,
-                                             __ll2float_rn(static_cast<int64_t>(T[i])) * exp2f_(er + (ev ? ev[col] : 0)),
-                                             p.alpha, p.beta);
-                        }
+                        // W1's 32-bit sums convert directly; 64-bit sums are
+                        // rounded on the integer pipe (the 64-bit conversion runs
+                        // at a small fraction of the 32-bit one's rate)
+                        store_row<EC, true>(
+                            out, colbase, lim,
+                            [&](int i) {
+                                const int x = er + (ev ? ev[colbase + i] : 0);
+                                float v;
+                                if constexpr (W1) {
+                                    v = __int2float_rn(static_cast<int32_t>(T[i])) * exp2f_(x);
+                                } else {
+                                    if (!ldexp_i64_rnf(static_cast<int64_t>(T[i]), x, v))
+                                        v = __ll2float_rn(static_cast<int64_t>(T[i])) * exp2f_(x);
+                                }
+                                return v;
+                            },
+                            p.alpha, p.beta);
                     }
                 }
             }

@@ -29,10 +29,18 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // c <- alpha * v + beta * c; with beta == 0 the old value is not read (so a
 // NaN left in C does not propagate), and alpha == 1, beta == 0 stores v as is.
 __device__ __forceinline__ void store_scaled(double *c, double v, double alpha, double beta) {
+    if (alpha == 1.0 && beta == 0.0) {  // (no FP64 multiply: the product would be v)
+        *c = v;
+        return;
+    }
     const double r = alpha * v;
     *c = beta != 0.0 ? fma(beta, *c, r) : r;
 }
 __device__ __forceinline__ void store_scaled(float *c, float v, double alpha, double beta) {
+    if (alpha == 1.0 && beta == 0.0) {
+        *c = v;
+        return;
+    }
     const float r = static_cast<float>(alpha) * v;
     *c = beta != 0.0 ? fmaf(static_cast<float>(beta), *c, r) : r;
 }
