@@ -1,14 +1,15 @@
-// Scaled integers to IEEE binary64 / binary32 with integer operations only.
+// Scaled integers to IEEE binary64 with integer operations only.
 //
-// The leaf's epilogue turns each exact integer sum T into T * 2^e.  GB300
-// runs FP64 arithmetic (and 64-bit integer conversions) at a small fraction
-// of its integer rate, so the rounded result is built from T's bits instead:
-// normalise, keep the leading 53 (24) bits, round to nearest with ties to
-// even on the bits below (IEEE 754-2019, 4.3.1 roundTiesToEven), and add the
-// biased exponent.  Where the result would not be a normal number the
-// functions return false and the caller takes the floating-point route.
-// Host and device code share these functions (the CPU tests check them
-// against the host's correctly rounded conversion).
+// The leaf's epilogue and the combine turn each exact integer sum T into
+// T * 2^e.  GB300 runs FP64 arithmetic (and conversions to FP64) at a small
+// fraction of its integer rate, so the rounded result is built from T's bits
+// instead: normalise, keep the leading 53 bits, round to nearest with ties
+// to even on the bits below (IEEE 754-2019, 4.3.1 roundTiesToEven), and add
+// the biased exponent.  Where the result would not be a normal number the
+// function returns false and the caller takes the floating-point route.
+// Host and device code share this function (the CPU tests check it against
+// the host's correctly rounded conversion).  FP32 output keeps the hardware
+// int64-to-float conversion, which measured faster than this construction.
 #pragma once
 
 #include <cstdint>
@@ -40,16 +41,6 @@ ATA_HD double bits_to_double_(uint64_t b) {
 #endif
 }
 
-ATA_HD float bits_to_float_(uint32_t b) {
-#ifdef __CUDA_ARCH__
-    return __uint_as_float(b);
-#else
-    float f;
-    std::memcpy(&f, &b, sizeof f);
-    return f;
-#endif
-}
-
 // out = T * 2^e rounded to the nearest double (ties to even).  Returns false
 // (out untouched) unless the result is 0 or a normal number below 2^1023.
 ATA_HD bool ldexp_i64_rn(int64_t T, int e, double &out) {
@@ -69,26 +60,6 @@ ATA_HD bool ldexp_i64_rn(int64_t T, int e, double &out) {
     // The leading one (bit 52, or bit 53 after a rounding carry) adds 1 (2)
     // to the exponent field E + 1022.
     out = bits_to_double_((neg << 63) | ((static_cast<uint64_t>(E + 1022) << 52) + mant));
-    return true;
-}
-
-// out = T * 2^e rounded to the nearest float (ties to even).  Returns false
-// (out untouched) unless the result is 0 or a normal number below 2^127.
-ATA_HD bool ldexp_i64_rnf(int64_t T, int e, float &out) {
-    if (T == 0) {
-        out = 0.0f;
-        return true;
-    }
-    const uint64_t neg = T < 0 ? 1u : 0u;
-    const uint64_t mag = neg ? 0ull - static_cast<uint64_t>(T) : static_cast<uint64_t>(T);
-    const int lz = clz64_(mag);
-    const uint64_t m = mag << lz;                                         // leading one at bit 63
-    uint32_t mant = static_cast<uint32_t>(m >> 40);                       // 24 bits, leading one at bit 23
-    const uint64_t rest = m & ((1ull << 40) - 1u), half = 1ull << 39;    // the 40 bits rounded away
-    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
-    const int E = 63 - lz + e;
-    if (E < -126 || E > 126) return false;
-    out = bits_to_float_((static_cast<uint32_t>(neg) << 31) | ((static_cast<uint32_t>(E + 126) << 23) + mant));
     return true;
 }
 

@@ -1143,19 +1143,17 @@ __device__ __forceinline__ void combine_region(const CombDesc &d, int r0, int co
         const int x = xc + expo[d.e_row0 + row];
         TOut *c = packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
                          : C + d.c_off + static_cast<int64_t>(row) * ldc + col;
-        // A 64-bit sum is rounded on the integer pipe (GB300's FP64 rate,
-        // and with it the 64-bit conversions, is low); int128 sums and
-        // results outside the normal range take the floating-point route.
+        // A 64-bit sum goes to FP64 on the integer pipe (GB300's FP64 rate is
+        // low); int128 sums and results outside the normal range take the
+        // FP64 route.  FP32 output keeps the hardware conversion, which
+        // measured faster than the integer construction.
         if constexpr (sizeof(TOut) == 8) {
             double r;
             if (sizeof(Acc) == 16 || !ldexp_i64_rn(static_cast<int64_t>(sum[i]), x, r))
                 r = acc_to_double(sum[i]) * exp2i(x);
             store_scaled(c, r, alpha, beta);
         } else {
-            float r;
-            if (sizeof(Acc) == 16 || !ldexp_i64_rnf(static_cast<int64_t>(sum[i]), x, r))
-                r = acc_to_float(sum[i]) * exp2f_i(x);
-            store_scaled(c, r, alpha, beta);
+            store_scaled(c, acc_to_float(sum[i]) * exp2f_i(x), alpha, beta);
         }
     }
 }

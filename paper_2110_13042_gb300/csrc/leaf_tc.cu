@@ -875,21 +875,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                             p.alpha, p.beta);
                     } else {
                         float *out = static_cast<float *>(cbase) + c_row_offset(t, row, p.packed);
-                        // W1's 32-bit sums convert directly; 64-bit sums are
-                        // rounded on the integer pipe (the 64-bit conversion runs
-                        // at a small fraction of the 32-bit one's rate)
+                        // (W1's sums are 32-bit: the 32-bit conversion)
                         store_row<EC, true>(
                             out, colbase, lim,
                             [&](int i) {
-                                const int x = er + (ev ? ev[colbase + i] : 0);
-                                float v;
-                                if constexpr (W1) {
-                                    v = __int2float_rn(static_cast<int32_t>(T[i])) * exp2f_(x);
-                                } else {
-                                    if (!ldexp_i64_rnf(static_cast<int64_t>(T[i]), x, v))
-                                        v = __ll2float_rn(static_cast<int64_t>(T[i])) * exp2f_(x);
-                                }
-                                return v;
+                                const float v = W1 ? __int2float_rn(static_cast<int32_t>(T[i]))
+                                                   : __ll2float_rn(static_cast<int64_t>(T[i]));
+                                return v * exp2f_(er + (ev ? ev[colbase + i] : 0));
                             },
                             p.alpha, p.beta);
                     }

@@ -1,6 +1,6 @@
 // Checks the integer-only rounding of csrc/fixconv.h against the host's
-// conversions: (double)T and (float)T round to nearest, ties to even, and
-// ldexp by a power of two is exact while the result stays normal.
+// conversion: (double)T rounds to nearest, ties to even, and ldexp by a power
+// of two is exact while the result stays normal.
 // Prints "<cases> <mismatches> <missed>" and exits 0.
 #include <cfloat>
 #include <cmath>
@@ -27,17 +27,11 @@ static void check(int64_t T, int e) {
     const bool normal = T == 0 || (std::fabs(want) >= DBL_MIN && std::fabs(want) < 0x1p1023);
     if (ok && !(got == want && std::signbit(got) == std::signbit(want))) ++bad;
     if (!ok && normal) ++missed;
-    const float wantf = std::ldexp(static_cast<float>(T), e);
-    float gotf = 1.5f;
-    const bool okf = ata::ldexp_i64_rnf(T, e, gotf);
-    const bool normalf = T == 0 || (std::fabs(wantf) >= FLT_MIN && std::fabs(wantf) < 0x1p127f);
-    if (okf && !(gotf == wantf && std::signbit(gotf) == std::signbit(wantf))) ++bad;
-    if (!okf && normalf) ++missed;
 }
 
 int main() {
     const int64_t specials[] = {0, 1, -1, 2, 3, INT64_MAX, INT64_MIN, INT64_MIN + 1, (1ll << 53) - 1, 1ll << 53,
-                                (1ll << 53) + 1, (1ll << 54) + 2, (1ll << 24) + 1, (1ll << 25) + 3};
+                                (1ll << 53) + 1, (1ll << 54) + 2, (1ll << 54) + 6, (1ll << 60) + (1ll << 7)};
     for (int64_t T : specials)
         for (int e = -1100; e <= 1100; e += 7) check(T, e);
     for (int i = 0; i < 2000000; ++i) {
@@ -45,8 +39,8 @@ int main() {
         const int bits = 1 + static_cast<int>(next() % 63);
         int64_t T = static_cast<int64_t>(r >> (64 - bits));
         const int kind = static_cast<int>(next() % 4);
-        if (kind == 1 && bits > 26) {  // an exact tie at the float or double rounding point
-            const int drop = bits > 54 && (next() & 1) ? bits - 53 : bits - 24;
+        if (kind == 1 && bits > 54) {  // an exact tie at the double rounding point
+            const int drop = bits - 53;
             T = (T >> drop << drop) | (int64_t(1) << (drop - 1));
         }
         if (next() & 1) T = -T;

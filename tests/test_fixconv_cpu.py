@@ -1,6 +1,6 @@
-"""The epilogue's integer-only conversion of an exact sum T to T * 2^e
+"""The integer-only conversion of an exact sum T to T * 2^e in FP64
 (csrc/fixconv.h), checked against the host's correctly rounded int64 to
-double / float conversions on random, tie and range-edge cases."""
+double conversion on random, tie and range-edge cases."""
 import os
 import subprocess
 
