@@ -377,14 +377,40 @@ __device__ __forceinline__ bool step_own(IssueState &st, Shared *sh, uint32_t tm
            (issuer_of<NI>(3) != G || step_acc<S, 3>(st, sh, tmem, da0, db0, abort_flag, status));
 }
 
+// T += a * b as one 32 x 32 -> 64-bit signed multiply-add instruction (on
+// the multiply-add pipe: no integer-ALU shift or carry chain).
+__device__ __forceinline__ void mad_wide(int64_t &t, int32_t a, int32_t b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(t) : "r"(a), "r"(b));
+}
+
 // Add one drained accumulator (16 columns) into T, kept in units of
 // 2^-(27 + h) of the leading digit product (h extra bits for short K).  The
-// scaled value x is an exact integer (|x| <= 2^24).  WIDE: x * 2^s + T as one
-// widening multiply-add (s <= 30 for acc1..acc3), fewer epilogue instructions;
-// it pays where drains dominate (S <= 3), while for larger S its extra live
-// registers spill and the shift-add form is faster.
-template <int ACC, bool WIDE>
+// scaled value x is an exact integer (|x| <= 2^24).  Three equivalent forms
+// (bit-identical T), chosen by measurement:
+//   FORM 0: x << s added to T (integer-ALU shift and 64-bit add);
+//   FORM 1: x * 2^s + T as one widening multiply-add written in C++ (s <= 30
+//           for acc1..acc3): fewer instructions where drains dominate (S <= 3);
+//   FORM 2: every accumulator as mad.wide.s32 (x rescaled so both factors fit
+//           32 bits), no integer-ALU work: the three-issuer path (5-7 digits),
+//           where the drains' ALU work delays the issuers (leaf -1.4 to -1.9 %
+//           at 8192^2; FORM 1 spilled there, and FORM 2 is 2-3 % slower below 4
+//           digits).
+template <int ACC, int FORM>
 __device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int h, float fold_scale) {
+    if constexpr (FORM == 2) {
+        // x = round(v 2^c) exact with |x| <= 2^30, s = (27 + h) - c <= 30:
+        // acc0 c = 6 (|v| <= 2^24), acc1..3 their unit (c = 9, 18, 27), acc4
+        // the fold scale (s = 0).
+        constexpr int C = ACC == 0 ? 6 : ACC == 1 ? 9 : ACC == 2 ? 18 : ACC == 3 ? 27 : 0;
+        const int32_t mul = ACC == 4 ? 1 : (1 << (27 - C + h));
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float v = __uint_as_float(r[i]);
+            const int32_t x = __float2int_rn(ACC == 4 ? v * fold_scale : v * static_cast<float>(1 << C));
+            mad_wide(T[i], x, mul);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const float v = __uint_as_float(r[i]);
@@ -399,7 +425,7 @@ __device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int 
             constexpr float sc = ACC == 1 ? 512.0f : ACC == 2 ? 262144.0f : 134217728.0f;
             constexpr int s0 = ACC == 1 ? 18 : ACC == 2 ? 9 : 0;
             const int x = __float2int_rn(v * sc);
-            if constexpr (WIDE)
+            if constexpr (FORM == 1)
                 T[i] += static_cast<int64_t>(x) * static_cast<int64_t>(1 << (s0 + h));
             else
                 T[i] += static_cast<int64_t>(x) << (s0 + h);
@@ -413,7 +439,7 @@ __device__ __forceinline__ void absorb(int64_t *T, const uint32_t (&r)[16], int 
 // ZERO: also clear what was read, so the next MMA into ACC accumulates onto
 // zero (the grouped issue path of S <= 4).
 // buf: the one-digit accumulator's TMEM buffer (0 for every other case).
-template <int ACC, bool WIDE, bool ZERO>
+template <int ACC, int FORM, bool ZERO>
 __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase, int colbase, Shared *sh,
                                           int h, float fold_scale, int buf = 0) {
     static_assert(EPI_COLS == 32, "two 16-column loads");
@@ -429,8 +455,8 @@ __device__ __forceinline__ void drain_one(int64_t (&T)[EPI_COLS], uint32_t tbase
     }
     tc_fence_before();
     mbar_arrive(&sh->acce[ACC + buf]);
-    absorb<ACC, WIDE>(T, r0, h, fold_scale);
-    absorb<ACC, WIDE>(T + 16, r1, h, fold_scale);
+    absorb<ACC, FORM>(T, r0, h, fold_scale);
+    absorb<ACC, FORM>(T + 16, r1, h, fold_scale);
 }
 
 // FP8 mode: drain the single accumulator (FP32 partial sums of E4M3
@@ -791,11 +817,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         }
                         accf_phase ^= 1u << gi;
                         tc_fence_after();
-                        if (m & 16u) drain_one<4, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (m & 1u) drain_one<0, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (m & 2u) drain_one<1, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (m & 4u) drain_one<2, false, false>(T, tbase, colbase, sh, h, fold_scale);
-                        if (m & 8u) drain_one<3, false, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 16u) drain_one<4, 2, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 1u) drain_one<0, 2, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 2u) drain_one<1, 2, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 4u) drain_one<2, 2, false>(T, tbase, colbase, sh, h, fold_scale);
+                        if (m & 8u) drain_one<3, 2, false>(T, tbase, colbase, sh, h, fold_scale);
                     }
                     if (!good) {
                         ok = false;
@@ -816,11 +842,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                 } else if constexpr (W1) {
                     drain_w1(T, tbase, colbase, sh, ebuf);
                 } else {
-                    if (due & 16u) drain_one<4, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                    if (due & 1u) drain_one<0, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale, S == 1 ? ebuf : 0);
-                    if (due & 2u) drain_one<1, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                    if (due & 4u) drain_one<2, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
-                    if (due & 8u) drain_one<3, (S <= 3), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 16u) drain_one<4, (S <= 3 ? 1 : 0), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 1u) drain_one<0, (S <= 3 ? 1 : 0), ZERO>(T, tbase, colbase, sh, h, fold_scale, S == 1 ? ebuf : 0);
+                    if (due & 2u) drain_one<1, (S <= 3 ? 1 : 0), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 4u) drain_one<2, (S <= 3 ? 1 : 0), ZERO>(T, tbase, colbase, sh, h, fold_scale);
+                    if (due & 8u) drain_one<3, (S <= 3 ? 1 : 0), ZERO>(T, tbase, colbase, sh, h, fold_scale);
                 }
                 if constexpr (S == 1) ebuf ^= 1;
             }
