@@ -32,6 +32,16 @@ __device__ __forceinline__ float exp2f_i(int x) {
     return scalbnf(1.0f, x);
 }
 
+// v * 2^x: one multiply while 2^x is a normal number, else scalbn (one
+// exact scaling and a single rounding, where 2^x alone would under- or
+// overflow although v * 2^x need not: tiny or subnormal columns).
+__device__ __forceinline__ double scale2d(double v, int x) {
+    return (x >= -1022 && x <= 1023) ? v * exp2i(x) : scalbn(v, x);
+}
+__device__ __forceinline__ float scale2f(float v, int x) {
+    return (x >= -126 && x <= 127) ? v * exp2f_i(x) : scalbnf(v, x);
+}
+
 // round(a * 2^sh) as int64 (round half away from zero), computed from the
 // bits of a with integer operations only.  Requires |a * 2^sh| < 2^62.
 __device__ __forceinline__ int64_t fixed_of(double a, int sh) {
@@ -194,10 +204,11 @@ __device__ __forceinline__ int find_desc(const OpDesc *ops, int nops, int64_t ti
 }
 
 // round(a * 2^sh) (half away from zero) without branches, for |a * 2^sh| <=
-// 2^F (guaranteed by the column exponents).  With a = M 2^s' and s = s' + sh
-// <= P = max(F - mantissa bits, 0): r = (M 2^(P+1) + 2^u) >> (u + 1), u = P - s,
-// clamped to 62 (the shifted mantissa stays below 2^62, so a clamped u gives
-// 0, as the exact value < 1/2 requires).
+// 2^F (guaranteed by the column exponents).  With a = M 2^s', s = s' + sh and
+// P = max(F - mantissa bits, 0): r = (X + 2^u) >> (u + 1), X = M 2^(P + 1 + L),
+// L = max(s - P, 0) (only a subnormal a in a column whose maximum is
+// subnormal too has s > P), u = max(P - s, 0) clamped to 62 (fixconv.h, which
+// the CPU tests check against the exact definition).
 template <int F, typename T>
 struct FastFixed {
     static constexpr int MB = sizeof(T) == 8 ? 52 : 23;
@@ -207,46 +218,20 @@ struct FastFixed {
 
 template <int F>
 __device__ __forceinline__ int64_t fixed_of_fast(double a, int sh) {
-    constexpr int P = FastFixed<F, double>::P;
-    const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(a));
-    const int eb = static_cast<int>((bits >> 52) & 0x7FF);
-    const uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
-    const uint64_t M = eb ? (mant | (1ull << 52)) : mant;
-    const int s = (eb ? eb - 1075 : -1074) + sh;
-    const int u = min(max(P - s, 0), 62);
-    const uint64_t r = ((M << (P + 1)) + (1ull << u)) >> (u + 1);
-    return (bits >> 63) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+    return fixed_of_f64<FastFixed<F, double>::P>(a, sh);
 }
 
 template <int F>
 __device__ __forceinline__ int64_t fixed_of_fast(float a, int sh) {
-    constexpr int P = FastFixed<F, float>::P;
-    const uint32_t bits = __float_as_uint(a);
-    const int eb = static_cast<int>((bits >> 23) & 0xFF);
-    const uint64_t mant = bits & 0x7FFFFFu;
-    const uint64_t M = eb ? (mant | 0x800000u) : mant;
-    const int s = (eb ? eb - 150 : -149) + sh;
-    const int u = min(max(P - s, 0), 62);
-    const uint64_t r = ((M << (P + 1)) + (1ull << u)) >> (u + 1);
-    return (bits >> 31) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+    return fixed_of_f32<FastFixed<F, float>::P>(a, sh);
 }
 
-// 32-bit form of fixed_of_fast for FP32 inputs and F <= 29 fraction bits
-// (one to three digits): M 2^(P+1) < 2^31 with P = F - 23 <= 6, and a
-// rounding position past bit 30 leaves |a 2^sh| < 1/2, i.e. 0.  Same result
-// as the 64-bit form.
+// 32-bit form for FP32 inputs and F <= 29 fraction bits (one to three
+// digits); same result as the 64-bit form.
 template <int F>
 __device__ __forceinline__ int32_t fixed32_of_fast(float a, int sh) {
     static_assert(F <= 29, "32-bit fixed point");
-    constexpr int P = F - 23 > 0 ? F - 23 : 0;
-    const uint32_t bits = __float_as_uint(a);
-    const int eb = static_cast<int>((bits >> 23) & 0xFF);
-    const uint32_t mant = bits & 0x7FFFFFu;
-    const uint32_t M = eb ? (mant | 0x800000u) : mant;
-    const int s = (eb ? eb - 150 : -149) + sh;
-    const int u = max(P - s, 0);
-    const uint32_t r = u > 30 ? 0u : ((M << (P + 1)) + (1u << u)) >> (u + 1);
-    return (bits >> 31) ? -static_cast<int32_t>(r) : static_cast<int32_t>(r);
+    return fixed32_of_f32<(F - 23 > 0 ? F - 23 : 0)>(a, sh);
 }
 
 // Digit q of w = V + sum_{j < S-1} 256 * 512^j as the BF16-exact float
@@ -568,17 +553,19 @@ __device__ __forceinline__ void prep_tile_f8_single(const T *__restrict__ A, int
     float raw[KSTEP];
 #pragma unroll
     for (int j = 0; j < KSTEP; ++j) raw[j] = j < lim ? static_cast<float>(base[j * rs]) : 0.0f;
-    // 2^(FP8_TOP - e) (and the term's sign), built from its exponent bits
+    // 2^(FP8_TOP - e) (and the term's sign) as two factors built from their
+    // exponent bits: x reaches 156 for a column whose maximum is subnormal,
+    // and each half stays in range; both products are exact power-of-two
+    // scalings (an intermediate underflow only hits values that round to 0).
     const int x = cv ? FP8_TOP - expo[tm.col0 + c] : 0;
-    const float sc = (x >= -126 && x <= 127 ? __uint_as_float(static_cast<unsigned>(x + 127) << 23)
-                                            : scalbnf(1.0f, x)) * (tm.coef < 0 ? -1.0f : 1.0f);
+    const float sc = exp2f_i(x >> 1) * (tm.coef < 0 ? -1.0f : 1.0f), sc2 = exp2f_i(x - (x >> 1));
     uint32_t pk[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         uint32_t w = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            w |= static_cast<uint32_t>(__nv_cvt_float_to_fp8(raw[4 * i + j] * sc, __NV_SATFINITE, __NV_E4M3))
+            w |= static_cast<uint32_t>(__nv_cvt_float_to_fp8(raw[4 * i + j] * sc * sc2, __NV_SATFINITE, __NV_E4M3))
                  << (8 * j);
         pk[i] = w;
     }
@@ -620,13 +607,14 @@ __device__ __forceinline__ void prep_tile_bf16_single(const T *__restrict__ A, i
     float raw[KSTEP];
 #pragma unroll
     for (int j = 0; j < KSTEP; ++j) raw[j] = j < lim ? static_cast<float>(base[j * rs]) : 0.0f;
+    // 2^(8 - e) as two exact factors (see prep_tile_f8_single)
     const int x = cv ? DIGIT_TOP_BITS - expo[tm.col0 + c] : 0;
-    const float sc = (x >= -126 && x <= 127 ? __uint_as_float(static_cast<unsigned>(x + 127) << 23)
-                                            : scalbnf(1.0f, x)) * (tm.coef < 0 ? -1.0f : 1.0f);
+    const float sc = exp2f_i(x >> 1) * (tm.coef < 0 ? -1.0f : 1.0f), sc2 = exp2f_i(x - (x >> 1));
     uint32_t pk[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const __nv_bfloat162 v = __floats2bfloat162_rn(roundf(raw[2 * i] * sc), roundf(raw[2 * i + 1] * sc));
+        const __nv_bfloat162 v =
+            __floats2bfloat162_rn(roundf(raw[2 * i] * sc * sc2), roundf(raw[2 * i + 1] * sc * sc2));
         pk[i] = *reinterpret_cast<const uint32_t *>(&v);
     }
     const int64_t ncb = fam.cols / BLOCK_COLS;
@@ -1015,14 +1003,14 @@ __global__ void __launch_bounds__(256) prep_f64_kernel(const T *__restrict__ A, 
         const OpTerm tm = terms[od.first_term + t];
         const int c = c0 + cc;
         if (c < tm.cols) {
-            const double sc = exp2i(-expo[tm.col0 + c]);
+            const int x = -expo[tm.col0 + c];
             const int64_t rs = trans ? 1 : lda, cs = trans ? lda : 1;
             const T *col = A + (tm.col0 + c) * cs;
 #pragma unroll
             for (int it = 0; it < 16; ++it) {
                 const int k = k0 + kr0 + 4 * it;
                 if (k < tm.rows) {
-                    const double v = static_cast<double>(col[(tm.row0 + k) * rs]) * sc;
+                    const double v = scale2d(static_cast<double>(col[(tm.row0 + k) * rs]), x);
                     V[it] = tm.coef > 0 ? V[it] + v : V[it] - v;
                 }
             }
@@ -1150,10 +1138,10 @@ __device__ __forceinline__ void combine_region(const CombDesc &d, int r0, int co
         if constexpr (sizeof(TOut) == 8) {
             double r;
             if (sizeof(Acc) == 16 || !ldexp_i64_rn(static_cast<int64_t>(sum[i]), x, r))
-                r = acc_to_double(sum[i]) * exp2i(x);
+                r = scale2d(acc_to_double(sum[i]), x);
             store_scaled(c, r, alpha, beta);
         } else {
-            store_scaled(c, acc_to_float(sum[i]) * exp2f_i(x), alpha, beta);
+            store_scaled(c, scale2f(acc_to_float(sum[i]), x), alpha, beta);
         }
     }
 }
@@ -1213,7 +1201,7 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombDesc *__rest
         if (d.diag && col > row + d.diag_off) continue;  // upper triangle: never written
         store_scaled(packed ? C + packed_at(d.e_row0 + row, d.e_col0 + col)
                             : C + d.c_off + static_cast<int64_t>(row) * ldc + col,
-                     static_cast<TOut>(sum[i] * exp2i(expo[d.e_row0 + row] + ec)), alpha, beta);
+                     static_cast<TOut>(scale2d(sum[i], expo[d.e_row0 + row] + ec)), alpha, beta);
     }
 }
 

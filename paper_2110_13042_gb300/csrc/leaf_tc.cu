@@ -236,6 +236,15 @@ __device__ __forceinline__ float exp2f_(int x) {
     if (x >= -126 && x <= 127) return __uint_as_float(static_cast<unsigned>(x + 127) << 23);
     return scalbnf(1.0f, x);
 }
+// v * 2^x: one multiply while 2^x is a normal number, else scalbn (one
+// exact scaling and a single rounding, where 2^x alone would under- or
+// overflow although v * 2^x need not: tiny or subnormal columns).
+__device__ __forceinline__ double scale2d(double v, int x) {
+    return (x >= -1022 && x <= 1023) ? v * exp2d(x) : scalbn(v, x);
+}
+__device__ __forceinline__ float scale2f(float v, int x) {
+    return (x >= -126 && x <= 127) ? v * exp2f_(x) : scalbnf(v, x);
+}
 
 // All digit pairs (P, Q) of accumulator ACC, unrolled at compile time.  The
 // shared-memory descriptors of digit P / Q differ from the stage's first by
@@ -867,7 +876,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                         const int *ev = t.ev >= 0 ? p.expo + t.ev : nullptr;
                         float *out = static_cast<float *>(p.C) + c_row_offset(t, row, p.packed);
                         store_row<EC, true>(
-                            out, colbase, lim, [&](int i) { return T[i] * exp2f_(er + (ev ? ev[colbase + i] : 0)); },
+                            out, colbase, lim, [&](int i) { return scale2f(T[i], er + (ev ? ev[colbase + i] : 0)); },
                             p.alpha, p.beta);
                     }
                 }
@@ -895,7 +904,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                                 const int x = er + (ev ? ev[colbase + i] : 0);
                                 double v;
                                 if (!ldexp_i64_rn(static_cast<int64_t>(T[i]), x, v))
-                                    v = static_cast<double>(T[i]) * exp2d(x);
+                                    v = scale2d(static_cast<double>(T[i]), x);
                                 return v;
                             },
                             p.alpha, p.beta);
@@ -907,7 +916,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) leaf_tc_kernel(const __grid_co
                             [&](int i) {
                                 const float v = W1 ? __int2float_rn(static_cast<int32_t>(T[i]))
                                                    : __ll2float_rn(static_cast<int64_t>(T[i]));
-                                return v * exp2f_(er + (ev ? ev[colbase + i] : 0));
+                                return scale2f(v, er + (ev ? ev[colbase + i] : 0));
                             },
                             p.alpha, p.beta);
                     }
