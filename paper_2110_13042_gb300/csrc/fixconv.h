@@ -71,6 +71,33 @@ ATA_HD int64_t fixed_of_f64(double a, int sh) {
     return (bits >> 63) ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
 }
 
+// Both round(a * 2^sh) and round(a * 2^(sh - 1)) (half away from zero) from
+// one truncation q = floor(|a| 2^(sh + 1)): for v >= 0 with q = floor(2 v),
+// floor(v + 1/2) = floor((q + 1) / 2) and floor(v / 2 + 1/2) = floor((q + 2) / 4),
+// whatever fraction q dropped.  Same bound as fixed_of_f64: |a 2^sh| <= 2^(53 + P),
+// so q < 2^(55 + P).
+template <int P>
+ATA_HD void fixed_pair_f64(double a, int sh, int64_t &x, int64_t &x_half) {
+    static_assert(P == 0 || P == 1, "q stays below 2^56");
+    uint64_t bits;
+#ifdef __CUDA_ARCH__
+    bits = static_cast<uint64_t>(__double_as_longlong(a));
+#else
+    std::memcpy(&bits, &a, sizeof bits);
+#endif
+    const int eb = static_cast<int>((bits >> 52) & 0x7FF);
+    const uint64_t mant = bits & 0xFFFFFFFFFFFFFull;
+    const uint64_t M = eb ? (mant | (1ull << 52)) : mant;
+    const int s1 = (eb ? eb - 1075 : -1074) + sh + 1;  // |a| 2^(sh + 1) = M 2^s1
+    const int L = s1 > 0 ? s1 : 0;
+    const int u = s1 < 0 ? (-s1 > 63 ? 63 : -s1) : 0;
+    const uint64_t q = (M << L) >> u;
+    const uint64_t r = (q + 1u) >> 1, rh = (q + 2u) >> 2;
+    const bool neg = (bits >> 63) != 0;
+    x = neg ? -static_cast<int64_t>(r) : static_cast<int64_t>(r);
+    x_half = neg ? -static_cast<int64_t>(rh) : static_cast<int64_t>(rh);
+}
+
 // The same for an FP32 value (24-bit significand M, subnormal exponent -149),
 // with P <= 37: X = M 2^(P + 1 + L) <= 2^(P + 25) or M 2^(s + 1) <= 2^(F + 1)
 // with F = P + 23, so X < 2^62.

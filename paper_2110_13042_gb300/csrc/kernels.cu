@@ -707,33 +707,60 @@ __device__ __forceinline__ void prep_fused_tile(const T *__restrict__ A, int64_t
         arow[q] = lim > 0 ? sb.row0 + kh : -1;
         acol[q] = sb.col0 + c;
     }
-    if (L.fuse_f0) {
-        // The planes of A itself (family 0, no operand sum: t = 0) for the
-        // blocks' own elements: each block starts on a K step, so this
-        // lane's 8 rows are half of one image row of A's planes; rows past a
-        // block's end belong to the next block (or are A's zero padding).
-        const Family &f0 = fams.f[0];
-        const int64_t ncb0 = f0.cols / BLOCK_COLS;
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            if (arow[q] < 0) continue;
-            const int r0 = static_cast<int>(acol[q] & (BLOCK_COLS - 1));
-            W w0[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) w0[j] = static_cast<W>(fixed(raw[q][j], F - ex[q])) + static_cast<W>(CADD);
-            uint8_t *dst = ws + f0.offset + (((arow[q] / KSTEP) * S) * ncb0 + acol[q] / BLOCK_COLS) * BLOCK_BYTES +
-                           r0 * 32;
-            store_digits_half<S>(w0, dst, ncb0 * BLOCK_BYTES, (part ^ ((r0 >> 2) & 1)) << 4);
-        }
-    }
+    // The planes of A itself (family 0, no operand sum: t = 0) for the
+    // blocks' own elements: each block starts on a K step, so this lane's 8
+    // rows are half of one image row of A's planes; rows past a block's end
+    // belong to the next block (or are A's zero padding).
+    const Family &f0 = fams.f[0];
+    const int64_t ncb0 = f0.cols / BLOCK_COLS;
+    auto store_f0 = [&](int q, const W (&w0)[R]) {
+        const int r0 = static_cast<int>(acol[q] & (BLOCK_COLS - 1));
+        uint8_t *dst = ws + f0.offset + (((arow[q] / KSTEP) * S) * ncb0 + acol[q] / BLOCK_COLS) * BLOCK_BYTES +
+                       r0 * 32;
+        store_digits_half<S>(w0, dst, ncb0 * BLOCK_BYTES, (part ^ ((r0 >> 2) & 1)) << 4);
+    };
     // UNI: every source value rounded once, for all members
     V x[UNI ? NS : 1][R];
-    if constexpr (UNI) {
+    // FP64 sources with the planes of A and members at t_shift 1 (depth 1):
+    // both roundings of each value from one truncation (fixed_pair_f64,
+    // bit-identical to two conversions)
+    constexpr bool PAIR = UNI && sizeof(T) == 8 && !NARROW && FastFixed<F, T>::ok;
+    bool paired = false;
+    if constexpr (PAIR) {
+        if (L.fuse_f0 && L.t_shift == 1) {
+            paired = true;
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            const int sh = F - L.t_shift - ex[q];
+            for (int q = 0; q < NS; ++q) {
+                W w0[R];
 #pragma unroll
-            for (int j = 0; j < R; ++j) x[q][j] = fixed(raw[q][j], sh);
+                for (int j = 0; j < R; ++j) {
+                    int64_t xf, xh;
+                    fixed_pair_f64<FastFixed<F, T>::P>(static_cast<double>(raw[q][j]), F - ex[q], xf, xh);
+                    x[q][j] = xh;
+                    w0[j] = static_cast<W>(xf) + static_cast<W>(CADD);
+                }
+                if (arow[q] >= 0) store_f0(q, w0);
+            }
+        }
+    }
+    if (!paired) {
+        if (L.fuse_f0) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                if (arow[q] < 0) continue;
+                W w0[R];
+#pragma unroll
+                for (int j = 0; j < R; ++j) w0[j] = static_cast<W>(fixed(raw[q][j], F - ex[q])) + static_cast<W>(CADD);
+                store_f0(q, w0);
+            }
+        }
+        if constexpr (UNI) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int sh = F - L.t_shift - ex[q];
+#pragma unroll
+                for (int j = 0; j < R; ++j) x[q][j] = fixed(raw[q][j], sh);
+            }
         }
     }
     const Family &fam = fams.f[L.family];

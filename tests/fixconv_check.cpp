@@ -55,6 +55,12 @@ static void check_fixed(double a, int sh) {
     const uint64_t mag = exact_fixed_mag(a, sh);
     const int64_t want = std::signbit(a) ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
     if (ata::fixed_of_f64<P>(a, sh) != want) ++fbad;
+    // the pair form: round(a 2^sh) and round(a 2^(sh - 1)) from one truncation
+    const uint64_t mag_h = exact_fixed_mag(a, sh - 1);
+    const int64_t want_h = std::signbit(a) ? -static_cast<int64_t>(mag_h) : static_cast<int64_t>(mag_h);
+    int64_t x = 0, xh = 0;
+    ata::fixed_pair_f64<P>(a, sh, x, xh);
+    if (x != want || xh != want_h) ++fbad;
 }
 
 // a random double with exponent field eb (0: subnormal) and sign
